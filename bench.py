@@ -1,0 +1,364 @@
+"""Throughput of the depth-completion chain (arXiv 1802.00036, Section IV) on GB300.
+
+Default workload: batched 352 x 1216 float32 sparse depth maps (64-beam,
+~5% valid, depths 2-80 m), 64 frames per step, paper defaults (diamond 5x5,
+31x31 fill, median + Gaussian).  A step is one dc_complete_uniform call over
+the batch: both kernels, every step of the chain.  Inputs rotate over 4
+resident batches (4 x 110 MB in, 4 x 110 MB out) so no step finds its data in
+the 129 MB L2.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(the plain C statement of the chain) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H, W = 352, 1216
+BATCH = 64
+ROTATE = 4
+BYTES_PER_PX = 8            # algorithmic: read the sparse map once, write the dense map once
+PAPER_CONTEXT = "paper: 90 Hz per frame on an Intel Core i7-7700K, Python + OpenCV (Sec. V-A)"
+METRIC = "frames/s @352x1216 batched"
+
+
+def workload_config(batch, blur):
+    return {"workload": f"batched {batch} x 352x1216 float32 sparse depth maps, 64-beam ~5% valid, "
+                        f"2-80 m; diamond5, fill31, median+{blur}",
+            "batch": batch, "frame": "352x1216", "blur": blur}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--blur", default="gauss", choices=["gauss", "bilateral"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("DC_BENCH_GLOO") is None else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier_max(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def make_frames(n):
+    from paper_1802_00036_gb300 import synth
+    return synth.make_batch(n, synth.ONE_FRAME, config=0)
+
+
+# ---------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons, sampled every 100 ms."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        if which == "start":
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ts, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((ts, float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        inside = [r for r in rows if self.t0 and self.t1 and self.t0 - 0.05 <= r[0] <= self.t1 + 0.05]
+        note = "during timed region"
+        if not inside and rows:
+            inside = sorted(rows, key=lambda r: abs(r[0] - (self.t1 or r[0])))[:3]
+            note = "nearest samples (timed region shorter than the sampling period)"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside), "note": note}
+
+
+# ------------------------------------------------------------------- CPU oracle
+
+def oracle_throughput(frames, threads: int, rounds: int = 1):
+    """Frames/s of the oracle over `frames`, one frame per thread at a time."""
+    import concurrent.futures
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
+        for _ in range(rounds):
+            list(ex.map(lambda f: oracle.complete(f), frames))
+    dt = time.perf_counter() - t0
+    return len(frames) * rounds / dt, dt
+
+
+def cpu_baseline(frames_pool):
+    cores = os.cpu_count() or 1
+    sample = [frames_pool[i % len(frames_pool)] for i in range(2 * cores)]
+    fps, dt = oracle_throughput(sample, cores)
+    return {"value": round(fps, 3), "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(sample)} frames of 352x1216 (2 per core) through the single-threaded C oracle, "
+                      f"one frame per thread on {cores} threads; {dt:.1f} s wall",
+            "context": PAPER_CONTEXT}
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: each step is a bounded sample of the
+    workload (one frame per host core), frames/s over K timed steps."""
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    pool = make_frames(min(cores, 16))
+    step_frames = [pool[i % len(pool)] for i in range(cores)]
+    for _ in range(args.warmup):
+        oracle_throughput(step_frames, cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_throughput(step_frames, cores)
+    dt = time.perf_counter() - t0
+    fps = cores * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(fps, 3), "unit": "frames/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * dt / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(args.batch, args.blur),
+                       sample=f"oracle on {cores} of the batch's frames per step, one per thread"),
+        "cpu_baseline": {"value": round(fps, 3), "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{cores} frames per step, one per thread"},
+        "e2e": {"value": round(fps, 3), "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------- GPU
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1802_00036_gb300 import dc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B = args.batch
+    host = make_frames(B)                                     # (B, H, W) float32
+    ins = [torch.from_numpy(host).to(dev) for _ in range(ROTATE)]
+    outs = [torch.empty_like(ins[0]) for _ in range(ROTATE)]
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    ctx = dc.Context(local)
+    p = dc.params(blur=args.blur)
+    dc.dc_reserve(ctx.h, B, H, W)
+
+    def step(i):
+        dc.dc_complete_uniform(ctx.h, ins[i % ROTATE].data_ptr(), outs[i % ROTATE].data_ptr(), B, H, W, p, sp)
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            step(i)
+    stream.synchronize()
+    launches_per_step = dc.dc_last_launch_count(ctx.h)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    dc.dc_set_profiling(ctx.h, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.mark("start")
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark("stop")
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    ktimes = dc.dc_kernel_times(ctx.h)
+    dc.dc_set_profiling(ctx.h, False)
+    time.sleep(0.25)
+    clocks.stop()
+    ms_max = barrier_max(ms, world, dev)
+    frames_total = B * args.steps * world
+    fps = frames_total / (ms_max / 1e3)
+
+    # per-kernel averages over the timed region
+    a_ms = statistics.mean(k[0] for k in ktimes) if ktimes else None
+    b_ms = statistics.mean(k[1] for k in ktimes) if ktimes else None
+
+    # per-frame GPU form: one call per frame
+    pf_steps = max(2, min(args.steps // 8, 50))
+    with torch.cuda.stream(stream):
+        for i in range(B):
+            dc.dc_complete_uniform(ctx.h, ins[0][i].data_ptr(), outs[0][i].data_ptr(), 1, H, W, p, sp)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(pf_steps):
+        for i in range(B):
+            dc.dc_complete_uniform(ctx.h, ins[s % ROTATE][i].data_ptr(), outs[s % ROTATE][i].data_ptr(),
+                                   1, H, W, p, sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pf_fps = B * pf_steps / (e0.elapsed_time(e1) / 1e3)
+
+    # end to end through the host-buffer entry point (pinned), copies inside the timed region
+    hin = torch.from_numpy(host).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    e2e_steps = max(3, min(args.steps // 4, 100))
+    for _ in range(2):
+        dc.dc_complete_host(ctx.h, hin.data_ptr(), hout.data_ptr(), B, H, W, p, sp)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dc.dc_complete_host(ctx.h, hin.data_ptr(), hout.data_ptr(), B, H, W, p, sp)
+    e2e_s = time.perf_counter() - t0
+    e2e_s = barrier_max(e2e_s, world, dev)
+    e2e_fps = B * e2e_steps * world / e2e_s
+
+    if rank != 0:
+        ctx.close()
+        return
+
+    hbm, peak_kind = peaks()
+    px = H * W
+    # dominant kernel: its algorithmic bytes are its own input map read once and
+    # output map written once (8 B per pixel), over its CUDA-event duration
+    dom = "stage_b" if (b_ms or 0) >= (a_ms or 0) else "stage_a"
+    dom_ms = max(a_ms or 0, b_ms or 0)
+    achieved = BYTES_PER_PX * px * B / (dom_ms / 1e3) / 1e9 if dom_ms else None
+    line = {
+        "metric": METRIC, "value": round(fps, 1), "unit": "frames/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(B, args.blur),
+                       parallelism="replicas" if world > 1 else "single",
+                       l2=f"inputs rotate over {ROTATE} resident batches "
+                          f"({ROTATE * B * px * 4 / 1e6:.0f} MB in + same out > 129 MB L2)"),
+        "roofline": {
+            "bound": "hbm", "kernel": dom,
+            "achieved": round(achieved, 1) if achieved else None,
+            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
+            "peak_kind": peak_kind,
+            "traffic": None,
+            "bytes_per_px": BYTES_PER_PX,
+            "path_achieved": round(BYTES_PER_PX * px * fps / 1e9, 1),
+            "path_frac": round(BYTES_PER_PX * px * fps / 1e9 / hbm, 4),
+        },
+        "kernels_ms": {"stage_a": round(a_ms, 4) if a_ms else None, "stage_b": round(b_ms, 4) if b_ms else None,
+                       "calls_timed": len(ktimes)},
+        "per_frame": {"value": round(pf_fps, 1), "unit": "frames/s", "note": "one dc_complete call per frame"},
+        "e2e": {"value": round(e2e_fps, 1), "unit": "frames/s",
+                "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
+                "note": "dc_complete_host on pinned host buffers, copies in the timed region"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks.summary(),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(host)
+    elif not args.no_cpu_baseline and rank == 0:
+        line["cpu_baseline"] = None
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        # the CPU oracle needs no process group: rank 0 runs it, others exit
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
+        return
+    world, rank, local = dist_setup(args.gpus)
+    run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

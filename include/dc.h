@@ -1,0 +1,171 @@
+/*
+ * dc.h -- C-ABI of libdc, the GB300 (sm_103a) depth-completion library.
+ *
+ * The library runs the eight-step classical depth-completion chain of
+ * Ku, Harakeh, Waslander, "In Defense of Classical Image Processing: Fast
+ * Depth Completion on the CPU" (arXiv 1802.00036), Section IV:
+ *
+ *   1 invert valid depths, D_inv = 100 - D                    (Sec. IV-1)
+ *   2 dilate with a 5x5 diamond (or another Fig. 4 element)   (Sec. IV-2)
+ *   3 5x5 full-kernel morphological close                     (Sec. IV-3)
+ *   4 7x7 full dilation written into empty pixels only        (Sec. IV-4)
+ *   5 copy each column's topmost value up to row 0            (Sec. IV-5)
+ *   6 31x31 full dilation written into empty pixels only      (Sec. IV-6)
+ *   7 5x5 median, then 5x5 Gaussian (or bilateral) blur       (Sec. IV-7)
+ *   8 invert back, D_out = 100 - D_inv                         (Sec. IV-8)
+ *
+ * It is the problem of Section III: a sparse M x N depth map in, a dense map
+ * of the same size out; the colour image is not used.
+ *
+ * Conventions (all entry points):
+ *   - Maps are row-major float32, 0 = empty, metres.  A pixel is empty when
+ *     its value is below 0.1 (raw or inverted).  Row pitches are in
+ *     elements, >= W.
+ *   - Device pointers are CUDA device (or managed) memory of the context's
+ *     device, owned by the caller; they must stay valid until the stream has
+ *     passed the call.  Host pointers are ordinary or pinned host memory.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Device work is asynchronous on it unless stated.
+ *   - Arguments are checked before any work is queued; a failed check
+ *     queues nothing and returns DC_ERR_INVALID_ARG.  Asynchronous CUDA
+ *     errors surface from dc_last_async_error() or from the next call.
+ *   - A context is not thread-safe: use one per host thread.  Calls on one
+ *     context run in call order on the device even when they name different
+ *     streams (a later call's stream waits for the earlier call), because
+ *     they share the context's scratch; use several contexts for overlap.
+ *   - Results are deterministic: every pixel's arithmetic is independent of
+ *     tiling, batch composition and launch shape.
+ *   - Max and min ignore out-of-frame pixels; the median replicates the
+ *     border; the blurs mirror it without repeating the edge (reflect-101).
+ */
+#ifndef DC_H
+#define DC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DC_OK = 0,
+    DC_ERR_INVALID_ARG = 1, /* bad pointer, size, pitch, aliasing or param  */
+    DC_ERR_OOM = 2,         /* scratch would exceed the budget, or malloc   */
+    DC_ERR_CUDA = 3,        /* a CUDA runtime call failed                   */
+    DC_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up           */
+    DC_ERR_UNSUPPORTED = 5  /* valid request this build cannot serve        */
+} dc_status;
+
+/* First structuring element, step 2 (Sec. IV-2, Fig. 4, Table 2). */
+typedef enum {
+    DC_K_DIAMOND5 = 0, /* |dy|+|dx| <= 2, 13 taps (paper's choice) */
+    DC_K_FULL5 = 1,    /* 5x5                                      */
+    DC_K_CROSS5 = 2,   /* dy == 0 or dx == 0 within 5x5, 9 taps    */
+    DC_K_FULL3 = 3,    /* 3x3                                      */
+    DC_K_CIRCLE5 = 4,  /* dy^2+dx^2 <= 5, 21 taps                  */
+    DC_K_FULL7 = 5     /* 7x7                                      */
+} dc_kernel;
+
+/* Blur of step 7 after the optional median (Sec. IV-7, Table 3). */
+typedef enum { DC_BLUR_NONE = 0, DC_BLUR_GAUSS = 1, DC_BLUR_BILATERAL = 2 } dc_blur;
+
+/* Where the chain stops; every stop except DC_STOP_FULL returns the map in
+ * the inverted domain (100 - depth on non-empty pixels, 0 elsewhere). */
+typedef enum {
+    DC_STOP_FULL = 0,
+    DC_STOP_INVERT = 1,
+    DC_STOP_DILATE = 2,
+    DC_STOP_CLOSE = 3,
+    DC_STOP_FILL7 = 4,
+    DC_STOP_EXTEND = 5,
+    DC_STOP_FILL_LARGE = 6,
+    DC_STOP_MEDIAN = 7,
+    DC_STOP_BLUR = 8
+} dc_stage;
+
+typedef struct {
+    int first_kernel;  /* dc_kernel, step 2; paper: DC_K_DIAMOND5            */
+    int large_fill;    /* odd side of the step-6 square, 3..63; paper: 31    */
+    int median;        /* 1: 5x5 median in step 7; paper: 1                  */
+    int blur;          /* dc_blur; paper: DC_BLUR_GAUSS                      */
+    float sigma_space; /* bilateral spatial sigma in pixels (default 1.5)    */
+    float sigma_color; /* bilateral range sigma, inverted metres (0.5)       */
+    int extend_top;    /* 1: step 5 on (Sec. V-B skips 5 and 6 for clouds)   */
+    int extend_rows;   /* < 0: extend to row 0; else at most this many rows  */
+    int large_fill_on; /* 1: step 6 on                                       */
+    int stop_after;    /* dc_stage                                           */
+} dc_params;
+
+/* One frame of a batch.  `in` and `out` are device pointers; they must not
+ * overlap (every step reads a neighbourhood, so in-place is refused). */
+typedef struct {
+    const float* in;
+    float* out;
+    int H, W;
+    int in_pitch, out_pitch; /* elements; >= W */
+} dc_frame;
+
+typedef struct dc_ctx dc_ctx;
+
+/* Fill *p with the paper's final design (diamond 5x5, 31x31 fill, median +
+ * Gaussian, full chain).  Returns DC_ERR_INVALID_ARG for p == NULL. */
+dc_status dc_params_default(dc_params* p);
+
+/* Create a context on CUDA device `device`.  The context owns its scratch
+ * (the step-4 map between the two kernels, per-column top rows, frame
+ * tables, staging for host calls).  Scratch grows on demand up to
+ * `scratch_budget_bytes` (0 = no limit); a call that would need more
+ * returns DC_ERR_OOM.  *ctx is set only on DC_OK. */
+dc_status dc_create(dc_ctx** ctx, int device, size_t scratch_budget_bytes);
+
+/* Run the chain on `n_frames` frames of any sizes, in one pass of the two
+ * kernels over all frames' tiles.  Asynchronous on `stream`.  n_frames == 0
+ * is a no-op.  Scratch grows (synchronously, outside any stream capture) if
+ * this batch needs more than earlier ones. */
+dc_status dc_complete(dc_ctx* ctx, const dc_frame* frames, int n_frames,
+                      const dc_params* params, void* stream);
+
+/* Same chain on `n` packed frames of one size: frame i is at
+ * in + i*H*W and out + i*H*W (pitch W).  Device pointers; asynchronous. */
+dc_status dc_complete_uniform(dc_ctx* ctx, const float* in, float* out, int n,
+                              int H, int W, const dc_params* params, void* stream);
+
+/* Same as dc_complete_uniform but `host_in` / `host_out` are HOST buffers
+ * (pinned memory gives full copy bandwidth): copies in, runs, copies out
+ * on `stream` and returns when the result is in host_out. */
+dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, int n,
+                           int H, int W, const dc_params* params, void* stream);
+
+/* Grow scratch now for batches of up to `n_frames` frames of up to H x W,
+ * so that later calls of that size do not allocate. */
+dc_status dc_reserve(dc_ctx* ctx, int n_frames, int H, int W);
+
+/* Number of kernel launches the last dc_complete* call queued. */
+int dc_last_launch_count(const dc_ctx* ctx);
+
+/* Per-kernel timing.  With profiling on, every later call records CUDA
+ * events around each of its kernels on the call's stream (a ring of the last
+ * DC_PROFILE_CALLS calls).  Turning it on allocates the events. */
+#define DC_PROFILE_CALLS 4096
+dc_status dc_set_profiling(dc_ctx* ctx, int on);
+
+/* Wait for the profiled calls and write, for each of the last `max_calls`
+ * profiled calls (oldest first), the milliseconds of stage A (steps 1-4)
+ * and of stage B (steps 5-8; 0 when not launched) to ms[2*i], ms[2*i+1].
+ * *n_out receives the number of calls written.  Clears the ring. */
+dc_status dc_kernel_times(dc_ctx* ctx, float* ms, int max_calls, int* n_out);
+
+/* First asynchronous error seen on the context's work so far (clears it).
+ * Synchronises the context's last stream. */
+dc_status dc_last_async_error(dc_ctx* ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char* dc_status_str(dc_status s);
+
+/* Free the context and its scratch.  Waits for its queued work. */
+void dc_destroy(dc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DC_H */

@@ -1,0 +1,95 @@
+// common.cuh -- definitions shared by the libdc kernels and host code.
+//
+// Depth completion of arXiv 1802.00036, Section IV.  Two kernels split the
+// chain where a whole-column dependency appears (step 5 needs the topmost
+// non-empty row of every column after step 4):
+//   stage A: steps 1-4 on halo'd tiles, writes the step-4 map C to scratch
+//            and the per-column top row with atomicMin;
+//   stage B: steps 5-8 on halo'd tiles of C, writes the output.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dcgb {
+
+// A pixel is empty below 0.1 (Section IV-1: empty pixels hold 0, valid
+// inverted depths lie 20 m or more above them).
+constexpr float kEmptyBelow = 0.1f;
+// D_inv = 100 - D (Section IV-1 and IV-8).
+constexpr float kInvertFrom = 100.0f;
+
+// top[] entries start at this value; any real row is smaller.
+constexpr int kNoTop = 0x7F7F7F7F;
+
+// Stage A output tile.
+constexpr int kTileAH = 32;
+constexpr int kTileAW = 64;
+constexpr int kThreadsA = 256;
+// Stage B output tile.
+constexpr int kTileBH = 32;
+constexpr int kTileBW = 64;
+constexpr int kThreadsB = 256;
+
+// Largest step-6 square side the kernels accept.
+constexpr int kMaxLargeFill = 63;
+
+// Codes shared with include/dc.h.
+enum Shape { kDiamond5 = 0, kFull5 = 1, kCross5 = 2, kFull3 = 3, kCircle5 = 4, kFull7 = 5 };
+enum Blur { kBlurNone = 0, kBlurGauss = 1, kBlurBilateral = 2 };
+enum Stop {
+    kStopFull = 0, kStopInvert = 1, kStopDilate = 2, kStopClose = 3, kStopFill7 = 4,
+    kStopExtend = 5, kStopFillLarge = 6, kStopMedian = 7, kStopBlur = 8
+};
+
+// One frame of a batch as the kernels see it.
+struct FrameDesc {
+    const float* in;   // sparse depth, in_pitch floats per row
+    float* out;        // result, out_pitch floats per row
+    float* c;          // step-4 map, c_pitch floats per row (scratch)
+    int* top;          // W entries: topmost non-empty row of C (scratch)
+    int H, W;
+    int in_pitch, out_pitch, c_pitch;
+    int tiles_x_a, base_a;  // stage A: tiles per row of tiles, first flat tile
+    int tiles_x_b, base_b;  // stage B: same
+};
+
+// Runtime parameters of stage B.
+struct StageBParams {
+    int large_radius;   // step-6 half width; 0 with large_fill_on == 0
+    int large_fill_on;
+    int median;
+    int blur;
+    int extend_top;
+    int extend_rows;    // < 0: unlimited
+    int stop;
+    float ws[5];        // bilateral spatial weight for dy^2+dx^2 = 0,1,2,(3),4
+    float inv_2sc2;     // 1 / (2 sigma_color^2)
+};
+
+__device__ __forceinline__ bool is_empty(float v) { return !(v >= kEmptyBelow); }
+
+__device__ __forceinline__ float ninf() { return __int_as_float(0xff800000); }
+__device__ __forceinline__ float pinf() { return __int_as_float(0x7f800000); }
+
+// Frame owning flat tile t: the last f with base(f) <= t.
+template <bool kStageA>
+__device__ __forceinline__ int find_frame(const FrameDesc* __restrict__ d, int n, int t)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        int b = kStageA ? d[mid].base_a : d[mid].base_b;
+        if (b <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Launchers (stage_a.cu, stage_b.cu).  Return cudaGetLastError().
+cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_tiles,
+                           int shape, int stop, int sm_count, cudaStream_t stream);
+cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,
+                           const StageBParams& p, int sm_count, cudaStream_t stream);
+size_t stage_b_smem_bytes(int large_radius);
+
+}  // namespace dcgb

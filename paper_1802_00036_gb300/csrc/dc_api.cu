@@ -1,0 +1,487 @@
+// dc_api.cu -- the C-ABI of libdc (include/dc.h): argument checks, scratch,
+// frame tables and the two kernel launches per call.
+#include "../../include/dc.h"
+#include "common.cuh"
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace dcgb;
+
+// Calls rotate over kSlots frame tables so that the host only waits when
+// kSlots calls are still in flight; each slot's event marks the end of the
+// call that last used it.
+constexpr int kSlots = 16;
+
+struct TableSlot {
+    FrameDesc* d = nullptr;      // device copy read by the kernels
+    FrameDesc* h = nullptr;      // pinned staging
+    cudaEvent_t done = nullptr;  // recorded after the call's last kernel
+};
+
+struct dc_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t budget = 0;  // 0 = unlimited
+    // scratch
+    float* c = nullptr;       // step-4 maps, all frames
+    size_t c_cap = 0;         // floats
+    int* top = nullptr;       // per-column tops, all frames
+    size_t top_cap = 0;       // ints
+    TableSlot slot[kSlots];
+    int frames_cap = 0;       // descriptors per slot
+    unsigned long long calls = 0;
+    // staging for host calls
+    float* io_in = nullptr;
+    float* io_out = nullptr;
+    size_t io_cap = 0;        // floats each
+    // bookkeeping
+    cudaStream_t last_stream = nullptr;
+    cudaEvent_t last_done = nullptr;  // event of the latest call, or null
+    int last_launches = 0;
+    dc_status sticky = DC_OK;
+    // profiling ring: 3 events per call (before A, between, after B)
+    bool profiling = false;
+    cudaEvent_t* prof_ev = nullptr;
+    int prof_next = 0;     // next ring entry
+    int prof_count = 0;    // valid entries
+    int prof_has_b[DC_PROFILE_CALLS] = {};
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+size_t scratch_bytes(size_t c_floats, size_t top_ints, int frames, size_t io_floats)
+{
+    return c_floats * sizeof(float) + top_ints * sizeof(int) +
+           (size_t)kSlots * (size_t)frames * sizeof(FrameDesc) + 2 * io_floats * sizeof(float);
+}
+
+bool params_ok(const dc_params* p)
+{
+    if (!p) return false;
+    if (p->first_kernel < DC_K_DIAMOND5 || p->first_kernel > DC_K_FULL7) return false;
+    if (p->large_fill_on && (p->large_fill < 1 || p->large_fill > kMaxLargeFill || (p->large_fill % 2) == 0))
+        return false;
+    if (p->blur < DC_BLUR_NONE || p->blur > DC_BLUR_BILATERAL) return false;
+    if (p->blur == DC_BLUR_BILATERAL && (!(p->sigma_space > 0.0f) || !(p->sigma_color > 0.0f) ||
+                                         !std::isfinite(p->sigma_space) || !std::isfinite(p->sigma_color)))
+        return false;
+    if (p->stop_after < DC_STOP_FULL || p->stop_after > DC_STOP_BLUR) return false;
+    return true;
+}
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb)
+{
+    const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+    return a0 < b0 + nb && b0 < a0 + na;
+}
+
+dc_status grow(dc_ctx* ctx, size_t c_floats, size_t top_ints, int frames, size_t io_floats)
+{
+    const bool need = c_floats > ctx->c_cap || top_ints > ctx->top_cap || frames > ctx->frames_cap ||
+                      io_floats > ctx->io_cap;
+    if (!need) return DC_OK;
+    const size_t nc = c_floats > ctx->c_cap ? c_floats : ctx->c_cap;
+    const size_t nt = top_ints > ctx->top_cap ? top_ints : ctx->top_cap;
+    const int nf = frames > ctx->frames_cap ? frames : ctx->frames_cap;
+    const size_t ni = io_floats > ctx->io_cap ? io_floats : ctx->io_cap;
+    if (ctx->budget && scratch_bytes(nc, nt, nf, ni) > ctx->budget) return DC_ERR_OOM;
+    // queued work may still use the old buffers
+    if (cudaDeviceSynchronize() != cudaSuccess) return DC_ERR_CUDA;
+    if (nc > ctx->c_cap) {
+        cudaFree(ctx->c);
+        ctx->c = nullptr;
+        ctx->c_cap = 0;
+        if (cudaMalloc(&ctx->c, nc * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return DC_ERR_OOM; }
+        ctx->c_cap = nc;
+    }
+    if (nt > ctx->top_cap) {
+        cudaFree(ctx->top);
+        ctx->top = nullptr;
+        ctx->top_cap = 0;
+        if (cudaMalloc(&ctx->top, nt * sizeof(int)) != cudaSuccess) { cudaGetLastError(); return DC_ERR_OOM; }
+        ctx->top_cap = nt;
+    }
+    if (nf > ctx->frames_cap) {
+        ctx->frames_cap = 0;
+        for (TableSlot& sl : ctx->slot) {
+            cudaFree(sl.d);
+            cudaFreeHost(sl.h);
+            sl.d = nullptr;
+            sl.h = nullptr;
+        }
+        for (TableSlot& sl : ctx->slot) {
+            if (cudaMalloc(&sl.d, nf * sizeof(FrameDesc)) != cudaSuccess ||
+                cudaMallocHost(&sl.h, nf * sizeof(FrameDesc)) != cudaSuccess) {
+                cudaGetLastError();
+                return DC_ERR_OOM;
+            }
+        }
+        ctx->frames_cap = nf;
+    }
+    if (ni > ctx->io_cap) {
+        cudaFree(ctx->io_in);
+        cudaFree(ctx->io_out);
+        ctx->io_in = ctx->io_out = nullptr;
+        ctx->io_cap = 0;
+        if (cudaMalloc(&ctx->io_in, ni * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&ctx->io_out, ni * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return DC_ERR_OOM;
+        }
+        ctx->io_cap = ni;
+    }
+    return DC_OK;
+}
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Scratch one frame needs: step-4 map rows padded to 32 floats, tops padded.
+size_t frame_c_floats(int H, int W) { return round_up((size_t)W, 32) * (size_t)H; }
+size_t frame_top_ints(int W) { return round_up((size_t)W, 32); }
+
+dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cudaStream_t stream)
+{
+    ctx->last_launches = 0;
+    if (n == 0) return DC_OK;
+
+    // layout of scratch and tiles
+    std::vector<FrameDesc> desc((size_t)n);
+    size_t c_off = 0, top_off = 0;
+    long long tiles_a = 0, tiles_b = 0;
+    for (int i = 0; i < n; ++i) {
+        const dc_frame& f = frames[i];
+        FrameDesc& d = desc[(size_t)i];
+        d.in = f.in;
+        d.out = f.out;
+        d.H = f.H;
+        d.W = f.W;
+        d.in_pitch = f.in_pitch;
+        d.out_pitch = f.out_pitch;
+        d.c_pitch = (int)round_up((size_t)f.W, 32);
+        d.tiles_x_a = ceil_div(f.W, kTileAW);
+        d.tiles_x_b = ceil_div(f.W, kTileBW);
+        d.base_a = (int)tiles_a;
+        d.base_b = (int)tiles_b;
+        tiles_a += (long long)d.tiles_x_a * ceil_div(f.H, kTileAH);
+        tiles_b += (long long)d.tiles_x_b * ceil_div(f.H, kTileBH);
+        d.c = reinterpret_cast<float*>(c_off);  // offsets until scratch is known
+        d.top = reinterpret_cast<int*>(top_off);
+        c_off += frame_c_floats(f.H, f.W);
+        top_off += frame_top_ints(f.W);
+    }
+    if (tiles_a > INT32_MAX / 2 || tiles_b > INT32_MAX / 2) return DC_ERR_UNSUPPORTED;
+
+    const bool need_b = (p->stop_after == DC_STOP_FULL || p->stop_after >= DC_STOP_EXTEND);
+    dc_status s = grow(ctx, need_b ? c_off : 0, need_b ? top_off : 0, n, 0);
+    if (s != DC_OK) return s;
+    for (auto& d : desc) {
+        d.c = need_b ? ctx->c + reinterpret_cast<size_t>(d.c) : nullptr;
+        d.top = need_b ? ctx->top + reinterpret_cast<size_t>(d.top) : nullptr;
+    }
+
+    // frame table: take the next slot once the call that last used it is done
+    TableSlot& sl = ctx->slot[ctx->calls % kSlots];
+    if (cudaEventSynchronize(sl.done) != cudaSuccess) return DC_ERR_CUDA;
+    // calls share the scratch: order this one after the previous call
+    if (ctx->last_done && stream != ctx->last_stream &&
+        cudaStreamWaitEvent(stream, ctx->last_done, 0) != cudaSuccess)
+        return DC_ERR_CUDA;
+    std::memcpy(sl.h, desc.data(), desc.size() * sizeof(FrameDesc));
+    if (cudaMemcpyAsync(sl.d, sl.h, desc.size() * sizeof(FrameDesc), cudaMemcpyHostToDevice, stream) !=
+        cudaSuccess)
+        return DC_ERR_CUDA;
+
+    if (need_b && cudaMemsetAsync(ctx->top, 0x7F, top_off * sizeof(int), stream) != cudaSuccess)
+        return DC_ERR_CUDA;
+
+    cudaEvent_t* ev = nullptr;
+    if (ctx->profiling) {
+        ev = ctx->prof_ev + 3 * ctx->prof_next;
+        ctx->prof_has_b[ctx->prof_next] = need_b ? 1 : 0;
+        ctx->prof_next = (ctx->prof_next + 1) % DC_PROFILE_CALLS;
+        if (ctx->prof_count < DC_PROFILE_CALLS) ++ctx->prof_count;
+        if (cudaEventRecord(ev[0], stream) != cudaSuccess) return DC_ERR_CUDA;
+    }
+    const int stop_a = need_b ? kStopFull : p->stop_after;
+    cudaError_t e = launch_stage_a(sl.d, n, (int)tiles_a, p->first_kernel, stop_a, ctx->sm_count, stream);
+    if (e != cudaSuccess) return DC_ERR_CUDA;
+    ctx->last_launches = 1;
+    if (ev && cudaEventRecord(ev[1], stream) != cudaSuccess) return DC_ERR_CUDA;
+    if (need_b) {
+        StageBParams bp{};
+        bp.large_fill_on = p->large_fill_on ? 1 : 0;
+        bp.large_radius = p->large_fill_on ? p->large_fill / 2 : 0;
+        bp.median = p->median ? 1 : 0;
+        bp.blur = p->blur;
+        bp.extend_top = p->extend_top ? 1 : 0;
+        bp.extend_rows = p->extend_rows;
+        bp.stop = p->stop_after;
+        const double ss = p->blur == DC_BLUR_BILATERAL ? p->sigma_space : 1.0;
+        const double sc = p->blur == DC_BLUR_BILATERAL ? p->sigma_color : 1.0;
+        for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));
+        bp.inv_2sc2 = (float)(1.0 / (2.0 * sc * sc));
+        e = launch_stage_b(sl.d, n, (int)tiles_b, bp, ctx->sm_count, stream);
+        if (e != cudaSuccess) return DC_ERR_CUDA;
+        ctx->last_launches = 2;
+    }
+    if (ev && cudaEventRecord(ev[2], stream) != cudaSuccess) return DC_ERR_CUDA;
+    if (cudaEventRecord(sl.done, stream) != cudaSuccess) return DC_ERR_CUDA;
+    ctx->last_done = sl.done;
+    ctx->last_stream = stream;
+    ++ctx->calls;
+    return DC_OK;
+}
+
+dc_status check_frames(const dc_frame* frames, int n)
+{
+    if (n < 0 || (n > 0 && !frames)) return DC_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        const dc_frame& f = frames[i];
+        if (!f.in || !f.out || f.H < 1 || f.W < 1 || f.in_pitch < f.W || f.out_pitch < f.W)
+            return DC_ERR_INVALID_ARG;
+        if ((size_t)f.H * (size_t)f.in_pitch > (size_t)INT32_MAX * 4) return DC_ERR_UNSUPPORTED;
+        if (((uintptr_t)f.in % sizeof(float)) != 0 || ((uintptr_t)f.out % sizeof(float)) != 0)
+            return DC_ERR_INVALID_ARG;
+        const size_t in_bytes = ((size_t)(f.H - 1) * f.in_pitch + f.W) * sizeof(float);
+        const size_t out_bytes = ((size_t)(f.H - 1) * f.out_pitch + f.W) * sizeof(float);
+        for (int j = 0; j < n; ++j) {
+            const dc_frame& g = frames[j];
+            const size_t g_in = ((size_t)(g.H - 1) * g.in_pitch + g.W) * sizeof(float);
+            if (overlap(f.out, out_bytes, g.in, g_in)) return DC_ERR_INVALID_ARG;
+            if (j != i) {
+                const size_t g_out = ((size_t)(g.H - 1) * g.out_pitch + g.W) * sizeof(float);
+                if (overlap(f.out, out_bytes, g.out, g_out)) return DC_ERR_INVALID_ARG;
+            }
+        }
+        (void)in_bytes;
+    }
+    return DC_OK;
+}
+
+dc_status note(dc_ctx* ctx, dc_status s)
+{
+    if (s == DC_ERR_CUDA && ctx->sticky == DC_OK) ctx->sticky = s;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+dc_status dc_params_default(dc_params* p)
+{
+    if (!p) return DC_ERR_INVALID_ARG;
+    p->first_kernel = DC_K_DIAMOND5;
+    p->large_fill = 31;
+    p->median = 1;
+    p->blur = DC_BLUR_GAUSS;
+    p->sigma_space = 1.5f;
+    p->sigma_color = 0.5f;
+    p->extend_top = 1;
+    p->extend_rows = -1;
+    p->large_fill_on = 1;
+    p->stop_after = DC_STOP_FULL;
+    return DC_OK;
+}
+
+dc_status dc_create(dc_ctx** out, int device, size_t scratch_budget_bytes)
+{
+    if (!out) return DC_ERR_INVALID_ARG;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) { cudaGetLastError(); return DC_ERR_CUDA; }
+    if (device < 0 || device >= count) return DC_ERR_INVALID_ARG;
+    dc_ctx* ctx = new (std::nothrow) dc_ctx();
+    if (!ctx) return DC_ERR_OOM;
+    ctx->device = device;
+    ctx->budget = scratch_budget_bytes;
+    DeviceGuard g(device);
+    bool ok = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) == cudaSuccess;
+    for (TableSlot& sl : ctx->slot)
+        ok = ok && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        dc_destroy(ctx);
+        return DC_ERR_CUDA;
+    }
+    *out = ctx;
+    return DC_OK;
+}
+
+dc_status dc_reserve(dc_ctx* ctx, int n_frames, int H, int W)
+{
+    if (!ctx || n_frames < 0 || H < 1 || W < 1) return DC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    return note(ctx, grow(ctx, frame_c_floats(H, W) * (size_t)n_frames,
+                          frame_top_ints(W) * (size_t)n_frames, n_frames, 0));
+}
+
+dc_status dc_complete(dc_ctx* ctx, const dc_frame* frames, int n_frames, const dc_params* params,
+                      void* stream)
+{
+    if (!ctx || !params_ok(params)) return DC_ERR_INVALID_ARG;
+    dc_status s = check_frames(frames, n_frames);
+    if (s != DC_OK) return s;
+    if (ctx->sticky != DC_OK) {
+        s = ctx->sticky;
+        ctx->sticky = DC_OK;
+        return s;
+    }
+    DeviceGuard g(ctx->device);
+    return note(ctx, run(ctx, frames, n_frames, params, (cudaStream_t)stream));
+}
+
+dc_status dc_complete_uniform(dc_ctx* ctx, const float* in, float* out, int n, int H, int W,
+                              const dc_params* params, void* stream)
+{
+    if (!ctx || n < 0 || (n > 0 && (!in || !out || H < 1 || W < 1))) return DC_ERR_INVALID_ARG;
+    std::vector<dc_frame> fr((size_t)n);
+    const size_t step = (size_t)H * (size_t)W;
+    for (int i = 0; i < n; ++i) fr[(size_t)i] = dc_frame{in + i * step, out + i * step, H, W, W, W};
+    // packed frames of one size: the overlap check reduces to the two spans
+    if (n > 0 && overlap(in, step * n * sizeof(float), out, step * n * sizeof(float)))
+        return DC_ERR_INVALID_ARG;
+    if (!params_ok(params)) return DC_ERR_INVALID_ARG;
+    if (ctx->sticky != DC_OK) {
+        dc_status s = ctx->sticky;
+        ctx->sticky = DC_OK;
+        return s;
+    }
+    if (((uintptr_t)in % sizeof(float)) != 0 || ((uintptr_t)out % sizeof(float)) != 0)
+        return DC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    return note(ctx, run(ctx, fr.data(), n, params, (cudaStream_t)stream));
+}
+
+dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, int n, int H, int W,
+                           const dc_params* params, void* stream)
+{
+    if (!ctx || n < 0 || (n > 0 && (!host_in || !host_out || H < 1 || W < 1)) || !params_ok(params))
+        return DC_ERR_INVALID_ARG;
+    if (n == 0) return DC_OK;
+    DeviceGuard g(ctx->device);
+    const size_t floats = (size_t)n * H * W;
+    dc_status s = grow(ctx, 0, 0, 0, floats);
+    if (s != DC_OK) return note(ctx, s);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(ctx->io_in, host_in, floats * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return note(ctx, DC_ERR_CUDA);
+    s = dc_complete_uniform(ctx, ctx->io_in, ctx->io_out, n, H, W, params, stream);
+    if (s != DC_OK) return s;
+    if (cudaMemcpyAsync(host_out, ctx->io_out, floats * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return note(ctx, DC_ERR_CUDA);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return note(ctx, DC_ERR_CUDA);
+    return DC_OK;
+}
+
+int dc_last_launch_count(const dc_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+dc_status dc_set_profiling(dc_ctx* ctx, int on)
+{
+    if (!ctx) return DC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (on && !ctx->prof_ev) {
+        ctx->prof_ev = new (std::nothrow) cudaEvent_t[3 * DC_PROFILE_CALLS]();
+        if (!ctx->prof_ev) return DC_ERR_OOM;
+        for (int i = 0; i < 3 * DC_PROFILE_CALLS; ++i)
+            if (cudaEventCreate(&ctx->prof_ev[i]) != cudaSuccess) { cudaGetLastError(); return DC_ERR_CUDA; }
+    }
+    ctx->profiling = on != 0;
+    ctx->prof_next = 0;
+    ctx->prof_count = 0;
+    return DC_OK;
+}
+
+dc_status dc_kernel_times(dc_ctx* ctx, float* ms, int max_calls, int* n_out)
+{
+    if (!ctx || !ms || max_calls < 0 || !n_out) return DC_ERR_INVALID_ARG;
+    *n_out = 0;
+    if (!ctx->prof_ev || ctx->prof_count == 0) return DC_OK;
+    DeviceGuard g(ctx->device);
+    const int n = ctx->prof_count < max_calls ? ctx->prof_count : max_calls;
+    int idx = (ctx->prof_next - n + DC_PROFILE_CALLS) % DC_PROFILE_CALLS;
+    for (int i = 0; i < n; ++i, idx = (idx + 1) % DC_PROFILE_CALLS) {
+        cudaEvent_t* ev = ctx->prof_ev + 3 * idx;
+        float a = 0.0f, b = 0.0f;
+        if (cudaEventSynchronize(ev[2]) != cudaSuccess || cudaEventElapsedTime(&a, ev[0], ev[1]) != cudaSuccess)
+            return DC_ERR_CUDA;
+        if (ctx->prof_has_b[idx] && cudaEventElapsedTime(&b, ev[1], ev[2]) != cudaSuccess) return DC_ERR_CUDA;
+        ms[2 * i] = a;
+        ms[2 * i + 1] = b;
+    }
+    *n_out = n;
+    ctx->prof_next = 0;
+    ctx->prof_count = 0;
+    return DC_OK;
+}
+
+dc_status dc_last_async_error(dc_ctx* ctx)
+{
+    if (!ctx) return DC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    dc_status s = ctx->sticky;
+    ctx->sticky = DC_OK;
+    if (cudaStreamSynchronize(ctx->last_stream) != cudaSuccess) s = DC_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) s = DC_ERR_CUDA;
+    return s;
+}
+
+const char* dc_status_str(dc_status s)
+{
+    switch (s) {
+    case DC_OK: return "DC_OK";
+    case DC_ERR_INVALID_ARG: return "DC_ERR_INVALID_ARG";
+    case DC_ERR_OOM: return "DC_ERR_OOM";
+    case DC_ERR_CUDA: return "DC_ERR_CUDA";
+    case DC_ERR_TIMEOUT: return "DC_ERR_TIMEOUT";
+    case DC_ERR_UNSUPPORTED: return "DC_ERR_UNSUPPORTED";
+    default: return "DC_ERR_UNKNOWN";
+    }
+}
+
+void dc_destroy(dc_ctx* ctx)
+{
+    if (!ctx) return;
+    {
+        DeviceGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        cudaFree(ctx->c);
+        cudaFree(ctx->top);
+        for (TableSlot& sl : ctx->slot) {
+            cudaFree(sl.d);
+            cudaFreeHost(sl.h);
+            if (sl.done) cudaEventDestroy(sl.done);
+        }
+        cudaFree(ctx->io_in);
+        cudaFree(ctx->io_out);
+        if (ctx->prof_ev) {
+            for (int i = 0; i < 3 * DC_PROFILE_CALLS; ++i)
+                if (ctx->prof_ev[i]) cudaEventDestroy(ctx->prof_ev[i]);
+            delete[] ctx->prof_ev;
+        }
+        cudaGetLastError();
+    }
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libdc (include/dc.h).
+
+Functions carry the C names and only marshal arguments: every step of the
+depth-completion chain runs in the CUDA kernels of ``lib/libdc.so``.  There is
+no CPU fallback: if the library is missing or no GPU is present, calls raise.
+
+PyTorch is used by callers only for device memory and streams; tensors are
+passed as raw device pointers (``tensor.data_ptr()``) and streams as
+``torch.cuda.Stream.cuda_stream`` integers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "lib", "libdc.so")
+
+DC_OK = 0
+STATUS = {0: "DC_OK", 1: "DC_ERR_INVALID_ARG", 2: "DC_ERR_OOM", 3: "DC_ERR_CUDA",
+          4: "DC_ERR_TIMEOUT", 5: "DC_ERR_UNSUPPORTED"}
+KERNELS = {"diamond5": 0, "full5": 1, "cross5": 2, "full3": 3, "circle5": 4, "full7": 5}
+BLURS = {"none": 0, "gauss": 1, "bilateral": 2}
+STOPS = {"full": 0, "invert": 1, "dilate": 2, "close": 3, "fill7": 4, "extend": 5,
+         "fill_large": 6, "median": 7, "blur": 8}
+
+
+class DcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+class dc_params(ctypes.Structure):
+    _fields_ = [
+        ("first_kernel", ctypes.c_int),
+        ("large_fill", ctypes.c_int),
+        ("median", ctypes.c_int),
+        ("blur", ctypes.c_int),
+        ("sigma_space", ctypes.c_float),
+        ("sigma_color", ctypes.c_float),
+        ("extend_top", ctypes.c_int),
+        ("extend_rows", ctypes.c_int),
+        ("large_fill_on", ctypes.c_int),
+        ("stop_after", ctypes.c_int),
+    ]
+
+
+class dc_frame(ctypes.Structure):
+    _fields_ = [
+        ("in_", ctypes.c_void_p),
+        ("out", ctypes.c_void_p),
+        ("H", ctypes.c_int),
+        ("W", ctypes.c_int),
+        ("in_pitch", ctypes.c_int),
+        ("out_pitch", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+# (name, restype, argtypes) for every symbol include/dc.h declares
+SIGNATURES = [
+    ("dc_params_default", ctypes.c_int, [ctypes.POINTER(dc_params)]),
+    ("dc_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_size_t]),
+    ("dc_complete", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dc_frame), ctypes.c_int,
+                                   ctypes.POINTER(dc_params), ctypes.c_void_p]),
+    ("dc_complete_uniform", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(dc_params), ctypes.c_void_p]),
+    ("dc_complete_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(dc_params), ctypes.c_void_p]),
+    ("dc_reserve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("dc_last_launch_count", ctypes.c_int, [ctypes.c_void_p]),
+    ("dc_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("dc_kernel_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int)]),
+    ("dc_last_async_error", ctypes.c_int, [ctypes.c_void_p]),
+    ("dc_status_str", ctypes.c_char_p, [ctypes.c_int]),
+    ("dc_destroy", None, [ctypes.c_void_p]),
+]
+
+
+def load(path: str = LIB_PATH):
+    """Load libdc.so (built by ``paper_1802_00036_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libdc.so not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != DC_OK:
+        raise DcError(status, what)
+
+
+def params(first_kernel="diamond5", large_fill=31, median=True, blur="gauss", sigma_space=1.5,
+           sigma_color=0.5, extend_top=True, extend_rows=-1, large_fill_on=True,
+           stop_after="full") -> dc_params:
+    """dc_params from keywords; defaults are the paper's final design."""
+    p = dc_params()
+    _check(load().dc_params_default(ctypes.byref(p)), "dc_params_default")
+    p.first_kernel = KERNELS[first_kernel] if isinstance(first_kernel, str) else int(first_kernel)
+    p.large_fill = int(large_fill)
+    p.median = int(bool(median))
+    p.blur = BLURS[blur] if isinstance(blur, str) else int(blur)
+    p.sigma_space = float(sigma_space)
+    p.sigma_color = float(sigma_color)
+    p.extend_top = int(bool(extend_top))
+    p.extend_rows = int(extend_rows)
+    p.large_fill_on = int(bool(large_fill_on))
+    p.stop_after = STOPS[stop_after] if isinstance(stop_after, str) else int(stop_after)
+    return p
+
+
+def dc_params_default() -> dc_params:
+    p = dc_params()
+    _check(load().dc_params_default(ctypes.byref(p)), "dc_params_default")
+    return p
+
+
+def dc_create(device: int = 0, scratch_budget_bytes: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().dc_create(ctypes.byref(h), int(device), int(scratch_budget_bytes)), "dc_create")
+    return h
+
+
+def dc_destroy(ctx) -> None:
+    if ctx:
+        load().dc_destroy(ctx)
+
+
+def dc_complete(ctx, frames, p: dc_params, stream: int = 0) -> None:
+    """frames: sequence of (in_ptr, out_ptr, H, W, in_pitch, out_pitch)."""
+    arr = (dc_frame * max(1, len(frames)))()
+    for i, (a, b, H, W, ip, op) in enumerate(frames):
+        arr[i] = dc_frame(a, b, H, W, ip, op)
+    _check(load().dc_complete(ctx, arr, len(frames), ctypes.byref(p), ctypes.c_void_p(stream)),
+           "dc_complete")
+
+
+def dc_complete_uniform(ctx, in_ptr: int, out_ptr: int, n: int, H: int, W: int, p: dc_params,
+                        stream: int = 0) -> None:
+    _check(load().dc_complete_uniform(ctx, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), n, H, W,
+                                      ctypes.byref(p), ctypes.c_void_p(stream)), "dc_complete_uniform")
+
+
+def dc_complete_host(ctx, host_in: int, host_out: int, n: int, H: int, W: int, p: dc_params,
+                     stream: int = 0) -> None:
+    _check(load().dc_complete_host(ctx, ctypes.c_void_p(host_in), ctypes.c_void_p(host_out), n, H, W,
+                                   ctypes.byref(p), ctypes.c_void_p(stream)), "dc_complete_host")
+
+
+def dc_reserve(ctx, n_frames: int, H: int, W: int) -> None:
+    _check(load().dc_reserve(ctx, n_frames, H, W), "dc_reserve")
+
+
+def dc_last_launch_count(ctx) -> int:
+    return int(load().dc_last_launch_count(ctx))
+
+
+DC_PROFILE_CALLS = 4096
+
+
+def dc_set_profiling(ctx, on: bool) -> None:
+    _check(load().dc_set_profiling(ctx, int(bool(on))), "dc_set_profiling")
+
+
+def dc_kernel_times(ctx, max_calls: int = DC_PROFILE_CALLS):
+    """[(stage_a_ms, stage_b_ms), ...] for the last profiled calls, oldest first."""
+    buf = (ctypes.c_float * (2 * max(1, max_calls)))()
+    n = ctypes.c_int()
+    _check(load().dc_kernel_times(ctx, buf, int(max_calls), ctypes.byref(n)), "dc_kernel_times")
+    return [(buf[2 * i], buf[2 * i + 1]) for i in range(n.value)]
+
+
+def dc_last_async_error(ctx) -> int:
+    return int(load().dc_last_async_error(ctx))
+
+
+def dc_status_str(s: int) -> str:
+    return load().dc_status_str(int(s)).decode()
+
+
+class Context:
+    """Owns one dc_ctx; helpers take torch CUDA tensors."""
+
+    def __init__(self, device: int = 0, scratch_budget_bytes: int = 0):
+        self.device = device
+        self.h = dc_create(device, scratch_budget_bytes)
+
+    def close(self):
+        if self.h:
+            dc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream(stream) -> int:
+        if stream is None:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        return int(stream) if not hasattr(stream, "cuda_stream") else stream.cuda_stream
+
+    def complete(self, inp, out=None, p: dc_params | None = None, stream=None):
+        """inp: (n, H, W) or (H, W) float32 CUDA tensor, contiguous."""
+        import torch
+        if inp.dtype != torch.float32 or not inp.is_cuda or not inp.is_contiguous():
+            raise ValueError("expected a contiguous float32 CUDA tensor")
+        x = inp if inp.dim() == 3 else inp.unsqueeze(0)
+        if out is None:
+            out = torch.empty_like(inp)
+        y = out if out.dim() == 3 else out.unsqueeze(0)
+        dc_complete_uniform(self.h, x.data_ptr(), y.data_ptr(), x.shape[0], x.shape[1], x.shape[2],
+                            p if p is not None else params(), self._stream(stream))
+        return out
+
+    def complete_frames(self, pairs, p: dc_params | None = None, stream=None):
+        """pairs: list of (in, out) 2-D float32 CUDA tensors of any sizes (row-major,
+        unit column stride); all frames run in one call."""
+        fr = []
+        for a, b in pairs:
+            fr.append((a.data_ptr(), b.data_ptr(), a.shape[0], a.shape[1], a.stride(0), b.stride(0)))
+        dc_complete(self.h, fr, p if p is not None else params(), self._stream(stream))
+
+    def launches(self) -> int:
+        return dc_last_launch_count(self.h)

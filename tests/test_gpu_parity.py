@@ -1,0 +1,228 @@
+"""GPU (libdc, sm_103a) against the CPU oracle, element by element.
+
+Bar (arXiv 1802.00036, Section IV): bit-exact through the step-7 median --
+steps 1-7a are selections and one float32 subtraction -- and within 1e-4 m
+after the blur and the final inversion.  Every case calls the C-ABI through
+the ctypes binding.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_00036_gb300 import synth
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL_BLUR_M = 1e-4          # absolute, metres, after the Gaussian / bilateral
+EXACT_STOPS = ["invert", "dilate", "close", "fill7", "extend", "fill_large", "median"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1802_00036_gb300 import build, dc
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    c = dc.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_run(ctx, frames, **kw):
+    from paper_1802_00036_gb300 import dc
+    x = torch.from_numpy(np.ascontiguousarray(frames, dtype=np.float32)).cuda()
+    y = torch.full_like(x, -7.0)
+    ctx.complete(x, y, dc.params(**kw))
+    torch.cuda.synchronize()
+    assert ctx.launches() >= 1
+    return y.cpu().numpy()
+
+
+def compare(got, want, stop, what=""):
+    if stop in ("full", "blur"):
+        err = np.abs(got.astype(np.float64) - want.astype(np.float64))
+        assert err.max() <= TOL_BLUR_M, f"{what} max err {err.max()} at {np.unravel_index(err.argmax(), err.shape)}"
+    else:
+        bad = np.argwhere(got.view(np.uint32) != want.view(np.uint32))
+        assert len(bad) == 0, f"{what} {len(bad)} mismatches, first {bad[:5].tolist()}"
+
+
+SMALL = synth.FrameSpec(96, 200, 16, 0.05, 2.0, 80.0)
+
+
+@pytest.mark.parametrize("stop", EXACT_STOPS + ["blur", "full"])
+def test_every_stop_small_frames(ctx, stop):
+    frames = np.stack([synth.make_frame(SMALL, 500 + i) for i in range(3)])
+    got = gpu_run(ctx, frames, stop_after=stop)
+    for i in range(3):
+        compare(got[i], oracle.complete(frames[i], stop_after=stop), stop, f"frame {i}")
+
+
+@pytest.mark.parametrize("shape", ["diamond5", "full5", "cross5", "full3", "circle5", "full7"])
+@pytest.mark.parametrize("stop", ["dilate", "fill7", "median"])
+def test_first_kernel_shapes(ctx, shape, stop):
+    f = synth.make_frame(SMALL, 77)
+    compare(gpu_run(ctx, f[None], first_kernel=shape, stop_after=stop)[0],
+            oracle.complete(f, first_kernel=shape, stop_after=stop), stop, shape)
+
+
+@pytest.mark.parametrize("large", [3, 15, 31, 51, 63])
+def test_large_fill_sizes(ctx, large):
+    f = synth.random_sparse(120, 170, 0.004, 31 + large)
+    for stop in ("fill_large", "median", "full"):
+        compare(gpu_run(ctx, f[None], large_fill=large, stop_after=stop)[0],
+                oracle.complete(f, large_fill=large, stop_after=stop), stop, f"large {large}")
+
+
+@pytest.mark.parametrize("blur", ["gauss", "bilateral", "none"])
+@pytest.mark.parametrize("median", [True, False])
+def test_blur_variants(ctx, blur, median):
+    f = synth.make_frame(synth.FrameSpec(150, 260, 32, 0.06, 1.0, 90.0), 11)
+    for stop in ("blur", "full"):
+        compare(gpu_run(ctx, f[None], blur=blur, median=median, stop_after=stop)[0],
+                oracle.complete(f, blur=blur, median=median, stop_after=stop), stop, blur)
+
+
+@pytest.mark.parametrize("variant", [dict(extend_top=False), dict(large_fill_on=False),
+                                     dict(extend_rows=5), dict(extend_rows=0),
+                                     dict(extend_top=False, large_fill_on=False)])
+def test_point_cloud_variants(ctx, variant):
+    f = synth.make_frame(SMALL, 123)
+    for stop in ("median", "full"):
+        compare(gpu_run(ctx, f[None], stop_after=stop, **variant)[0],
+                oracle.complete(f, stop_after=stop, **variant), stop, str(variant))
+
+
+@pytest.mark.parametrize("hw", [(1, 1), (1, 37), (41, 1), (2, 2), (3, 5), (7, 64), (33, 65),
+                                (64, 128), (65, 129), (5, 300)])
+def test_edge_shapes(ctx, hw):
+    f = synth.random_sparse(*hw, 0.2, hw[0] * 1000 + hw[1])
+    for stop in ("fill7", "median", "full"):
+        compare(gpu_run(ctx, f[None], stop_after=stop)[0], oracle.complete(f, stop_after=stop),
+                stop, str(hw))
+
+
+@pytest.mark.parametrize("fill", ["empty", "dense", "top_only", "one_point"])
+def test_degenerate_frames(ctx, fill):
+    H, W = 70, 140
+    f = np.zeros((H, W), np.float32)
+    if fill == "dense":
+        f = synth.random_sparse(H, W, 1.0, 5, 1.0, 80.0)
+    elif fill == "top_only":
+        f[0, :] = 12.5
+    elif fill == "one_point":
+        f[50, 70] = 33.0
+    for stop in ("fill7", "median", "full"):
+        compare(gpu_run(ctx, f[None], stop_after=stop)[0], oracle.complete(f, stop_after=stop),
+                stop, fill)
+
+
+def test_out_of_range_inputs_follow_the_formulas(ctx):
+    # depths >= 100 m invert to values <= 0 (empty); tiny depths are empty
+    f = synth.random_sparse(40, 90, 0.3, 8, 0.0, 130.0)
+    f[5, 5] = 100.0
+    f[6, 6] = 0.05
+    for stop in ("fill7", "median", "full"):
+        compare(gpu_run(ctx, f[None], stop_after=stop)[0], oracle.complete(f, stop_after=stop),
+                stop, "range")
+
+
+def test_full_size_frame_352x1216(ctx):
+    f = synth.make_frame(synth.ONE_FRAME, synth.frame_seed(0, 0))
+    for stop in ("fill7", "median", "full"):
+        compare(gpu_run(ctx, f[None], stop_after=stop)[0], oracle.complete(f, stop_after=stop),
+                stop, "352x1216")
+
+
+def test_batched_375x1242_sampled_and_batch_independent(ctx):
+    # the 64-frame batched workload; three frames checked against the oracle,
+    # every frame checked against its own single-frame run
+    n = 64
+    frames = synth.make_batch(n, synth.UNIFORM_375, config=1, density_range=(0.04, 0.06))
+    for stop in ("median", "full"):
+        got = gpu_run(ctx, frames, stop_after=stop)
+        for i in (0, 31, 63):
+            compare(got[i], oracle.complete(frames[i], stop_after=stop), stop, f"frame {i}")
+        for i in range(0, n, 9):
+            alone = gpu_run(ctx, frames[i:i + 1], stop_after=stop)[0]
+            assert np.array_equal(alone.view(np.uint32), got[i].view(np.uint32)), i
+
+
+def test_bilateral_full_size(ctx):
+    f = synth.make_frame(synth.UNIFORM_375, synth.frame_seed(1, 3))
+    compare(gpu_run(ctx, f[None], blur="bilateral")[0], oracle.complete(f, blur="bilateral"),
+            "full", "bilateral")
+
+
+def test_uneven_batch_one_call(ctx):
+    from paper_1802_00036_gb300 import dc
+    specs = [synth.MIX[i % 4] for i in range(8)]
+    host = [synth.make_frame(s, synth.frame_seed(2, i)) for i, s in enumerate(specs)]
+    ins = [torch.from_numpy(h).cuda() for h in host]
+    # the third frame's output lives in a wider buffer (pitch > W)
+    outs = []
+    for i, h in enumerate(host):
+        buf = torch.full((h.shape[0], h.shape[1] + (24 if i == 2 else 0)), -3.0, device="cuda")
+        outs.append(buf[:, :h.shape[1]])
+    for stop in ("median", "full"):
+        ctx.complete_frames(list(zip(ins, outs)), dc.params(stop_after=stop))
+        torch.cuda.synchronize()
+        for i in (0, 1, 2, 3, 6):
+            compare(outs[i].cpu().numpy(), oracle.complete(host[i], stop_after=stop), stop, f"mix {i}")
+
+
+def test_host_buffers_entry_point(ctx):
+    from paper_1802_00036_gb300 import dc
+    frames = np.stack([synth.make_frame(SMALL, 900 + i) for i in range(4)])
+    out = np.full_like(frames, -1.0)
+    dc.dc_complete_host(ctx.h, frames.ctypes.data, out.ctypes.data, 4, SMALL.H, SMALL.W, dc.params())
+    dev = gpu_run(ctx, frames)
+    assert np.array_equal(out.view(np.uint32), dev.view(np.uint32))
+
+
+def test_invalid_arguments_are_refused(ctx):
+    from paper_1802_00036_gb300 import dc
+    x = torch.zeros((2, 16, 16), device="cuda")
+    y = torch.zeros_like(x)
+    p = dc.params()
+    bad = [
+        lambda: dc.dc_complete_uniform(ctx.h, 0, y.data_ptr(), 2, 16, 16, p),
+        lambda: dc.dc_complete_uniform(ctx.h, x.data_ptr(), y.data_ptr(), 2, 0, 16, p),
+        lambda: dc.dc_complete_uniform(ctx.h, x.data_ptr(), x.data_ptr(), 2, 16, 16, p),
+        lambda: dc.dc_complete_uniform(ctx.h, x.data_ptr(), x.data_ptr() + 1024, 2, 16, 16, p),
+        lambda: dc.dc_complete(ctx.h, [(x.data_ptr(), y.data_ptr(), 16, 16, 8, 16)], p),
+        lambda: dc.dc_complete_uniform(ctx.h, x.data_ptr(), y.data_ptr(), 2, 16, 16,
+                                       dc.params(large_fill=30)),
+        lambda: dc.dc_complete_uniform(ctx.h, x.data_ptr(), y.data_ptr(), 2, 16, 16,
+                                       dc.params(first_kernel=9)),
+        lambda: dc.dc_complete_uniform(ctx.h, x.data_ptr(), y.data_ptr(), 2, 16, 16,
+                                       dc.params(blur="bilateral", sigma_color=0.0)),
+    ]
+    for i, call in enumerate(bad):
+        with pytest.raises(dc.DcError) as e:
+            call()
+        assert e.value.status == 1, i
+    # nothing was queued and the context still works
+    assert dc.dc_last_async_error(ctx.h) == 0
+    dc.dc_complete_uniform(ctx.h, x.data_ptr(), y.data_ptr(), 2, 16, 16, p)
+    torch.cuda.synchronize()
+
+
+def test_zero_frames_is_a_no_op(ctx):
+    from paper_1802_00036_gb300 import dc
+    dc.dc_complete(ctx.h, [], dc.params())
+    assert ctx.launches() == 0
+
+
+def test_scratch_budget_is_enforced(ctx):
+    from paper_1802_00036_gb300 import dc
+    small = dc.Context(0, scratch_budget_bytes=64 * 1024)
+    try:
+        x = torch.zeros((4, 352, 1216), device="cuda")
+        with pytest.raises(dc.DcError) as e:
+            small.complete(x)
+        assert e.value.status == 2
+    finally:
+        small.close()
