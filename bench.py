@@ -174,10 +174,10 @@ def oracle_throughput(frames, threads: int, rounds: int = 1):
 
 def cpu_baseline(frames_pool):
     cores = os.cpu_count() or 1
-    sample = [frames_pool[i % len(frames_pool)] for i in range(2 * cores)]
+    sample = [frames_pool[i % len(frames_pool)] for i in range(8 * cores)]
     fps, dt = oracle_throughput(sample, cores)
     return {"value": round(fps, 3), "unit": "frames/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(sample)} frames of 352x1216 (2 per core) through the single-threaded C oracle, "
+            "sample": f"{len(sample)} frames of 352x1216 (8 per core) through the single-threaded C oracle, "
                       f"one frame per thread on {cores} threads; {dt:.1f} s wall",
             "context": PAPER_CONTEXT}
 
