@@ -165,6 +165,39 @@ const char* dc_status_str(dc_status s);
 /* Free the context and its scratch.  Waits for its queued work. */
 void dc_destroy(dc_ctx* ctx);
 
+/* ---- Allocation-free entry point (the paper has no counterpart) ----------
+ *
+ * For callers that must not allocate device memory at run time: code that
+ * runs under a fixed memory plan (safety-certified or real-time stacks that
+ * forbid cudaMalloc after start-up, because it can block, fragment memory or
+ * fail unpredictably), plug-ins that only receive buffers from a host
+ * framework, and allocators that forbid foreign allocations.  It takes no
+ * context: the scratch it needs lives in one fixed array inside the library
+ * (DC_NOALLOC_SCRATCH_BYTES of device memory that every GPU which loads the
+ * library keeps until the process exits).
+ *
+ * Same chain and results as dc_complete_uniform on `n` packed frames of
+ * H x W (device pointers, pitch W, `in` and `out` must not overlap),
+ * asynchronous on `stream`.  Limits: n <= DC_NOALLOC_MAX_FRAMES,
+ * n * H * roundup(W, 32) <= DC_NOALLOC_MAX_PIXELS and
+ * n * roundup(W, 32) <= DC_NOALLOC_MAX_COLUMNS; larger requests return
+ * DC_ERR_UNSUPPORTED and queue nothing (bad pointers, sizes, overlap or
+ * params return DC_ERR_INVALID_ARG as elsewhere).  It calls no cudaMalloc, cudaFree or
+ * other allocating routine; it only launches kernels.
+ *
+ * The first call on each device looks up the array's device address for that
+ * device (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Every call, on every stream, shares the one array and leaves the
+ * last call's data in it; calls whose device work overlaps in time (other
+ * streams, other host threads) race and give wrong results.  Order them on
+ * one stream or with events. */
+#define DC_NOALLOC_MAX_FRAMES 64
+#define DC_NOALLOC_MAX_PIXELS (1 << 21)
+#define DC_NOALLOC_MAX_COLUMNS 131072
+#define DC_NOALLOC_SCRATCH_BYTES (4 * DC_NOALLOC_MAX_PIXELS + 4 * DC_NOALLOC_MAX_COLUMNS + 65536)
+dc_status dc_complete_noalloc(const float* in, float* out, int n, int H, int W,
+                              const dc_params* params, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,166 @@
+// noalloc.cu -- dc_complete_noalloc: the chain without any run-time device
+// allocation.  The paper has no counterpart; see include/dc.h for who needs it.
+//
+// All scratch (frame table, per-column tops, step-4 map) sits in one
+// file-scope device array.  Host code must not use the array's name as a
+// pointer: here it is only a host-side stand-in, and a kernel handed it would
+// fault or read the wrong memory.  The device address is looked up once per
+// device with cudaGetSymbolAddress, with that device current, and cached.
+#include "../../include/dc.h"
+#include "common.cuh"
+
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+
+using namespace dcgb;
+
+namespace {
+
+constexpr size_t kTableBytes = 65536;
+constexpr size_t kTopBytes = 4u * DC_NOALLOC_MAX_COLUMNS;
+constexpr size_t kMapBytes = 4u * DC_NOALLOC_MAX_PIXELS;
+static_assert(kTableBytes + kTopBytes + kMapBytes == DC_NOALLOC_SCRATCH_BYTES, "layout");
+static_assert(DC_NOALLOC_MAX_FRAMES * sizeof(FrameDesc) <= kTableBytes, "frame table");
+
+// Layout: [frame table | tops | step-4 maps]; each part 256-byte aligned.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[DC_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned char* g_dev_ptr[kMaxDevices] = {};  // device address of the array, per device
+int g_sm_count[kMaxDevices] = {};
+
+// Per-device set-up; must run with `dev` current.
+dc_status setup(int dev, unsigned char** ptr, int* sms)
+{
+    if (dev < 0 || dev >= kMaxDevices) return DC_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_dev_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return DC_ERR_CUDA;
+        }
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return DC_ERR_CUDA;
+        }
+        g_sm_count[dev] = n;
+        g_dev_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *ptr = g_dev_ptr[dev];
+    *sms = g_sm_count[dev];
+    return DC_OK;
+}
+
+// Writes the frame table for n packed frames and resets the tops: the only
+// preparation the two stage kernels need, done on the device so that the
+// call copies nothing from the host.
+__global__ void noalloc_prepare(FrameDesc* table, int* top, float* cmap, const float* in, float* out,
+                                int n, int H, int W, int c_pitch, int tiles_x_a, int tiles_a,
+                                int tiles_x_b, int tiles_b, int top_ints)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = tid; i < n; i += stride) {
+        FrameDesc d;
+        d.in = in + (size_t)i * H * W;
+        d.out = out + (size_t)i * H * W;
+        d.c = cmap ? cmap + (size_t)i * H * c_pitch : nullptr;
+        d.top = top ? top + (size_t)i * c_pitch : nullptr;
+        d.H = H;
+        d.W = W;
+        d.in_pitch = W;
+        d.out_pitch = W;
+        d.c_pitch = c_pitch;
+        d.tiles_x_a = tiles_x_a;
+        d.base_a = i * tiles_a;
+        d.tiles_x_b = tiles_x_b;
+        d.base_b = i * tiles_b;
+        table[i] = d;
+    }
+    if (top)
+        for (int i = tid; i < top_ints; i += stride) top[i] = kNoTop;
+}
+
+bool params_valid(const dc_params* p)
+{
+    if (!p) return false;
+    if (p->first_kernel < DC_K_DIAMOND5 || p->first_kernel > DC_K_FULL7) return false;
+    if (p->large_fill_on && (p->large_fill < 1 || p->large_fill > kMaxLargeFill || (p->large_fill % 2) == 0))
+        return false;
+    if (p->blur < DC_BLUR_NONE || p->blur > DC_BLUR_BILATERAL) return false;
+    if (p->blur == DC_BLUR_BILATERAL && (!(p->sigma_space > 0.0f) || !(p->sigma_color > 0.0f) ||
+                                         !std::isfinite(p->sigma_space) || !std::isfinite(p->sigma_color)))
+        return false;
+    return p->stop_after >= DC_STOP_FULL && p->stop_after <= DC_STOP_BLUR;
+}
+
+}  // namespace
+
+extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int H, int W,
+                                         const dc_params* params, void* stream)
+{
+    if (n < 0 || !params_valid(params)) return DC_ERR_INVALID_ARG;
+    if (n == 0) return DC_OK;
+    if (!in || !out || H < 1 || W < 1) return DC_ERR_INVALID_ARG;
+    if (((uintptr_t)in % sizeof(float)) != 0 || ((uintptr_t)out % sizeof(float)) != 0)
+        return DC_ERR_INVALID_ARG;
+    const size_t span = (size_t)n * H * W * sizeof(float);
+    if ((uintptr_t)in < (uintptr_t)out + span && (uintptr_t)out < (uintptr_t)in + span)
+        return DC_ERR_INVALID_ARG;
+    const size_t c_pitch = ((size_t)W + 31) / 32 * 32;
+    if (n > DC_NOALLOC_MAX_FRAMES || (size_t)n * H * c_pitch > (size_t)DC_NOALLOC_MAX_PIXELS ||
+        (size_t)n * c_pitch > (size_t)DC_NOALLOC_MAX_COLUMNS)
+        return DC_ERR_UNSUPPORTED;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return DC_ERR_CUDA; }
+    unsigned char* base = nullptr;
+    int sms = 0;
+    dc_status s = setup(dev, &base, &sms);
+    if (s != DC_OK) return s;
+
+    FrameDesc* table = reinterpret_cast<FrameDesc*>(base);
+    int* top = reinterpret_cast<int*>(base + kTableBytes);
+    float* cmap = reinterpret_cast<float*>(base + kTableBytes + kTopBytes);
+    const bool need_b = (params->stop_after == DC_STOP_FULL || params->stop_after >= DC_STOP_EXTEND);
+    const int tiles_x_a = (W + kTileAW - 1) / kTileAW;
+    const int tiles_a = tiles_x_a * ((H + kTileAH - 1) / kTileAH);
+    const int tiles_x_b = (W + kTileBW - 1) / kTileBW;
+    const int tiles_b = tiles_x_b * ((H + kTileBH - 1) / kTileBH);
+    if ((long long)tiles_a * n > INT32_MAX / 2 || (long long)tiles_b * n > INT32_MAX / 2)
+        return DC_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    const int top_ints = need_b ? (int)((size_t)n * c_pitch) : 0;
+    const int threads = 256;
+    int blocks = (top_ints > n ? top_ints : n) / threads + 1;
+    if (blocks > 1024) blocks = 1024;
+    noalloc_prepare<<<blocks, threads, 0, st>>>(table, need_b ? top : nullptr, need_b ? cmap : nullptr,
+                                                 in, out, n, H, W, (int)c_pitch, tiles_x_a, tiles_a,
+                                                 tiles_x_b, tiles_b, top_ints);
+    if (cudaGetLastError() != cudaSuccess) return DC_ERR_CUDA;
+
+    const int stop_a = need_b ? kStopFull : params->stop_after;
+    if (launch_stage_a(table, n, tiles_a * n, params->first_kernel, stop_a, sms, st) != cudaSuccess)
+        return DC_ERR_CUDA;
+    if (need_b) {
+        StageBParams bp{};
+        bp.large_fill_on = params->large_fill_on ? 1 : 0;
+        bp.large_radius = params->large_fill_on ? params->large_fill / 2 : 0;
+        bp.median = params->median ? 1 : 0;
+        bp.blur = params->blur;
+        bp.extend_top = params->extend_top ? 1 : 0;
+        bp.extend_rows = params->extend_rows;
+        bp.stop = params->stop_after;
+        const double ss = params->blur == DC_BLUR_BILATERAL ? params->sigma_space : 1.0;
+        const double sc = params->blur == DC_BLUR_BILATERAL ? params->sigma_color : 1.0;
+        for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));
+        bp.inv_2sc2 = (float)(1.0 / (2.0 * sc * sc));
+        if (launch_stage_b(table, n, tiles_b * n, bp, sms, st) != cudaSuccess) return DC_ERR_CUDA;
+    }
+    return DC_OK;
+}

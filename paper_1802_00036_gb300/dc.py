@@ -79,6 +79,8 @@ SIGNATURES = [
     ("dc_last_async_error", ctypes.c_int, [ctypes.c_void_p]),
     ("dc_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("dc_destroy", None, [ctypes.c_void_p]),
+    ("dc_complete_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.POINTER(dc_params), ctypes.c_void_p]),
 ]
 
 
@@ -157,6 +159,15 @@ def dc_complete_host(ctx, host_in: int, host_out: int, n: int, H: int, W: int, p
                      stream: int = 0) -> None:
     _check(load().dc_complete_host(ctx, ctypes.c_void_p(host_in), ctypes.c_void_p(host_out), n, H, W,
                                    ctypes.byref(p), ctypes.c_void_p(stream)), "dc_complete_host")
+
+
+def dc_complete_noalloc(in_ptr: int, out_ptr: int, n: int, H: int, W: int, p: dc_params,
+                        stream: int = 0) -> None:
+    """Context-free call that allocates no device memory: its scratch is a
+    fixed array inside the library, shared by every call (see include/dc.h
+    for the limits and for why overlapping calls race)."""
+    _check(load().dc_complete_noalloc(ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), n, H, W,
+                                      ctypes.byref(p), ctypes.c_void_p(stream)), "dc_complete_noalloc")
 
 
 def dc_reserve(ctx, n_frames: int, H: int, W: int) -> None:
