@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--blur", default="gauss", choices=["gauss", "bilateral"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed batched steps only (no per-frame, e2e or CPU legs): for profiling")
     return ap.parse_args()
 
 
@@ -269,6 +271,13 @@ def run_gpu(args, world, rank, local):
     # per-kernel averages over the timed region
     a_ms = statistics.mean(k[0] for k in ktimes) if ktimes else None
     b_ms = statistics.mean(k[1] for k in ktimes) if ktimes else None
+
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": round(fps, 1), "unit": "frames/s", "quick": True,
+                              "kernels_ms": {"stage_a": a_ms, "stage_b": b_ms}}), flush=True)
+        ctx.close()
+        return
 
     # per-frame GPU form: one call per frame
     pf_steps = max(2, min(args.steps // 8, 50))

@@ -26,9 +26,9 @@ constexpr int kNoTop = 0x7F7F7F7F;
 constexpr int kTileAH = 32;
 constexpr int kTileAW = 64;
 constexpr int kThreadsA = 256;
-// Stage B output tile.
-constexpr int kTileBH = 32;
-constexpr int kTileBW = 64;
+// Stage B output tile (median blocks of 2 x 8 over the tile + 2 ring).
+constexpr int kTileBH = 60;
+constexpr int kTileBW = 60;
 constexpr int kThreadsB = 256;
 
 // Largest step-6 square side the kernels accept.
@@ -86,10 +86,11 @@ __device__ __forceinline__ int find_frame(const FrameDesc* __restrict__ d, int n
 }
 
 // Launchers (stage_a.cu, stage_b.cu).  Return cudaGetLastError().
+// `worklist` holds 1 + (stage B tiles) ints: a count that stage A zeroes,
+// then the stage-B tiles that need step 6.
 cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_tiles,
-                           int shape, int stop, int sm_count, cudaStream_t stream);
+                           int shape, int stop, int* worklist, int sm_count, cudaStream_t stream);
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,
-                           const StageBParams& p, int sm_count, cudaStream_t stream);
-size_t stage_b_smem_bytes(int large_radius);
+                           const StageBParams& p, int* worklist, int sm_count, cudaStream_t stream);
 
 }  // namespace dcgb

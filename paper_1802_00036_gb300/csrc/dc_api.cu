@@ -32,6 +32,8 @@ struct dc_ctx {
     size_t c_cap = 0;         // floats
     int* top = nullptr;       // per-column tops, all frames
     size_t top_cap = 0;       // ints
+    int* work = nullptr;      // stage-B worklist: count, then tile indices
+    size_t work_cap = 0;      // ints
     TableSlot slot[kSlots];
     int frames_cap = 0;       // descriptors per slot
     unsigned long long calls = 0;
@@ -70,9 +72,9 @@ struct DeviceGuard {
 
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
-size_t scratch_bytes(size_t c_floats, size_t top_ints, int frames, size_t io_floats)
+size_t scratch_bytes(size_t c_floats, size_t top_ints, int frames, size_t io_floats, size_t work_ints)
 {
-    return c_floats * sizeof(float) + top_ints * sizeof(int) +
+    return c_floats * sizeof(float) + top_ints * sizeof(int) + work_ints * sizeof(int) +
            (size_t)kSlots * (size_t)frames * sizeof(FrameDesc) + 2 * io_floats * sizeof(float);
 }
 
@@ -96,16 +98,18 @@ bool overlap(const void* a, size_t na, const void* b, size_t nb)
     return a0 < b0 + nb && b0 < a0 + na;
 }
 
-dc_status grow(dc_ctx* ctx, size_t c_floats, size_t top_ints, int frames, size_t io_floats)
+dc_status grow(dc_ctx* ctx, size_t c_floats, size_t top_ints, int frames, size_t io_floats,
+               size_t work_ints = 0)
 {
     const bool need = c_floats > ctx->c_cap || top_ints > ctx->top_cap || frames > ctx->frames_cap ||
-                      io_floats > ctx->io_cap;
+                      io_floats > ctx->io_cap || work_ints > ctx->work_cap;
     if (!need) return DC_OK;
     const size_t nc = c_floats > ctx->c_cap ? c_floats : ctx->c_cap;
     const size_t nt = top_ints > ctx->top_cap ? top_ints : ctx->top_cap;
     const int nf = frames > ctx->frames_cap ? frames : ctx->frames_cap;
     const size_t ni = io_floats > ctx->io_cap ? io_floats : ctx->io_cap;
-    if (ctx->budget && scratch_bytes(nc, nt, nf, ni) > ctx->budget) return DC_ERR_OOM;
+    const size_t nw = work_ints > ctx->work_cap ? work_ints : ctx->work_cap;
+    if (ctx->budget && scratch_bytes(nc, nt, nf, ni, nw) > ctx->budget) return DC_ERR_OOM;
     // queued work may still use the old buffers
     if (cudaDeviceSynchronize() != cudaSuccess) return DC_ERR_CUDA;
     if (nc > ctx->c_cap) {
@@ -121,6 +125,13 @@ dc_status grow(dc_ctx* ctx, size_t c_floats, size_t top_ints, int frames, size_t
         ctx->top_cap = 0;
         if (cudaMalloc(&ctx->top, nt * sizeof(int)) != cudaSuccess) { cudaGetLastError(); return DC_ERR_OOM; }
         ctx->top_cap = nt;
+    }
+    if (nw > ctx->work_cap) {
+        cudaFree(ctx->work);
+        ctx->work = nullptr;
+        ctx->work_cap = 0;
+        if (cudaMalloc(&ctx->work, nw * sizeof(int)) != cudaSuccess) { cudaGetLastError(); return DC_ERR_OOM; }
+        ctx->work_cap = nw;
     }
     if (nf > ctx->frames_cap) {
         ctx->frames_cap = 0;
@@ -193,7 +204,8 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
     if (tiles_a > INT32_MAX / 2 || tiles_b > INT32_MAX / 2) return DC_ERR_UNSUPPORTED;
 
     const bool need_b = (p->stop_after == DC_STOP_FULL || p->stop_after >= DC_STOP_EXTEND);
-    dc_status s = grow(ctx, need_b ? c_off : 0, need_b ? top_off : 0, n, 0);
+    dc_status s = grow(ctx, need_b ? c_off : 0, need_b ? top_off : 0, n, 0,
+                       need_b ? (size_t)tiles_b + 1 : 0);
     if (s != DC_OK) return s;
     for (auto& d : desc) {
         d.c = need_b ? ctx->c + reinterpret_cast<size_t>(d.c) : nullptr;
@@ -224,7 +236,8 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         if (cudaEventRecord(ev[0], stream) != cudaSuccess) return DC_ERR_CUDA;
     }
     const int stop_a = need_b ? kStopFull : p->stop_after;
-    cudaError_t e = launch_stage_a(sl.d, n, (int)tiles_a, p->first_kernel, stop_a, ctx->sm_count, stream);
+    cudaError_t e = launch_stage_a(sl.d, n, (int)tiles_a, p->first_kernel, stop_a,
+                                   need_b ? ctx->work : nullptr, ctx->sm_count, stream);
     if (e != cudaSuccess) return DC_ERR_CUDA;
     ctx->last_launches = 1;
     if (ev && cudaEventRecord(ev[1], stream) != cudaSuccess) return DC_ERR_CUDA;
@@ -241,9 +254,10 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         const double sc = p->blur == DC_BLUR_BILATERAL ? p->sigma_color : 1.0;
         for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));
         bp.inv_2sc2 = (float)(1.0 / (2.0 * sc * sc));
-        e = launch_stage_b(sl.d, n, (int)tiles_b, bp, ctx->sm_count, stream);
+        e = launch_stage_b(sl.d, n, (int)tiles_b, bp, ctx->work, ctx->sm_count, stream);
         if (e != cudaSuccess) return DC_ERR_CUDA;
-        ctx->last_launches = 2;
+        // stage B is one kernel, plus the step-6 pass when step 6 can run
+        ctx->last_launches = (bp.large_fill_on && bp.stop != kStopExtend) ? 3 : 2;
     }
     if (ev && cudaEventRecord(ev[2], stream) != cudaSuccess) return DC_ERR_CUDA;
     if (cudaEventRecord(sl.done, stream) != cudaSuccess) return DC_ERR_CUDA;
@@ -332,8 +346,9 @@ dc_status dc_reserve(dc_ctx* ctx, int n_frames, int H, int W)
 {
     if (!ctx || n_frames < 0 || H < 1 || W < 1) return DC_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
+    const size_t tiles = (size_t)ceil_div(W, kTileBW) * (size_t)ceil_div(H, kTileBH) * (size_t)n_frames;
     return note(ctx, grow(ctx, frame_c_floats(H, W) * (size_t)n_frames,
-                          frame_top_ints(W) * (size_t)n_frames, n_frames, 0));
+                          frame_top_ints(W) * (size_t)n_frames, n_frames, 0, tiles + 1));
 }
 
 dc_status dc_complete(dc_ctx* ctx, const dc_frame* frames, int n_frames, const dc_params* params,
@@ -467,6 +482,7 @@ void dc_destroy(dc_ctx* ctx)
         cudaDeviceSynchronize();
         cudaFree(ctx->c);
         cudaFree(ctx->top);
+        cudaFree(ctx->work);
         for (TableSlot& sl : ctx->slot) {
             cudaFree(sl.d);
             cudaFreeHost(sl.h);

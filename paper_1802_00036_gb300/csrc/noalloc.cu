@@ -19,11 +19,12 @@ namespace {
 
 constexpr size_t kTableBytes = 65536;
 constexpr size_t kTopBytes = 4u * DC_NOALLOC_MAX_COLUMNS;
+constexpr size_t kWorkBytes = 4u * DC_NOALLOC_WORK_INTS;
 constexpr size_t kMapBytes = 4u * DC_NOALLOC_MAX_PIXELS;
-static_assert(kTableBytes + kTopBytes + kMapBytes == DC_NOALLOC_SCRATCH_BYTES, "layout");
+static_assert(kTableBytes + kTopBytes + kWorkBytes + kMapBytes == DC_NOALLOC_SCRATCH_BYTES, "layout");
 static_assert(DC_NOALLOC_MAX_FRAMES * sizeof(FrameDesc) <= kTableBytes, "frame table");
 
-// Layout: [frame table | tops | step-4 maps]; each part 256-byte aligned.
+// Layout: [frame table | tops | worklist | step-4 maps]; each part 256-byte aligned.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[DC_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
@@ -125,13 +126,14 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
 
     FrameDesc* table = reinterpret_cast<FrameDesc*>(base);
     int* top = reinterpret_cast<int*>(base + kTableBytes);
-    float* cmap = reinterpret_cast<float*>(base + kTableBytes + kTopBytes);
+    int* work = reinterpret_cast<int*>(base + kTableBytes + kTopBytes);
+    float* cmap = reinterpret_cast<float*>(base + kTableBytes + kTopBytes + kWorkBytes);
     const bool need_b = (params->stop_after == DC_STOP_FULL || params->stop_after >= DC_STOP_EXTEND);
     const int tiles_x_a = (W + kTileAW - 1) / kTileAW;
     const int tiles_a = tiles_x_a * ((H + kTileAH - 1) / kTileAH);
     const int tiles_x_b = (W + kTileBW - 1) / kTileBW;
     const int tiles_b = tiles_x_b * ((H + kTileBH - 1) / kTileBH);
-    if ((long long)tiles_a * n > INT32_MAX / 2 || (long long)tiles_b * n > INT32_MAX / 2)
+    if ((long long)tiles_a * n > INT32_MAX / 2 || (long long)tiles_b * n + 1 > DC_NOALLOC_WORK_INTS)
         return DC_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
 
@@ -145,7 +147,8 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     if (cudaGetLastError() != cudaSuccess) return DC_ERR_CUDA;
 
     const int stop_a = need_b ? kStopFull : params->stop_after;
-    if (launch_stage_a(table, n, tiles_a * n, params->first_kernel, stop_a, sms, st) != cudaSuccess)
+    if (launch_stage_a(table, n, tiles_a * n, params->first_kernel, stop_a, need_b ? work : nullptr, sms, st) !=
+        cudaSuccess)
         return DC_ERR_CUDA;
     if (need_b) {
         StageBParams bp{};
@@ -160,7 +163,7 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
         const double sc = params->blur == DC_BLUR_BILATERAL ? params->sigma_color : 1.0;
         for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));
         bp.inv_2sc2 = (float)(1.0 / (2.0 * sc * sc));
-        if (launch_stage_b(table, n, tiles_b * n, bp, sms, st) != cudaSuccess) return DC_ERR_CUDA;
+        if (launch_stage_b(table, n, tiles_b * n, bp, work, sms, st) != cudaSuccess) return DC_ERR_CUDA;
     }
     return DC_OK;
 }

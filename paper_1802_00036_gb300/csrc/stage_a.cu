@@ -42,8 +42,10 @@ __device__ __forceinline__ constexpr bool in_shape(int dy, int dx)
 
 template <int S>
 __global__ void __launch_bounds__(kThreadsA)
-stage_a_kernel(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles, int stop)
+stage_a_kernel(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles, int stop,
+               int* __restrict__ worklist)
 {
+    if (worklist && blockIdx.x == 0 && threadIdx.x == 0) worklist[0] = 0;
     constexpr int R1 = ShapeInfo<S>::r;
     constexpr int R = R1 + 2 + 2 + 3;
     constexpr int BH = kTileAH + 2 * R;
@@ -209,7 +211,7 @@ stage_a_kernel(const FrameDesc* __restrict__ frames, int n_frames, int total_til
 
 template <int S>
 cudaError_t launch_shape(const FrameDesc* d_frames, int n_frames, int total_tiles, int stop,
-                         int sm_count, cudaStream_t stream)
+                         int* worklist, int sm_count, cudaStream_t stream)
 {
     constexpr int R = ShapeInfo<S>::r + 7;
     const size_t smem = 2u * sizeof(float) * (kTileAH + 2 * R) * (kTileAW + 2 * R);
@@ -226,22 +228,22 @@ cudaError_t launch_shape(const FrameDesc* d_frames, int n_frames, int total_tile
     const int cap = sm_count * 8;
     if (grid > cap) grid = cap;
     if (grid < 1) return cudaSuccess;
-    stage_a_kernel<S><<<grid, kThreadsA, smem, stream>>>(d_frames, n_frames, total_tiles, stop);
+    stage_a_kernel<S><<<grid, kThreadsA, smem, stream>>>(d_frames, n_frames, total_tiles, stop, worklist);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_tiles, int shape,
-                           int stop, int sm_count, cudaStream_t stream)
+                           int stop, int* worklist, int sm_count, cudaStream_t stream)
 {
     switch (shape) {
-    case kDiamond5: return launch_shape<kDiamond5>(d_frames, n_frames, total_tiles, stop, sm_count, stream);
-    case kFull5: return launch_shape<kFull5>(d_frames, n_frames, total_tiles, stop, sm_count, stream);
-    case kCross5: return launch_shape<kCross5>(d_frames, n_frames, total_tiles, stop, sm_count, stream);
-    case kFull3: return launch_shape<kFull3>(d_frames, n_frames, total_tiles, stop, sm_count, stream);
-    case kCircle5: return launch_shape<kCircle5>(d_frames, n_frames, total_tiles, stop, sm_count, stream);
-    case kFull7: return launch_shape<kFull7>(d_frames, n_frames, total_tiles, stop, sm_count, stream);
+    case kDiamond5: return launch_shape<kDiamond5>(d_frames, n_frames, total_tiles, stop, worklist, sm_count, stream);
+    case kFull5: return launch_shape<kFull5>(d_frames, n_frames, total_tiles, stop, worklist, sm_count, stream);
+    case kCross5: return launch_shape<kCross5>(d_frames, n_frames, total_tiles, stop, worklist, sm_count, stream);
+    case kFull3: return launch_shape<kFull3>(d_frames, n_frames, total_tiles, stop, worklist, sm_count, stream);
+    case kCircle5: return launch_shape<kCircle5>(d_frames, n_frames, total_tiles, stop, worklist, sm_count, stream);
+    case kFull7: return launch_shape<kFull7>(d_frames, n_frames, total_tiles, stop, worklist, sm_count, stream);
     default: return cudaErrorInvalidValue;
     }
 }

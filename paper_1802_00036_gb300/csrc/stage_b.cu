@@ -1,36 +1,58 @@
 // stage_b.cu -- steps 5-8 of arXiv 1802.00036, Section IV, fused per tile.
 //
-// One CTA loads a kTileBH x kTileBW output tile of the step-4 map C plus a
-// halo of Rl + 4 pixels (step-6 half width, median 2, blur 2) into shared
-// memory, applying step 5 on the fly: a pixel above its column's top row
-// takes C(top, x), which is what copying the topmost value to the top of the
-// frame produces.  Then, as passes over shared memory:
-//   step 6  row max over 2 Rl + 1 columns, column max over 2 Rl + 1 rows,
-//           written only into empty pixels (skipped when the tile's
-//           median footprint holds no empty pixel -- the result is the same);
-//   step 7  5x5 median with the border replicated, then the 5x5 binomial
-//           Gaussian or the 13-tap bilateral with reflect-101 borders,
-//           written only where the median output is non-empty;
-//   step 8  100 - value where the median output is non-empty, 0 elsewhere.
+// Output tile kTBH x kTBW.  Phase 1 (every tile) loads the step-5 map E over
+// the tile plus a 4-pixel ring (median 2 + blur 2) into shared memory,
+// applying step 5 on the fly (a pixel above its column's top row takes
+// C(top, x), which is what copying the topmost value to row 0 gives) and
+// replicating the frame border, which is the median's border rule.  If no
+// pixel there is empty, step 6 changes nothing the tile reads, so the tile
+// goes straight to the median; otherwise it is put on a worklist and phase 2
+// handles it: it loads the wider ring step 6 needs (Rl = half the large
+// square), takes row then column maxima and fills only the empty pixels.
+// Both phases then run the same tail:
+//   step 7  5x5 median on the tile + 2 ring by the generated network of
+//           median_net.cuh (2 x 8 outputs per thread), the ring mirrored
+//           (reflect-101) for the blur; then the Gaussian [1 4 6 4 1]/16 as
+//           a row pass and a column pass (FMA chains, dyadic weights), or
+//           the 13-tap bilateral; both only where the median is non-empty;
+//   step 8  100 - value where the median is non-empty, 0 elsewhere.
 #include "common.cuh"
+#include "median_net.cuh"
 
 namespace dcgb {
 namespace {
 
-// Median of 25 values: after pass i, v[i] is the (i+1)-th smallest, so
-// v[12] is the median once passes 0..12 are done.  Compare-exchanges only.
-__device__ __forceinline__ float median25(float (&v)[25])
-{
-#pragma unroll
-    for (int i = 0; i <= 12; ++i)
-#pragma unroll
-        for (int j = i + 1; j < 25; ++j) {
-            const float a = v[i], b = v[j];
-            v[i] = fminf(a, b);
-            v[j] = fmaxf(a, b);
-        }
-    return v[12];
-}
+constexpr int kTBH = kTileBH;       // output tile rows
+constexpr int kTBW = kTileBW;       // output tile columns
+constexpr int kMR = kTBH + 4;       // median region rows (tile + 2 ring)
+constexpr int kMC = kTBW + 4;       // median region columns
+constexpr int kER = kTBH + 8;       // median input rows (tile + 4 ring)
+constexpr int kEC = kTBW + 8;       // median input columns
+constexpr int kES = kEC;            // stride of the median input buffer
+constexpr int kMS = kMC;            // stride of the median output buffer
+constexpr int kRS = kTBW;           // stride of the Gaussian row-pass buffer
+static_assert(kMR % 2 == 0 && kMC % 8 == 0, "median blocks are 2 x 8");
+static_assert((kMR / 2) * (kMC / 8) == kThreadsB, "one median block per thread");
+static_assert(kES % 4 == 0, "rows of the median input are 16-byte aligned");
+
+struct FloatOps {
+    static __device__ __forceinline__ float min2(float a, float b) { return fminf(a, b); }
+    static __device__ __forceinline__ float max2(float a, float b) { return fmaxf(a, b); }
+    static __device__ __forceinline__ float min3(float a, float b, float c)
+    {
+        float r;
+        asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+        return r;
+    }
+    static __device__ __forceinline__ float max3(float a, float b, float c)
+    {
+        float r;
+        asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+        return r;
+    }
+};
+
+__device__ __forceinline__ int clampi(int p, int n) { return p < 0 ? 0 : (p >= n ? n - 1 : p); }
 
 // Mirror p into [0, n) without repeating the edge pixel (reflect-101).
 __device__ __forceinline__ int reflect101(int p, int n)
@@ -40,220 +62,319 @@ __device__ __forceinline__ int reflect101(int p, int n)
     return p;
 }
 
-__device__ __forceinline__ int clampi(int p, int n) { return p < 0 ? 0 : (p >= n ? n - 1 : p); }
+struct Tile {
+    FrameDesc fd;
+    int y0, x0;  // first output pixel
+};
 
-__global__ void __launch_bounds__(kThreadsB)
-stage_b_kernel(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles, StageBParams p)
+__device__ __forceinline__ Tile tile_of(const FrameDesc* __restrict__ frames, int n_frames, int t)
 {
-    const int Rl = p.large_radius;
-    const int R = Rl + 4;
-    const int BH = kTileBH + 2 * R;
-    const int BW = kTileBW + 2 * R;
-    const int N = BH * BW;
+    Tile T;
+    const int f = find_frame<false>(frames, n_frames, t);
+    T.fd = frames[f];
+    const int local = t - T.fd.base_b;
+    const int ty = local / T.fd.tiles_x_b;
+    T.y0 = ty * kTBH;
+    T.x0 = (local - ty * T.fd.tiles_x_b) * kTBW;
+    return T;
+}
 
-    extern __shared__ float smem[];
-    float* bE = smem;          // step 5 output E, then reused for nothing else
-    float* bR = smem + N;      // step 6 row maxima, later the median output M
-    float* bF = smem + 2 * N;  // step 6 output F
-    int* ctop = reinterpret_cast<int*>(smem + 3 * N);      // BW entries
-    float* cval = smem + 3 * N + BW;                        // BW entries
+// Column tops and their values for columns [xa, xa + n) (clamped into the
+// frame), into ctop / cval.
+__device__ __forceinline__ void load_tops(const Tile& T, const StageBParams& p, int xa, int n,
+                                          int* ctop, float* cval)
+{
+    for (int i = threadIdx.x; i < n; i += kThreadsB) {
+        const int x = clampi(xa + i, T.fd.W);
+        int top = kNoTop;
+        float v = 0.0f;
+        if (p.extend_top) {
+            const int t = T.fd.top[x];
+            if (t < T.fd.H) {
+                top = t;
+                v = T.fd.c[(size_t)t * T.fd.c_pitch + x];
+            }
+        }
+        ctop[i] = top;
+        cval[i] = v;
+    }
+}
 
+// E at frame pixel (y, x) (in frame), from C and the column's top.
+__device__ __forceinline__ float extended(const Tile& T, const StageBParams& p, int y, int x,
+                                          int top, float topval)
+{
+    const bool above = (top != kNoTop) && y < top && (p.extend_rows < 0 || y >= top - p.extend_rows);
+    return above ? topval : T.fd.c[(size_t)y * T.fd.c_pitch + x];
+}
+
+// The shared tail: median of F (kER x kEC, border replicated) into M
+// (kMR x kMC), mirrored ring, blur, inversion, store.
+__device__ void median_blur_store(const Tile& T, const StageBParams& p, const float* __restrict__ F,
+                                  float* __restrict__ M, float* __restrict__ R)
+{
+    const int H = T.fd.H, W = T.fd.W;
     const int tid = threadIdx.x;
-    const float wn[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};  // [1 4 6 4 1]/16
-
-    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-        __syncthreads();
-        const int f = find_frame<false>(frames, n_frames, t);
-        const FrameDesc fd = frames[f];
-        const int local = t - fd.base_b;
-        const int ty = local / fd.tiles_x_b, tx = local - ty * fd.tiles_x_b;
-        const int oy = ty * kTileBH - R, ox = tx * kTileBW - R;
-        const int H = fd.H, W = fd.W;
-
-        // column tops and their values for the buffer's columns
-        for (int bx = tid; bx < BW; bx += kThreadsB) {
-            const int x = ox + bx;
-            int top = kNoTop;
-            float v = 0.0f;
-            if (p.extend_top && x >= 0 && x < W) {
-                top = fd.top[x];
-                if (top < H) v = fd.c[(size_t)top * fd.c_pitch + x];
-                else top = kNoTop;
-            }
-            ctop[bx] = top;
-            cval[bx] = v;
-        }
-        __syncthreads();
-
-        // P0, step 5 applied while loading C: E; out-of-frame -> -inf
-        for (int i = tid; i < N; i += kThreadsB) {
-            const int by = i / BW, bx = i - by * BW;
-            const int y = oy + by, x = ox + bx;
-            float e = ninf();
-            if (y >= 0 && y < H && x >= 0 && x < W) {
-                const int top = ctop[bx];
-                const bool above = (top != kNoTop) && y < top &&
-                                   (p.extend_rows < 0 || y >= top - p.extend_rows);
-                e = above ? cval[bx] : fd.c[(size_t)y * fd.c_pitch + x];
-            }
-            bE[i] = e;
-        }
-        __syncthreads();
-
-        auto emit = [&](const float* buf) {
-            for (int i = tid; i < kTileBH * kTileBW; i += kThreadsB) {
-                const int ly = i / kTileBW, lx = i - ly * kTileBW;
-                const int y = oy + R + ly, x = ox + R + lx;
-                if (y < H && x < W) fd.out[(size_t)y * fd.out_pitch + x] = buf[(ly + R) * BW + lx + R];
-            }
-        };
-        if (p.stop == kStopExtend) { emit(bE); continue; }
-
-        // Is any pixel the median will read empty?  (T + 4, clipped)
-        int any_empty = 0;
-        if (p.large_fill_on) {
-            for (int i = tid; i < N; i += kThreadsB) {
-                const int by = i / BW, bx = i - by * BW;
-                const int y = oy + by, x = ox + bx;
-                if (by >= Rl && by < BH - Rl && bx >= Rl && bx < BW - Rl &&
-                    y >= 0 && y < H && x >= 0 && x < W && is_empty(bE[i]))
-                    any_empty = 1;
+    // -- step 7: median, one 2 x 8 block per thread
+    {
+        const int rb = tid / (kMC / 8), cb = tid % (kMC / 8);
+        float x[6][12];
+        const float* src = F + (2 * rb) * kES + 8 * cb;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float4 v = *reinterpret_cast<const float4*>(src + r * kES + 4 * q);
+                x[r][4 * q + 0] = v.x;
+                x[r][4 * q + 1] = v.y;
+                x[r][4 * q + 2] = v.z;
+                x[r][4 * q + 3] = v.w;
             }
         }
-        any_empty = __syncthreads_or(any_empty);
-
-        const float* bFill = bE;
-        if (any_empty) {
-            // P1, step 6 rows on rows [0, BH), cols [Rl, BW - Rl)
-            for (int i = tid; i < N; i += kThreadsB) {
-                const int by = i / BW, bx = i - by * BW;
-                if (bx < Rl || bx >= BW - Rl) continue;
-                const int y = oy + by, x = ox + bx;
-                float m = ninf();
-                if (y >= 0 && y < H && x >= 0 && x < W) {
-                    for (int dx = -Rl; dx <= Rl; ++dx) m = fmaxf(m, bE[i + dx]);
-                }
-                bR[i] = m;
-            }
-            __syncthreads();
-            // P2, step 6 columns, empty pixels only: F on [Rl, BH-Rl) x [Rl, BW-Rl)
-            for (int i = tid; i < N; i += kThreadsB) {
-                const int by = i / BW, bx = i - by * BW;
-                if (by < Rl || by >= BH - Rl || bx < Rl || bx >= BW - Rl) continue;
-                float e = bE[i];
-                if (is_empty(e)) {
-                    float m = e;
-                    for (int dy = -Rl; dy <= Rl; ++dy) m = fmaxf(m, bR[i + dy * BW]);
-                    e = m;
-                }
-                bF[i] = e;
-            }
-            __syncthreads();
-            bFill = bF;
-        }
-        if (p.stop == kStopFillLarge) { emit(bFill); continue; }
-
-        // P3, step 7 median on T + 2 (in frame), border replicated -> bR (M)
-        const float* bMed = bFill;
+        float m[2][8];
         if (p.median) {
-            const int lo = R - 2, hiy = BH - R + 2, hix = BW - R + 2;
-            for (int i = tid; i < N; i += kThreadsB) {
-                const int by = i / BW, bx = i - by * BW;
-                if (by < lo || by >= hiy || bx < lo || bx >= hix) continue;
-                const int y = oy + by, x = ox + bx;
-                if (y < 0 || y >= H || x < 0 || x >= W) continue;
-                float v[25];
+            median_block_2x8<float, FloatOps>(x, m);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) m[r][j] = x[r + 2][j + 2];
+        }
+        float* dst = M + (2 * rb) * kMS + 8 * cb;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            *reinterpret_cast<float4*>(dst + r * kMS) = make_float4(m[r][0], m[r][1], m[r][2], m[r][3]);
+            *reinterpret_cast<float4*>(dst + r * kMS + 4) = make_float4(m[r][4], m[r][5], m[r][6], m[r][7]);
+        }
+    }
+    __syncthreads();
+    // -- mirror the ring outside the frame (the blur's reflect-101 border)
+    const bool edge = T.y0 < 2 || T.x0 < 2 || T.y0 + kTBH + 2 > H || T.x0 + kTBW + 2 > W;
+    if (edge) {
+        for (int i = tid; i < kMR * kMC; i += kThreadsB) {
+            const int a = i / kMC, b = i - a * kMC;
+            const int y = T.y0 - 2 + a, x = T.x0 - 2 + b;
+            const bool in = y >= 0 && y < H && x >= 0 && x < W;
+            if (!in && y >= -2 && y < H + 2 && x >= -2 && x < W + 2) {
+                const int sy = reflect101(y, H) - (T.y0 - 2), sx = reflect101(x, W) - (T.x0 - 2);
+                M[a * kMS + b] = M[sy * kMS + sx];
+            }
+        }
+        __syncthreads();
+    }
+    if (p.stop == kStopMedian) {
+        for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
+            const int a = i / kTBW, b = i - a * kTBW;
+            const int y = T.y0 + a, x = T.x0 + b;
+            if (y < H && x < W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = M[(a + 2) * kMS + b + 2];
+        }
+        return;
+    }
+    constexpr float w0 = 0.0625f, w1 = 0.25f, w2 = 0.375f;  // [1 4 6 4 1] / 16
+    if (p.blur == kBlurGauss) {
+        // row pass over all kMR rows of M, the tile's kTBW columns -> R
+        for (int i = tid; i < kMR * (kTBW / 4); i += kThreadsB) {
+            const int a = i / (kTBW / 4), b0 = 4 * (i - a * (kTBW / 4));
+            const float* s = M + a * kMS + b0;
+            float v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = s[k];
+            float o[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float acc = w0 * v[k];
+                acc = fmaf(w1, v[k + 1], acc);
+                acc = fmaf(w2, v[k + 2], acc);
+                acc = fmaf(w1, v[k + 3], acc);
+                acc = fmaf(w0, v[k + 4], acc);
+                o[k] = acc;
+            }
+            *reinterpret_cast<float4*>(R + a * kRS + b0) = make_float4(o[0], o[1], o[2], o[3]);
+        }
+        __syncthreads();
+    }
+    // column pass / bilateral, masked by the median, inverted, stored
+    for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
+        const int a = i / kTBW, b = i - a * kTBW;
+        const int y = T.y0 + a, x = T.x0 + b;
+        if (y >= H || x >= W) continue;
+        const float m = M[(a + 2) * kMS + b + 2];
+        float g = m;
+        if (!is_empty(m)) {
+            if (p.blur == kBlurGauss) {
+                const float* s = R + a * kRS + b;
+                float acc = w0 * s[0];
+                acc = fmaf(w1, s[kRS], acc);
+                acc = fmaf(w2, s[2 * kRS], acc);
+                acc = fmaf(w1, s[3 * kRS], acc);
+                acc = fmaf(w0, s[4 * kRS], acc);
+                g = acc;
+            } else if (p.blur == kBlurBilateral) {
+                float num = 0.0f, den = 0.0f;
 #pragma unroll
                 for (int dy = -2; dy <= 2; ++dy)
 #pragma unroll
                     for (int dx = -2; dx <= 2; ++dx) {
-                        const int yy = clampi(y + dy, H) - oy, xx = clampi(x + dx, W) - ox;
-                        v[(dy + 2) * 5 + dx + 2] = bFill[yy * BW + xx];
+                        const int r2 = dy * dy + dx * dx;
+                        if (r2 > 4) continue;
+                        const float v = M[(a + 2 + dy) * kMS + b + 2 + dx];
+                        const float d = v - m;
+                        const float wgt = p.ws[r2] * expf(-(d * d) * p.inv_2sc2);
+                        num = fmaf(v, wgt, num);
+                        den += wgt;
                     }
-                bR[i] = median25(v);
+                g = num / den;
             }
-            __syncthreads();
-            bMed = bR;
         }
-        if (p.stop == kStopMedian) { emit(bMed); continue; }
+        float o;
+        if (p.stop == kStopBlur) o = g;
+        else o = is_empty(m) ? 0.0f : __fsub_rn(kInvertFrom, g);
+        T.fd.out[(size_t)y * T.fd.out_pitch + x] = o;
+    }
+}
 
-        // P4, step 7 blur and step 8 inversion on the tile
-        for (int i = tid; i < kTileBH * kTileBW; i += kThreadsB) {
-            const int ly = i / kTileBW, lx = i - ly * kTileBW;
-            const int y = oy + R + ly, x = ox + R + lx;
-            if (y >= H || x >= W) continue;
-            const float m = bMed[(ly + R) * BW + lx + R];
-            float g = m;
-            if (!is_empty(m)) {
-                if (p.blur == kBlurGauss) {
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int dy = -2; dy <= 2; ++dy) {
-                        const int yy = reflect101(y + dy, H) - oy;
-                        float row = 0.0f;
-#pragma unroll
-                        for (int dx = -2; dx <= 2; ++dx) {
-                            const int xx = reflect101(x + dx, W) - ox;
-                            row = fmaf(wn[dx + 2], bMed[yy * BW + xx], row);
-                        }
-                        acc = fmaf(wn[dy + 2], row, acc);
-                    }
-                    g = acc;
-                } else if (p.blur == kBlurBilateral) {
-                    float num = 0.0f, den = 0.0f;
-#pragma unroll
-                    for (int dy = -2; dy <= 2; ++dy) {
-                        const int yy = reflect101(y + dy, H) - oy;
-#pragma unroll
-                        for (int dx = -2; dx <= 2; ++dx) {
-                            const int r2 = dy * dy + dx * dx;
-                            if (r2 > 4) continue;
-                            const int xx = reflect101(x + dx, W) - ox;
-                            const float v = bMed[yy * BW + xx];
-                            const float diff = v - m;
-                            const float w = p.ws[r2] * expf(-(diff * diff) * p.inv_2sc2);
-                            num = fmaf(v, w, num);
-                            den += w;
-                        }
-                    }
-                    g = num / den;
-                }
-            }
-            float o;
-            if (p.stop == kStopBlur) o = g;
-            else o = is_empty(m) ? 0.0f : __fsub_rn(kInvertFrom, g);
-            fd.out[(size_t)y * fd.out_pitch + x] = o;
+// Phase 1: every tile.  Tiles whose median input holds an empty pixel (and
+// step 6 is on) go to the worklist instead.
+__global__ void __launch_bounds__(kThreadsB, 2)
+stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p, int* __restrict__ worklist)
+{
+    __shared__ __align__(16) float E[kER * kES];
+    __shared__ __align__(16) float M[kMR * kMS];
+    __shared__ int ctop[kEC];
+    __shared__ float cval[kEC];
+    float* R = E;  // the Gaussian row pass reuses E once the median has read it
+
+    const Tile T = tile_of(frames, n_frames, blockIdx.x);
+    const int H = T.fd.H, W = T.fd.W;
+    const int tid = threadIdx.x;
+    load_tops(T, p, T.x0 - 4, kEC, ctop, cval);
+    __syncthreads();
+    int any_empty = 0;
+    for (int i = tid; i < kER * kEC; i += kThreadsB) {
+        const int k = i / kEC, l = i - k * kEC;
+        const int y = clampi(T.y0 - 4 + k, H);
+        const int xr = T.x0 - 4 + l;
+        const int x = clampi(xr, W);
+        const int cl = x - (T.x0 - 4);  // column of the clamped pixel in ctop/cval
+        const float e = extended(T, p, y, x, ctop[cl], cval[cl]);
+        any_empty |= is_empty(e);
+        E[k * kES + l] = e;
+    }
+    any_empty = __syncthreads_or(any_empty);
+    if (p.stop == kStopExtend || (p.stop == kStopFillLarge && !(any_empty && p.large_fill_on))) {
+        for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
+            const int a = i / kTBW, b = i - a * kTBW;
+            const int y = T.y0 + a, x = T.x0 + b;
+            if (y < H && x < W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = E[(a + 4) * kES + b + 4];
         }
+        return;
+    }
+    if (any_empty && p.large_fill_on) {
+        if (tid == 0) {
+            const int slot = atomicAdd(worklist, 1);
+            worklist[1 + slot] = blockIdx.x;
+        }
+        return;
+    }
+    median_blur_store(T, p, E, M, R);
+}
+
+// Phase 2: tiles from the worklist, with step 6.
+__global__ void __launch_bounds__(kThreadsB, 1)
+stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
+             const int* __restrict__ worklist)
+{
+    extern __shared__ __align__(16) float dyn[];
+    const int Rl = p.large_radius;
+    const int GR = kER + 2 * Rl, GC = kEC + 2 * Rl;  // the wide region
+    float* G = dyn;                       // E over the wide region, out of frame -inf
+    float* RM = G + GR * GC;              // row maxima
+    float* F = RM + GR * GC;              // F over tile + 4, border replicated
+    float* M = F + kER * kES;
+    int* ctop = reinterpret_cast<int*>(M + kMR * kMS);
+    float* cval = reinterpret_cast<float*>(ctop + GC);
+    float* R = G;
+
+    const int count = worklist[0];
+    const int tid = threadIdx.x;
+    for (int w = blockIdx.x; w < count; w += gridDim.x) {
+        __syncthreads();
+        const Tile T = tile_of(frames, n_frames, worklist[1 + w]);
+        const int H = T.fd.H, W = T.fd.W;
+        const int gy = T.y0 - 4 - Rl, gx = T.x0 - 4 - Rl;  // frame position of G(0, 0)
+        load_tops(T, p, gx, GC, ctop, cval);
+        __syncthreads();
+        for (int i = tid; i < GR * GC; i += kThreadsB) {
+            const int k = i / GC, l = i - k * GC;
+            const int y = gy + k, x = gx + l;
+            float e = ninf();
+            if (y >= 0 && y < H && x >= 0 && x < W) e = extended(T, p, y, x, ctop[l], cval[l]);
+            G[i] = e;
+        }
+        __syncthreads();
+        // row maxima over 2 Rl + 1 columns, for columns [Rl, GC - Rl)
+        for (int i = tid; i < GR * GC; i += kThreadsB) {
+            const int k = i / GC, l = i - k * GC;
+            if (l < Rl || l >= GC - Rl) continue;
+            float m = ninf();
+            for (int d = -Rl; d <= Rl; ++d) m = fmaxf(m, G[i + d]);
+            RM[i] = m;
+        }
+        __syncthreads();
+        // column maxima and the fill of empty pixels, tile + 4, replicated border
+        for (int i = tid; i < kER * kEC; i += kThreadsB) {
+            const int k = i / kEC, l = i - k * kEC;
+            const int y = clampi(T.y0 - 4 + k, H), x = clampi(T.x0 - 4 + l, W);
+            const int gk = y - gy, gl = x - gx;
+            float e = G[gk * GC + gl];
+            if (is_empty(e)) {
+                float m = e;
+                for (int d = -Rl; d <= Rl; ++d) m = fmaxf(m, RM[(gk + d) * GC + gl]);
+                e = m;
+            }
+            F[k * kES + l] = e;
+        }
+        __syncthreads();
+        if (p.stop == kStopFillLarge) {
+            for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
+                const int a = i / kTBW, b = i - a * kTBW;
+                const int y = T.y0 + a, x = T.x0 + b;
+                if (y < H && x < W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = F[(a + 4) * kES + b + 4];
+            }
+            continue;
+        }
+        median_blur_store(T, p, F, M, R);
     }
 }
 
 }  // namespace
 
-size_t stage_b_smem_bytes(int large_radius)
+size_t stage_b_fill_smem_bytes(int large_radius)
 {
-    const int R = large_radius + 4;
-    const size_t BH = kTileBH + 2 * R, BW = kTileBW + 2 * R;
-    return sizeof(float) * (3 * BH * BW + 2 * BW);
+    const size_t GR = kER + 2 * large_radius, GC = kEC + 2 * large_radius;
+    return sizeof(float) * (2 * GR * GC + kER * kES + kMR * kMS + 2 * GC);
 }
 
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,
-                           const StageBParams& p, int sm_count, cudaStream_t stream)
+                           const StageBParams& p, int* worklist, int sm_count, cudaStream_t stream)
 {
     static int configured_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (configured_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(stage_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)stage_b_smem_bytes(kMaxLargeFill / 2));
+        cudaError_t e = cudaFuncSetAttribute(stage_b_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)stage_b_fill_smem_bytes(kMaxLargeFill / 2));
         if (e != cudaSuccess) return e;
         configured_dev = dev;
     }
-    int grid = total_tiles;
-    const int cap = sm_count * 8;
-    if (grid > cap) grid = cap;
-    if (grid < 1) return cudaSuccess;
-    stage_b_kernel<<<grid, kThreadsB, stage_b_smem_bytes(p.large_radius), stream>>>(
-        d_frames, n_frames, total_tiles, p);
+    if (total_tiles < 1) return cudaSuccess;
+    stage_b_main<<<total_tiles, kThreadsB, 0, stream>>>(d_frames, n_frames, p, worklist);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !p.large_fill_on || p.stop == kStopExtend) return e;
+    int grid = sm_count;
+    if (grid > total_tiles) grid = total_tiles;
+    stage_b_fill<<<grid, kThreadsB, stage_b_fill_smem_bytes(p.large_radius), stream>>>(d_frames, n_frames, p,
+                                                                                       worklist);
     return cudaGetLastError();
 }
 
