@@ -3,12 +3,12 @@
 // Output tile kTBH x kTBW.  Phase 1 (every tile) loads the step-5 map E over
 // the tile plus a 4-pixel ring (median 2 + blur 2) into shared memory,
 // applying step 5 on the fly (a pixel above its column's top row takes
-// C(top, x), which is what copying the topmost value to row 0 gives) and
-// replicating the frame border, which is the median's border rule.  If no
-// pixel there is empty, step 6 changes nothing the tile reads, so the tile
-// goes straight to the median; otherwise it is put on a worklist and phase 2
-// handles it: it loads the wider ring step 6 needs (Rl = half the large
-// square), takes row then column maxima and fills only the empty pixels.
+// C(top, x), which is what copying the topmost value to row 0 gives).
+// Step 6 changes only empty pixels: a tile with a few of them in that region
+// fills each with one warp (the maximum over its (2 Rl + 1)^2 window, read
+// from C); a tile with many goes on a worklist for phase 2, which loads the
+// wider ring, takes row then column maxima and fills the empty pixels.  The
+// frame border is then replicated around the region (the median's rule).
 // Both phases then run the same tail:
 //   step 7  5x5 median on the tile + 2 ring by the generated network of
 //           median_net.cuh (2 x 8 outputs per thread), the ring mirrored
@@ -233,8 +233,42 @@ __device__ void median_blur_store(const Tile& T, const StageBParams& p, const fl
     }
 }
 
-// Phase 1: every tile.  Tiles whose median input holds an empty pixel (and
-// step 6 is on) go to the worklist instead.
+// Step 6 at one empty pixel (y, x): the maximum of E over the in-frame part
+// of its (2 Rl + 1)^2 window, read from C (L2) with step 5 applied.  One
+// warp per pixel, lane = column offset; returns the maximum in every lane.
+__device__ float large_fill_at(const Tile& T, const StageBParams& p, int y, int x, int lane)
+{
+    const int Rl = p.large_radius, H = T.fd.H, W = T.fd.W;
+    const int ylo = max(0, y - Rl), yhi = min(H - 1, y + Rl);
+    float m = ninf();
+    for (int dx0 = -Rl; dx0 <= Rl; dx0 += 32) {
+        const int dx = dx0 + lane;
+        const int xx = x + dx;
+        if (dx <= Rl && xx >= 0 && xx < W) {
+            int top = kNoTop;
+            float tv = 0.0f;
+            if (p.extend_top) {
+                const int t = T.fd.top[xx];
+                if (t < H) {
+                    top = t;
+                    tv = T.fd.c[(size_t)t * T.fd.c_pitch + xx];
+                }
+            }
+#pragma unroll 4
+            for (int yy = ylo; yy <= yhi; ++yy) m = fmaxf(m, extended(T, p, yy, xx, top, tv));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    return m;
+}
+
+// Empty pixels a tile fills itself; more go to the worklist (phase 2).
+constexpr int kMaxSparseFill = 160;
+
+// Phase 1: every tile.  A tile whose median input holds at most
+// kMaxSparseFill empty pixels fills them itself (step 6, pixel by pixel);
+// a tile with more goes to the worklist.
 __global__ void __launch_bounds__(kThreadsB, 2)
 stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p, int* __restrict__ worklist)
 {
@@ -242,40 +276,67 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
     __shared__ __align__(16) float M[kMR * kMS];
     __shared__ int ctop[kEC];
     __shared__ float cval[kEC];
+    __shared__ int elist[kMaxSparseFill];
+    __shared__ int ecount;
     float* R = E;  // the Gaussian row pass reuses E once the median has read it
 
     const Tile T = tile_of(frames, n_frames, blockIdx.x);
     const int H = T.fd.H, W = T.fd.W;
     const int tid = threadIdx.x;
+    if (tid == 0) ecount = 0;
     load_tops(T, p, T.x0 - 4, kEC, ctop, cval);
     __syncthreads();
-    int any_empty = 0;
+    // step 5 while loading the in-frame part of tile + 4; note empty pixels
     for (int i = tid; i < kER * kEC; i += kThreadsB) {
         const int k = i / kEC, l = i - k * kEC;
-        const int y = clampi(T.y0 - 4 + k, H);
-        const int xr = T.x0 - 4 + l;
-        const int x = clampi(xr, W);
-        const int cl = x - (T.x0 - 4);  // column of the clamped pixel in ctop/cval
-        const float e = extended(T, p, y, x, ctop[cl], cval[cl]);
-        any_empty |= is_empty(e);
+        const int y = T.y0 - 4 + k, x = T.x0 - 4 + l;
+        if (y < 0 || y >= H || x < 0 || x >= W) continue;
+        const float e = extended(T, p, y, x, ctop[l], cval[l]);
         E[k * kES + l] = e;
+        if (p.large_fill_on && is_empty(e)) {
+            const int j = atomicAdd(&ecount, 1);
+            if (j < kMaxSparseFill) elist[j] = (k << 16) | l;
+        }
     }
-    any_empty = __syncthreads_or(any_empty);
-    if (p.stop == kStopExtend || (p.stop == kStopFillLarge && !(any_empty && p.large_fill_on))) {
+    __syncthreads();
+    const int n_empty = ecount;
+    auto store_tile = [&](const float* buf) {
         for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
             const int a = i / kTBW, b = i - a * kTBW;
             const int y = T.y0 + a, x = T.x0 + b;
-            if (y < H && x < W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = E[(a + 4) * kES + b + 4];
+            if (y < H && x < W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = buf[(a + 4) * kES + b + 4];
         }
-        return;
-    }
-    if (any_empty && p.large_fill_on) {
+    };
+    if (p.stop == kStopExtend) { store_tile(E); return; }
+    if (n_empty > kMaxSparseFill) {
         if (tid == 0) {
             const int slot = atomicAdd(worklist, 1);
             worklist[1 + slot] = blockIdx.x;
         }
         return;
     }
+    if (n_empty > 0) {  // step 6 at the few empty pixels, one warp each
+        // E is only written here (at empty pixels); large_fill_at reads C
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int j = warp; j < n_empty; j += kThreadsB / 32) {
+            const int k = elist[j] >> 16, l = elist[j] & 0xFFFF;
+            const float m = large_fill_at(T, p, T.y0 - 4 + k, T.x0 - 4 + l, lane);
+            if (lane == 0) E[k * kES + l] = m;
+        }
+        __syncthreads();
+    }
+    // replicate the frame border into the out-of-frame part (the median's rule)
+    if (T.y0 < 4 || T.x0 < 4 || T.y0 + kTBH + 4 > H || T.x0 + kTBW + 4 > W) {
+        for (int i = tid; i < kER * kEC; i += kThreadsB) {
+            const int k = i / kEC, l = i - k * kEC;
+            const int y = T.y0 - 4 + k, x = T.x0 - 4 + l;
+            if (y >= 0 && y < H && x >= 0 && x < W) continue;
+            const int sk = clampi(y, H) - (T.y0 - 4), sl = clampi(x, W) - (T.x0 - 4);
+            E[i] = E[sk * kES + sl];
+        }
+        __syncthreads();
+    }
+    if (p.stop == kStopFillLarge) { store_tile(E); return; }
     median_blur_store(T, p, E, M, R);
 }
 
@@ -371,7 +432,7 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
     stage_b_main<<<total_tiles, kThreadsB, 0, stream>>>(d_frames, n_frames, p, worklist);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !p.large_fill_on || p.stop == kStopExtend) return e;
-    int grid = sm_count;
+    int grid = 2 * sm_count;
     if (grid > total_tiles) grid = total_tiles;
     stage_b_fill<<<grid, kThreadsB, stage_b_fill_smem_bytes(p.large_radius), stream>>>(d_frames, n_frames, p,
                                                                                        worklist);

@@ -76,6 +76,20 @@ def test_large_fill_sizes(ctx, large):
                 oracle.complete(f, large_fill=large, stop_after=stop), stop, f"large {large}")
 
 
+@pytest.mark.parametrize("hole", [14, 22, 44])
+@pytest.mark.parametrize("large", [15, 31, 51])
+def test_large_fill_holes(ctx, hole, large):
+    # a dense map with square holes: after steps 1-5 a hole of side s keeps
+    # roughly (s - 6)^2 empty pixels, so small holes take the per-pixel fill
+    # inside the main stage-B pass and large ones the worklist pass
+    f = synth.random_sparse(150, 250, 1.0, 3 + hole, 2.0, 80.0)
+    for (y, x) in ((60, 40), (95, 130), (70, 200), (140, 5), (3, 246)):
+        f[max(0, y - hole // 2):y + hole // 2, max(0, x - hole // 2):x + hole // 2] = 0.0
+    for stop in ("fill_large", "median", "full"):
+        compare(gpu_run(ctx, f[None], large_fill=large, stop_after=stop)[0],
+                oracle.complete(f, large_fill=large, stop_after=stop), stop, f"hole {hole} large {large}")
+
+
 @pytest.mark.parametrize("blur", ["gauss", "bilateral", "none"])
 @pytest.mark.parametrize("median", [True, False])
 def test_blur_variants(ctx, blur, median):
