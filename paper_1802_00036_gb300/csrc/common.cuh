@@ -22,10 +22,9 @@ constexpr float kInvertFrom = 100.0f;
 // top[] entries start at this value; any real row is smaller.
 constexpr int kNoTop = 0x7F7F7F7F;
 
-// Stage A output tile.
-constexpr int kTileAH = 32;
-constexpr int kTileAW = 64;
-constexpr int kThreadsA = 256;
+// Stage A: one warp streams one (strip, band) unit; 4 units per block.
+constexpr int kStageAColsPerLane = 4;
+constexpr int kThreadsA = 128;
 // Stage B output tile (median blocks of 2 x 8 over the tile + 2 ring).
 constexpr int kTileBH = 60;
 constexpr int kTileBW = 60;
@@ -50,7 +49,8 @@ struct FrameDesc {
     int* top;          // W entries: topmost non-empty row of C (scratch)
     int H, W;
     int in_pitch, out_pitch, c_pitch;
-    int tiles_x_a, base_a;  // stage A: tiles per row of tiles, first flat tile
+    int tiles_x_a, base_a;  // stage A: strips per frame, first flat unit
+    int band_a;             // stage A: rows per band
     int tiles_x_b, base_b;  // stage B: same
 };
 
@@ -84,6 +84,14 @@ __device__ __forceinline__ int find_frame(const FrameDesc* __restrict__ d, int n
     }
     return lo;
 }
+
+// Stage A geometry (stage_a.cu): output columns per strip and the halo
+// (= vertical delay) for a first element.
+int stage_a_strip_width(int shape);
+int stage_a_halo(int shape);
+// Rows per stage-A band so that a batch with `total_strips` strips gives the
+// GPU enough warps; at least 32 rows.
+int stage_a_band_rows(int H, long long total_strips, int sm_count);
 
 // Launchers (stage_a.cu, stage_b.cu).  Return cudaGetLastError().
 // `worklist` holds 1 + (stage B tiles) ints: a count that stage A zeroes,

@@ -176,8 +176,11 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
     ctx->last_launches = 0;
     if (n == 0) return DC_OK;
 
-    // layout of scratch and tiles
+    // layout of scratch, stage-A units (strip x band) and stage-B tiles
     std::vector<FrameDesc> desc((size_t)n);
+    const int strip_w = stage_a_strip_width(p->first_kernel);
+    long long total_strips = 0;
+    for (int i = 0; i < n; ++i) total_strips += ceil_div(frames[i].W, strip_w);
     size_t c_off = 0, top_off = 0;
     long long tiles_a = 0, tiles_b = 0;
     for (int i = 0; i < n; ++i) {
@@ -190,11 +193,12 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         d.in_pitch = f.in_pitch;
         d.out_pitch = f.out_pitch;
         d.c_pitch = (int)round_up((size_t)f.W, 32);
-        d.tiles_x_a = ceil_div(f.W, kTileAW);
+        d.tiles_x_a = ceil_div(f.W, strip_w);
+        d.band_a = stage_a_band_rows(f.H, total_strips, ctx->sm_count);
         d.tiles_x_b = ceil_div(f.W, kTileBW);
         d.base_a = (int)tiles_a;
         d.base_b = (int)tiles_b;
-        tiles_a += (long long)d.tiles_x_a * ceil_div(f.H, kTileAH);
+        tiles_a += (long long)d.tiles_x_a * ceil_div(f.H, d.band_a);
         tiles_b += (long long)d.tiles_x_b * ceil_div(f.H, kTileBH);
         d.c = reinterpret_cast<float*>(c_off);  // offsets until scratch is known
         d.top = reinterpret_cast<int*>(top_off);

@@ -60,7 +60,7 @@ dc_status setup(int dev, unsigned char** ptr, int* sms)
 // preparation the two stage kernels need, done on the device so that the
 // call copies nothing from the host.
 __global__ void noalloc_prepare(FrameDesc* table, int* top, float* cmap, const float* in, float* out,
-                                int n, int H, int W, int c_pitch, int tiles_x_a, int tiles_a,
+                                int n, int H, int W, int c_pitch, int tiles_x_a, int tiles_a, int band_a,
                                 int tiles_x_b, int tiles_b, int top_ints)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -78,6 +78,7 @@ __global__ void noalloc_prepare(FrameDesc* table, int* top, float* cmap, const f
         d.c_pitch = c_pitch;
         d.tiles_x_a = tiles_x_a;
         d.base_a = i * tiles_a;
+        d.band_a = band_a;
         d.tiles_x_b = tiles_x_b;
         d.base_b = i * tiles_b;
         table[i] = d;
@@ -129,8 +130,10 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     int* work = reinterpret_cast<int*>(base + kTableBytes + kTopBytes);
     float* cmap = reinterpret_cast<float*>(base + kTableBytes + kTopBytes + kWorkBytes);
     const bool need_b = (params->stop_after == DC_STOP_FULL || params->stop_after >= DC_STOP_EXTEND);
-    const int tiles_x_a = (W + kTileAW - 1) / kTileAW;
-    const int tiles_a = tiles_x_a * ((H + kTileAH - 1) / kTileAH);
+    const int strip_w = stage_a_strip_width(params->first_kernel);
+    const int tiles_x_a = (W + strip_w - 1) / strip_w;
+    const int band_a = stage_a_band_rows(H, (long long)tiles_x_a * n, sms);
+    const int tiles_a = tiles_x_a * ((H + band_a - 1) / band_a);
     const int tiles_x_b = (W + kTileBW - 1) / kTileBW;
     const int tiles_b = tiles_x_b * ((H + kTileBH - 1) / kTileBH);
     if ((long long)tiles_a * n > INT32_MAX / 2 || (long long)tiles_b * n + 1 > DC_NOALLOC_WORK_INTS)
@@ -142,7 +145,7 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     int blocks = (top_ints > n ? top_ints : n) / threads + 1;
     if (blocks > 1024) blocks = 1024;
     noalloc_prepare<<<blocks, threads, 0, st>>>(table, need_b ? top : nullptr, need_b ? cmap : nullptr,
-                                                 in, out, n, H, W, (int)c_pitch, tiles_x_a, tiles_a,
+                                                 in, out, n, H, W, (int)c_pitch, tiles_x_a, tiles_a, band_a,
                                                  tiles_x_b, tiles_b, top_ints);
     if (cudaGetLastError() != cudaSuccess) return DC_ERR_CUDA;
 

@@ -1,23 +1,78 @@
-// stage_a.cu -- steps 1-4 of arXiv 1802.00036, Section IV, fused per tile.
+// stage_a.cu -- steps 1-4 of arXiv 1802.00036, Section IV, streamed down
+// column strips.
 //
-// One CTA loads a kTileAH x kTileAW output tile plus a halo of
-// R = r1 + 2 + 2 + 3 pixels (first element, close dilation, close erosion,
-// 7x7 fill) into shared memory and runs the steps as passes over two
-// ping-pong buffers.  Every pass computes the region its consumer reads;
-// out-of-frame positions hold the neutral value of the consumer's operation
-// (-inf before a max, +inf before a min), which is exactly "out-of-frame
-// pixels are ignored".  The 5x5 and 7x7 squares are separable (row pass, then
-// column pass); the first element is applied tap by tap from its shape.
+// One warp owns a strip of 32 x kV adjacent columns (lane l holds columns
+// kV*l .. kV*l + kV - 1) and walks down a band of rows, one input row per
+// step.  Every vertical window lives in small register rings; the horizontal
+// part of every window comes from the lane's own columns plus up to three
+// columns of each neighbouring lane (warp shuffles).  The steps are
+//   1  invert: 100 - d on valid pixels (one float32 subtraction), 0 else;
+//   2  the first element (Fig. 4) as row maxima of half-width 0..3 combined
+//      over its rows;
+//   3  5x5 close: 5-wide row max, 5-row max, 5-wide row min, 5-row min;
+//   4  7x7 max (7-wide, 7-row) written into empty pixels only;
+// with 3-input min/max (one instruction on sm_103a).  Each step delays its
+// output by its vertical radius, so step 4 emits row t - (r1 + 7) when input
+// row t arrives.  A pixel outside the frame holds the neutral value of the
+// operation that reads it (-inf before a max, +inf before a min), which is
+// "out-of-frame pixels are ignored".  The strip's outer r1 + 7 columns on
+// each side are only halo: strips overlap by that much, bands by as many
+// rows, and the rings start with values that only reach rows above the band.
 //
-// Output: C (step-4 map) into scratch, and for each column the smallest row
-// whose C is non-empty via atomicMin on top[] (step 5 needs it).  With a
-// stop before step 5 the tile is written straight to the output instead.
+// Output: C (the step-4 map) into scratch, and for each column the smallest
+// row with a non-empty C via atomicMin on top[] (step 5 needs it).  With a
+// stop before step 5 the requested map goes to the output instead.
 #include "common.cuh"
 
 #include <climits>
+#include <type_traits>
 
 namespace dcgb {
 namespace {
+
+constexpr int kV = kStageAColsPerLane;
+constexpr int kSW = 32 * kV;  // strip width in columns
+
+__device__ __forceinline__ float max3f(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// A row of kV values plus up to three neighbours on each side.
+struct Row {
+    float v[kV];
+    float l[4];  // l[i]: column -i  (l[0] unused)
+    float r[4];  // r[i]: column kV - 1 + i (r[0] unused)
+    __device__ __forceinline__ float at(int j) const
+    {
+        return j < 0 ? l[-j] : (j >= kV ? r[j - kV + 1] : v[j]);
+    }
+};
+
+// Fetch `rad` neighbour columns on each side from the adjacent lanes.
+template <int rad>
+__device__ __forceinline__ void neighbours(Row& x)
+{
+#pragma unroll
+    for (int i = 1; i <= rad; ++i) {
+        x.l[i] = __shfl_up_sync(0xffffffffu, x.v[kV - i], 1);
+        x.r[i] = __shfl_down_sync(0xffffffffu, x.v[i - 1], 1);
+    }
+}
+
+template <bool kMax>
+__device__ __forceinline__ float ext3(float a, float b, float c)
+{
+    return kMax ? max3f(a, b, c) : min3f(a, b, c);
+}
 
 template <int S> struct ShapeInfo;
 template <> struct ShapeInfo<kDiamond5> { static constexpr int r = 2; };
@@ -27,223 +82,408 @@ template <> struct ShapeInfo<kFull3> { static constexpr int r = 1; };
 template <> struct ShapeInfo<kCircle5> { static constexpr int r = 2; };
 template <> struct ShapeInfo<kFull7> { static constexpr int r = 3; };
 
-// Membership of offset (dy, dx) in the element (Fig. 4).
-template <int S>
-__device__ __forceinline__ constexpr bool in_shape(int dy, int dx)
-{
-    const int ay = dy < 0 ? -dy : dy, ax = dx < 0 ? -dx : dx;
-    if (S == kDiamond5) return ay + ax <= 2;
-    if (S == kFull5) return ay <= 2 && ax <= 2;
-    if (S == kCross5) return (ay == 0 && ax <= 2) || (ax == 0 && ay <= 2);
-    if (S == kFull3) return ay <= 1 && ax <= 1;
-    if (S == kCircle5) return ay * ay + ax * ax <= 5;
-    return ay <= 3 && ax <= 3;  // kFull7
-}
+// 7-row window of a row extreme h: u(o) = ext(h(o-2), h(o-1), h(o));
+// out(o-3) = ext(u(o-4), u(o-1), h(o)).
+template <bool kMax>
+struct Window7 {
+    float h[2][kV], u[4][kV];
+    __device__ void init(float fill)
+    {
+        for (int v = 0; v < kV; ++v) {
+            h[0][v] = h[1][v] = fill;
+            u[0][v] = u[1][v] = u[2][v] = u[3][v] = fill;
+        }
+    }
+    template <int PHI>
+    __device__ __forceinline__ float push(int v, float hn)
+    {
+        const float un = ext3<kMax>(h[PHI & 1][v], h[(PHI + 1) & 1][v], hn);
+        const float o = ext3<kMax>(u[PHI & 3][v], u[(PHI + 3) & 3][v], hn);
+        h[PHI & 1][v] = hn;
+        u[PHI & 3][v] = un;
+        return o;
+    }
+};
+
+// Step 2 for each element: rings of the rows it still needs; push() takes
+// input row t and returns the dilation of row t - r1.
+template <int S> struct FirstDilation;
+
+template <> struct FirstDilation<kDiamond5> {
+    // rows: |dy| = 2 -> width 1, |dy| = 1 -> 3, dy = 0 -> 5
+    // p(o) = max(x(o-2), h1(o-1), h2(o));  A(o) = max(p(o), h1(o+1), x(o+2))
+    float x[2][kV], p[2][kV], h1[kV];
+    __device__ void init()
+    {
+        for (int v = 0; v < kV; ++v) x[0][v] = x[1][v] = p[0][v] = p[1][v] = h1[v] = ninf();
+    }
+    template <int PHI>
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    {
+        neighbours<2>(in);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const float a1 = max3f(in.at(v - 1), in.v[v], in.at(v + 1));
+            const float a2 = max3f(a1, in.at(v - 2), in.at(v + 2));
+            const float pn = max3f(x[PHI & 1][v], h1[v], a2);
+            out[v] = max3f(p[PHI & 1][v], h1[v], in.v[v]);
+            x[PHI & 1][v] = in.v[v];
+            p[PHI & 1][v] = pn;
+            h1[v] = a1;
+        }
+    }
+};
+
+template <> struct FirstDilation<kFull5> {
+    // 5-wide row max h; s(o) = max(h(o-2), h(o-1), h(o)); A(o-2) = max(s(o-2), h(o-1), h(o))
+    float h[2][kV], s[2][kV];
+    __device__ void init()
+    {
+        for (int v = 0; v < kV; ++v) h[0][v] = h[1][v] = s[0][v] = s[1][v] = ninf();
+    }
+    template <int PHI>
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    {
+        neighbours<2>(in);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const float a2 = max3f(max3f(in.at(v - 2), in.at(v - 1), in.v[v]), in.at(v + 1), in.at(v + 2));
+            const float hm1 = h[(PHI + 1) & 1][v], hm2 = h[PHI & 1][v];
+            out[v] = max3f(s[PHI & 1][v], hm1, a2);
+            s[PHI & 1][v] = max3f(hm2, hm1, a2);
+            h[PHI & 1][v] = a2;
+        }
+    }
+};
+
+template <> struct FirstDilation<kCross5> {
+    // p(o) = max(x(o-2), x(o-1), h2(o));  A(o) = max(p(o), x(o+1), x(o+2))
+    float x[2][kV], p[2][kV];
+    __device__ void init()
+    {
+        for (int v = 0; v < kV; ++v) x[0][v] = x[1][v] = p[0][v] = p[1][v] = ninf();
+    }
+    template <int PHI>
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    {
+        neighbours<2>(in);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const float a2 = max3f(max3f(in.at(v - 2), in.at(v - 1), in.v[v]), in.at(v + 1), in.at(v + 2));
+            const float xm1 = x[(PHI + 1) & 1][v], xm2 = x[PHI & 1][v];
+            const float pn = max3f(xm2, xm1, a2);
+            out[v] = max3f(p[PHI & 1][v], xm1, in.v[v]);
+            x[PHI & 1][v] = in.v[v];
+            p[PHI & 1][v] = pn;
+        }
+    }
+};
+
+template <> struct FirstDilation<kFull3> {
+    // A(o-1) = max(h1(o-2), h1(o-1), h1(o))
+    float h[2][kV];
+    __device__ void init()
+    {
+        for (int v = 0; v < kV; ++v) h[0][v] = h[1][v] = ninf();
+    }
+    template <int PHI>
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    {
+        neighbours<1>(in);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const float a1 = max3f(in.at(v - 1), in.v[v], in.at(v + 1));
+            out[v] = max3f(h[PHI & 1][v], h[(PHI + 1) & 1][v], a1);
+            h[PHI & 1][v] = a1;
+        }
+    }
+};
+
+template <> struct FirstDilation<kCircle5> {
+    // rows: |dy| = 2 -> width 3, |dy| <= 1 -> 5
+    // p(o) = max(h1(o-2), h2(o-1), h2(o));  A(o) = max(p(o), h2(o+1), h1(o+2))
+    float h1[2][kV], h2[kV], p[2][kV];
+    __device__ void init()
+    {
+        for (int v = 0; v < kV; ++v) h1[0][v] = h1[1][v] = h2[v] = p[0][v] = p[1][v] = ninf();
+    }
+    template <int PHI>
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    {
+        neighbours<2>(in);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const float a1 = max3f(in.at(v - 1), in.v[v], in.at(v + 1));
+            const float a2 = max3f(a1, in.at(v - 2), in.at(v + 2));
+            const float pn = max3f(h1[PHI & 1][v], h2[v], a2);
+            out[v] = max3f(p[PHI & 1][v], h2[v], a1);
+            h1[PHI & 1][v] = a1;
+            h2[v] = a2;
+            p[PHI & 1][v] = pn;
+        }
+    }
+};
+
+template <> struct FirstDilation<kFull7> {
+    Window7<true> w;
+    __device__ void init() { w.init(ninf()); }
+    template <int PHI>
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    {
+        neighbours<3>(in);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const float a3 = max3f(max3f(in.at(v - 3), in.at(v - 2), in.at(v - 1)), in.v[v],
+                                   max3f(in.at(v + 1), in.at(v + 2), in.at(v + 3)));
+            out[v] = w.template push<PHI>(v, a3);
+        }
+    }
+};
+
+// 5x5 square max or min: 5-wide row extreme h, then
+// s(o) = ext(h(o-2), h(o-1), h(o)); out(o-2) = ext(s(o-2), h(o-1), h(o)).
+template <bool kMax>
+struct Square5 {
+    float h[2][kV], s[2][kV];
+    __device__ void init(float fill)
+    {
+        for (int v = 0; v < kV; ++v) h[0][v] = h[1][v] = s[0][v] = s[1][v] = fill;
+    }
+    template <int PHI>
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    {
+        neighbours<2>(in);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const float hn =
+                ext3<kMax>(ext3<kMax>(in.at(v - 2), in.at(v - 1), in.v[v]), in.at(v + 1), in.at(v + 2));
+            const float hm1 = h[(PHI + 1) & 1][v], hm2 = h[PHI & 1][v];
+            out[v] = ext3<kMax>(s[PHI & 1][v], hm1, hn);
+            s[PHI & 1][v] = ext3<kMax>(hm2, hm1, hn);
+            h[PHI & 1][v] = hn;
+        }
+    }
+};
+
+// Step 4: 7x7 max written into empty pixels of B only.
+struct Fill7 {
+    Window7<true> w;
+    float b[4][kV];  // B rows, to select C(o - 3)
+    __device__ void init()
+    {
+        w.init(ninf());
+        for (int v = 0; v < kV; ++v) b[0][v] = b[1][v] = b[2][v] = b[3][v] = ninf();
+    }
+    template <int PHI>
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    {
+        neighbours<3>(in);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const float hn = max3f(max3f(in.at(v - 3), in.at(v - 2), in.at(v - 1)), in.v[v],
+                                   max3f(in.at(v + 1), in.at(v + 2), in.at(v + 3)));
+            const float m7 = w.template push<PHI>(v, hn);
+            const float bc = b[(PHI + 1) & 3][v];  // B(o - 3)
+            out[v] = is_empty(bc) ? m7 : bc;
+            b[PHI & 3][v] = in.v[v];
+        }
+    }
+};
 
 template <int S>
-__global__ void __launch_bounds__(kThreadsA)
-stage_a_kernel(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles, int stop,
+__global__ void __launch_bounds__(kThreadsA, 3)
+stage_a_stream(const FrameDesc* __restrict__ frames, int n_frames, int total_units, int stop,
                int* __restrict__ worklist)
 {
-    if (worklist && blockIdx.x == 0 && threadIdx.x == 0) worklist[0] = 0;
     constexpr int R1 = ShapeInfo<S>::r;
-    constexpr int R = R1 + 2 + 2 + 3;
-    constexpr int BH = kTileAH + 2 * R;
-    constexpr int BW = kTileAW + 2 * R;
-    constexpr int N = BH * BW;
+    constexpr int Rh = R1 + 7;        // halo, horizontal and vertical
+    constexpr int OW = kSW - 2 * Rh;  // output columns per strip
+    const int lane = threadIdx.x & 31;
+    const int unit = blockIdx.x * (kThreadsA / 32) + (threadIdx.x >> 5);
+    if (worklist && unit == 0 && lane == 0) worklist[0] = 0;
+    if (unit >= total_units) return;  // whole warps only
 
-    extern __shared__ float smem[];
-    float* b0 = smem;
-    float* b1 = smem + N;
-    __shared__ int colmin[kTileAW];
+    const int f = find_frame<true>(frames, n_frames, unit);
+    const FrameDesc& fd = frames[f];
+    const int H = fd.H, W = fd.W, in_pitch = fd.in_pitch;
+    const float* __restrict__ src = fd.in;
+    const int local = unit - fd.base_a;
+    const int band = local / fd.tiles_x_a, strip = local - band * fd.tiles_x_a;
+    const int r0 = band * fd.band_a, r1 = min(r0 + fd.band_a, H);
+    const int sx = strip * OW - Rh;            // frame column of strip column 0
+    const int cx = sx + lane * kV;             // frame column of this lane's first column
+    const bool edge = sx < 0 || sx + kSW > W;  // strip crosses a frame edge
+    bool col_in[kV], col_out[kV];
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
+        const int c = cx + v, j = lane * kV + v;
+        col_in[v] = c >= 0 && c < W;
+        col_out[v] = col_in[v] && j >= Rh && j < Rh + OW;
+    }
 
-    const int tid = threadIdx.x;
+    FirstDilation<S> s2;
+    Square5<true> s3d;
+    Square5<false> s3e;
+    Fill7 s4;
+    s2.init();
+    s3d.init(ninf());
+    s3e.init(pinf());
+    s4.init();
+    int top_row[kV];
+#pragma unroll
+    for (int v = 0; v < kV; ++v) top_row[v] = INT_MAX;
+    bool tops_pending = (stop == kStopFull);
 
-    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-        __syncthreads();  // previous tile fully consumed
-        const int f = find_frame<true>(frames, n_frames, t);
-        const FrameDesc fd = frames[f];
-        const int local = t - fd.base_a;
-        const int ty = local / fd.tiles_x_a, tx = local - ty * fd.tiles_x_a;
-        const int oy = ty * kTileAH - R, ox = tx * kTileAW - R;  // buffer origin
-        const int H = fd.H, W = fd.W;
-        auto inside = [&](int by, int bx) {
-            const int y = oy + by, x = ox + bx;
-            return y >= 0 && y < H && x >= 0 && x < W;
-        };
+    const int t0 = r0 - Rh;
+    const int nsteps = (r1 - r0) + 2 * Rh;
+    float raw[4][kV];
+    auto load_row = [&](int t, float (&d)[kV]) {
+#pragma unroll
+        for (int v = 0; v < kV; ++v) d[v] = 0.0f;
+        if (t >= 0 && t < H) {
+            const float* p = src + (size_t)t * in_pitch + cx;
+#pragma unroll
+            for (int v = 0; v < kV; ++v)
+                if (col_in[v]) d[v] = __ldcs(p + v);
+        }
+    };
+#pragma unroll
+    for (int q = 0; q < 4; ++q) load_row(t0 + q, raw[q]);
 
-        if (tid < kTileAW) colmin[tid] = INT_MAX;
+    auto step = [&](auto phi, int u0) {
+        constexpr int PHI = decltype(phi)::value;
+        const int t = t0 + u0 + PHI;
+        // step 1
+        Row x;
+        const bool row_in = t >= 0 && t < H;
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const float d = raw[PHI][v];
+            const float inv = (d >= kEmptyBelow) ? __fsub_rn(kInvertFrom, d) : 0.0f;
+            x.v[v] = (row_in && (!edge || col_in[v])) ? inv : ninf();
+        }
+        load_row(t + 4, raw[PHI]);
+        // step 2: row t -> A(t - R1)
+        Row a;
+        s2.template push<PHI>(x, a.v);
+        const int ra = t - R1;
+        const bool a_in = ra >= 0 && ra < H;
+#pragma unroll
+        for (int v = 0; v < kV; ++v)
+            if (!a_in || (edge && !col_in[v])) a.v[v] = ninf();
+        // step 3, dilation: A(ra) -> D(ra - 2)
+        Row dd;
+        s3d.template push<PHI>(a, dd.v);
+        const int rd = ra - 2;
+        const bool d_in = rd >= 0 && rd < H;
+#pragma unroll
+        for (int v = 0; v < kV; ++v)
+            if (!d_in || (edge && !col_in[v])) dd.v[v] = pinf();
+        // step 3, erosion: D(rd) -> B(rd - 2)
+        Row b;
+        s3e.template push<PHI>(dd, b.v);
+        const int rb = rd - 2;
+        const bool b_in = rb >= 0 && rb < H;
+#pragma unroll
+        for (int v = 0; v < kV; ++v)
+            if (!b_in || (edge && !col_in[v])) b.v[v] = ninf();
+        // step 4: B(rb) -> C(rb - 3)
+        float c[kV];
+        s4.template push<PHI>(b, c);
+        const int rc = rb - 3;  // == t - Rh
+        if (stop == kStopFull) {
+            if (rc >= r0 && rc < r1) {
+                float* dst = fd.c + (size_t)rc * fd.c_pitch + cx;
+#pragma unroll
+                for (int v = 0; v < kV; ++v)
+                    if (col_out[v]) dst[v] = c[v];
+                if (tops_pending) {
+                    bool left = false;
+#pragma unroll
+                    for (int v = 0; v < kV; ++v) {
+                        if (col_out[v] && !is_empty(c[v]) && top_row[v] == INT_MAX) top_row[v] = rc;
+                        left |= col_out[v] && top_row[v] == INT_MAX;
+                    }
+                    tops_pending = __any_sync(0xffffffffu, left);
+                }
+            }
+        } else {
+            // a stop before step 5: the requested map, row by row, to the output
+            int r = rc;
+            float val[kV];
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                val[v] = c[v];
+                if (stop == kStopInvert) val[v] = x.v[v];
+                if (stop == kStopDilate) val[v] = a.v[v];
+                if (stop == kStopClose) val[v] = b.v[v];
+            }
+            if (stop == kStopInvert) r = t;
+            if (stop == kStopDilate) r = ra;
+            if (stop == kStopClose) r = rb;
+            if (r >= r0 && r < r1) {
+                float* dst = fd.out + (size_t)r * fd.out_pitch + cx;
+#pragma unroll
+                for (int v = 0; v < kV; ++v)
+                    if (col_out[v]) dst[v] = val[v];
+            }
+        }
+    };
 
-        // P0, step 1: invert valid depths into b0; out-of-frame -> -inf
-        for (int i = tid; i < N; i += kThreadsA) {
-            const int by = i / BW, bx = i - by * BW;
-            float v = ninf();
-            if (inside(by, bx)) {
-                const float d = fd.in[(size_t)(oy + by) * fd.in_pitch + (ox + bx)];
-                v = (d >= kEmptyBelow) ? __fsub_rn(kInvertFrom, d) : 0.0f;
-            }
-            b0[i] = v;
-        }
-        __syncthreads();
-
-        auto emit = [&](const float* buf) {  // write the tile region of buf to out
-            for (int i = tid; i < kTileAH * kTileAW; i += kThreadsA) {
-                const int ly = i / kTileAW, lx = i - ly * kTileAW;
-                const int by = ly + R, bx = lx + R;
-                if (inside(by, bx))
-                    fd.out[(size_t)(oy + by) * fd.out_pitch + (ox + bx)] = buf[by * BW + bx];
-            }
-        };
-        if (stop == kStopInvert) { emit(b0); continue; }
-
-        // P1, step 2: first dilation b0 -> b1 on [R1, BH-R1) x [R1, BW-R1)
-        for (int i = tid; i < N; i += kThreadsA) {
-            const int by = i / BW, bx = i - by * BW;
-            if (by < R1 || by >= BH - R1 || bx < R1 || bx >= BW - R1) continue;
-            float m = ninf();
-            if (inside(by, bx)) {
-                m = b0[i];
+    for (int u0 = 0; u0 < nsteps; u0 += 4) {
+        step(std::integral_constant<int, 0>{}, u0);
+        step(std::integral_constant<int, 1>{}, u0);
+        step(std::integral_constant<int, 2>{}, u0);
+        step(std::integral_constant<int, 3>{}, u0);
+    }
+    if (stop == kStopFull) {
 #pragma unroll
-                for (int dy = -R1; dy <= R1; ++dy)
-#pragma unroll
-                    for (int dx = -R1; dx <= R1; ++dx)
-                        if (in_shape<S>(dy, dx)) m = fmaxf(m, b0[i + dy * BW + dx]);
-            }
-            b1[i] = m;
-        }
-        __syncthreads();
-        if (stop == kStopDilate) { emit(b1); continue; }
-
-        // P2, step 3a rows: max over 5 columns, b1 -> b0
-        for (int i = tid; i < N; i += kThreadsA) {
-            const int by = i / BW, bx = i - by * BW;
-            if (by < R1 || by >= BH - R1 || bx < R1 + 2 || bx >= BW - R1 - 2) continue;
-            float m = ninf();
-            if (inside(by, bx)) {
-                m = b1[i];
-#pragma unroll
-                for (int dx = -2; dx <= 2; ++dx) m = fmaxf(m, b1[i + dx]);
-            }
-            b0[i] = m;
-        }
-        __syncthreads();
-        // P3, step 3a columns: max over 5 rows, b0 -> b1 (D; out-of-frame +inf)
-        for (int i = tid; i < N; i += kThreadsA) {
-            const int by = i / BW, bx = i - by * BW;
-            if (by < R1 + 2 || by >= BH - R1 - 2 || bx < R1 + 2 || bx >= BW - R1 - 2) continue;
-            float m = pinf();
-            if (inside(by, bx)) {
-                m = b0[i];
-#pragma unroll
-                for (int dy = -2; dy <= 2; ++dy) m = fmaxf(m, b0[i + dy * BW]);
-            }
-            b1[i] = m;
-        }
-        __syncthreads();
-        // P4, step 3b rows: min over 5 columns, b1 -> b0
-        for (int i = tid; i < N; i += kThreadsA) {
-            const int by = i / BW, bx = i - by * BW;
-            if (by < R1 + 2 || by >= BH - R1 - 2 || bx < R1 + 4 || bx >= BW - R1 - 4) continue;
-            float m = pinf();
-            if (inside(by, bx)) {
-                m = b1[i];
-#pragma unroll
-                for (int dx = -2; dx <= 2; ++dx) m = fminf(m, b1[i + dx]);
-            }
-            b0[i] = m;
-        }
-        __syncthreads();
-        // P5, step 3b columns: min over 5 rows, b0 -> b1 (B; out-of-frame -inf)
-        for (int i = tid; i < N; i += kThreadsA) {
-            const int by = i / BW, bx = i - by * BW;
-            if (by < R1 + 4 || by >= BH - R1 - 4 || bx < R1 + 4 || bx >= BW - R1 - 4) continue;
-            float m = ninf();
-            if (inside(by, bx)) {
-                m = b0[i];
-#pragma unroll
-                for (int dy = -2; dy <= 2; ++dy) m = fminf(m, b0[i + dy * BW]);
-            }
-            b1[i] = m;
-        }
-        __syncthreads();
-        if (stop == kStopClose) { emit(b1); continue; }
-        // P6, step 4 rows: max over 7 columns, b1 -> b0
-        for (int i = tid; i < N; i += kThreadsA) {
-            const int by = i / BW, bx = i - by * BW;
-            if (by < R1 + 4 || by >= BH - R1 - 4 || bx < R || bx >= BW - R) continue;
-            float m = ninf();
-            if (inside(by, bx)) {
-                m = b1[i];
-#pragma unroll
-                for (int dx = -3; dx <= 3; ++dx) m = fmaxf(m, b1[i + dx]);
-            }
-            b0[i] = m;
-        }
-        __syncthreads();
-        // P7, step 4 columns + fill of empty pixels only: C on the tile
-        const bool to_out = (stop == kStopFill7);
-        for (int i = tid; i < kTileAH * kTileAW; i += kThreadsA) {
-            const int ly = i / kTileAW, lx = i - ly * kTileAW;
-            const int by = ly + R, bx = lx + R;
-            if (!inside(by, bx)) continue;
-            const int j = by * BW + bx;
-            float c = b1[j];
-            if (is_empty(c)) {
-                float m = b0[j];
-#pragma unroll
-                for (int dy = -3; dy <= 3; ++dy) m = fmaxf(m, b0[j + dy * BW]);
-                c = m;
-            }
-            const int y = oy + by, x = ox + bx;
-            if (to_out) {
-                fd.out[(size_t)y * fd.out_pitch + x] = c;
-            } else {
-                fd.c[(size_t)y * fd.c_pitch + x] = c;
-                if (!is_empty(c)) atomicMin(&colmin[lx], y);
-            }
-        }
-        if (!to_out) {
-            __syncthreads();
-            if (tid < kTileAW && colmin[tid] != INT_MAX) atomicMin(&fd.top[ox + R + tid], colmin[tid]);
-        }
+        for (int v = 0; v < kV; ++v)
+            if (col_out[v] && top_row[v] != INT_MAX) atomicMin(&fd.top[cx + v], top_row[v]);
     }
 }
 
 template <int S>
-cudaError_t launch_shape(const FrameDesc* d_frames, int n_frames, int total_tiles, int stop,
-                         int* worklist, int sm_count, cudaStream_t stream)
+cudaError_t launch_shape(const FrameDesc* d_frames, int n_frames, int total_units, int stop, int* worklist,
+                         cudaStream_t stream)
 {
-    constexpr int R = ShapeInfo<S>::r + 7;
-    const size_t smem = 2u * sizeof(float) * (kTileAH + 2 * R) * (kTileAW + 2 * R);
-    static int configured_dev = -1;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (configured_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(stage_a_kernel<S>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured_dev = dev;
-    }
-    int grid = total_tiles;
-    const int cap = sm_count * 8;
-    if (grid > cap) grid = cap;
+    const int per_block = kThreadsA / 32;
+    const int grid = (total_units + per_block - 1) / per_block;
     if (grid < 1) return cudaSuccess;
-    stage_a_kernel<S><<<grid, kThreadsA, smem, stream>>>(d_frames, n_frames, total_tiles, stop, worklist);
+    stage_a_stream<S><<<grid, kThreadsA, 0, stream>>>(d_frames, n_frames, total_units, stop, worklist);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_tiles, int shape,
-                           int stop, int* worklist, int sm_count, cudaStream_t stream)
+int stage_a_halo(int shape)
 {
+    return shape == kFull3 ? 8 : (shape == kFull7 ? 10 : 9);
+}
+
+int stage_a_strip_width(int shape) { return kSW - 2 * stage_a_halo(shape); }
+
+int stage_a_band_rows(int H, long long total_strips, int sm_count)
+{
+    const long long target = 12LL * (sm_count > 0 ? sm_count : 1);  // warps in flight
+    long long bands = total_strips > 0 ? (target + total_strips - 1) / total_strips : 1;
+    if (bands < 1) bands = 1;
+    long long rows = (H + bands - 1) / bands;
+    if (rows < 32) rows = 32;
+    return (int)rows;
+}
+
+cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_units, int shape, int stop,
+                           int* worklist, int sm_count, cudaStream_t stream)
+{
+    (void)sm_count;
     switch (shape) {
-    case kDiamond5: return launch_shape<kDiamond5>(d_frames, n_frames, total_tiles, stop, worklist, sm_count, stream);
-    case kFull5: return launch_shape<kFull5>(d_frames, n_frames, total_tiles, stop, worklist, sm_count, stream);
-    case kCross5: return launch_shape<kCross5>(d_frames, n_frames, total_tiles, stop, worklist, sm_count, stream);
-    case kFull3: return launch_shape<kFull3>(d_frames, n_frames, total_tiles, stop, worklist, sm_count, stream);
-    case kCircle5: return launch_shape<kCircle5>(d_frames, n_frames, total_tiles, stop, worklist, sm_count, stream);
-    case kFull7: return launch_shape<kFull7>(d_frames, n_frames, total_tiles, stop, worklist, sm_count, stream);
+    case kDiamond5: return launch_shape<kDiamond5>(d_frames, n_frames, total_units, stop, worklist, stream);
+    case kFull5: return launch_shape<kFull5>(d_frames, n_frames, total_units, stop, worklist, stream);
+    case kCross5: return launch_shape<kCross5>(d_frames, n_frames, total_units, stop, worklist, stream);
+    case kFull3: return launch_shape<kFull3>(d_frames, n_frames, total_units, stop, worklist, stream);
+    case kCircle5: return launch_shape<kCircle5>(d_frames, n_frames, total_units, stop, worklist, stream);
+    case kFull7: return launch_shape<kFull7>(d_frames, n_frames, total_units, stop, worklist, stream);
     default: return cudaErrorInvalidValue;
     }
 }
