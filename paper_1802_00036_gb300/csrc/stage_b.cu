@@ -266,11 +266,36 @@ __device__ float large_fill_at(const Tile& T, const StageBParams& p, int y, int 
 // Empty pixels a tile fills itself; more go to the worklist (phase 2).
 constexpr int kMaxSparseFill = 160;
 
-// Phase 1: every tile.  A tile whose median input holds at most
-// kMaxSparseFill empty pixels fills them itself (step 6, pixel by pixel);
-// a tile with more goes to the worklist.
+// The median input region as 16-byte chunks: kER rows x kChunksPerRow.  The
+// region's first column x0 - 4 is a multiple of 4 (tiles start at multiples
+// of 60) and rows of C are 128-byte aligned, so every chunk is aligned.
+constexpr int kChunksPerRow = kEC / 4;
+constexpr int kChunks = kER * kChunksPerRow;
+constexpr int kChunksPerThread = (kChunks + kThreadsB - 1) / kThreadsB;
+static_assert(kEC % 4 == 0 && kTBW % 4 == 0, "chunked region");
+
+// Prefetch a tile's region of C into registers: the in-frame chunks (a chunk
+// straddling the right edge reads the row padding of C, which is allocated).
+__device__ __forceinline__ void prefetch_region(const Tile& T, float4 (&pre)[kChunksPerThread])
+{
+#pragma unroll
+    for (int j = 0; j < kChunksPerThread; ++j) {
+        const int ch = threadIdx.x + j * kThreadsB;
+        const int k = ch / kChunksPerRow, q = ch - k * kChunksPerRow;
+        const int y = T.y0 - 4 + k, xs = T.x0 - 4 + 4 * q;
+        if (ch < kChunks && y >= 0 && y < T.fd.H && xs >= 0 && xs < T.fd.W)
+            pre[j] = __ldcg(reinterpret_cast<const float4*>(T.fd.c + (size_t)y * T.fd.c_pitch + xs));
+    }
+}
+
+// Phase 1, persistent: each CTA walks tiles blockIdx.x, + gridDim.x, ...,
+// prefetching the next tile's region and column tops into registers while
+// it computes the current one.  A tile whose median input holds at most
+// kMaxSparseFill empty pixels fills them itself (step 6, pixel by pixel); a
+// tile with more goes to the worklist.
 __global__ void __launch_bounds__(kThreadsB, 2)
-stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p, int* __restrict__ worklist)
+stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles, StageBParams p,
+             int* __restrict__ worklist)
 {
     __shared__ __align__(16) float E[kER * kES];
     __shared__ __align__(16) float M[kMR * kMS];
@@ -280,64 +305,113 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
     __shared__ int ecount;
     float* R = E;  // the Gaussian row pass reuses E once the median has read it
 
-    const Tile T = tile_of(frames, n_frames, blockIdx.x);
-    const int H = T.fd.H, W = T.fd.W;
     const int tid = threadIdx.x;
-    if (tid == 0) ecount = 0;
+    int t = blockIdx.x;
+    if (t >= total_tiles) return;
+    Tile T = tile_of(frames, n_frames, t);
+    float4 pre[kChunksPerThread];
+    prefetch_region(T, pre);
     load_tops(T, p, T.x0 - 4, kEC, ctop, cval);
+    if (tid == 0) ecount = 0;
     __syncthreads();
-    // step 5 while loading the in-frame part of tile + 4; note empty pixels
-    for (int i = tid; i < kER * kEC; i += kThreadsB) {
-        const int k = i / kEC, l = i - k * kEC;
-        const int y = T.y0 - 4 + k, x = T.x0 - 4 + l;
-        if (y < 0 || y >= H || x < 0 || x >= W) continue;
-        const float e = extended(T, p, y, x, ctop[l], cval[l]);
-        E[k * kES + l] = e;
-        if (p.large_fill_on && is_empty(e)) {
-            const int j = atomicAdd(&ecount, 1);
-            if (j < kMaxSparseFill) elist[j] = (k << 16) | l;
-        }
-    }
-    __syncthreads();
-    const int n_empty = ecount;
-    auto store_tile = [&](const float* buf) {
-        for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
-            const int a = i / kTBW, b = i - a * kTBW;
-            const int y = T.y0 + a, x = T.x0 + b;
-            if (y < H && x < W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = buf[(a + 4) * kES + b + 4];
-        }
-    };
-    if (p.stop == kStopExtend) { store_tile(E); return; }
-    if (n_empty > kMaxSparseFill) {
-        if (tid == 0) {
-            const int slot = atomicAdd(worklist, 1);
-            worklist[1 + slot] = blockIdx.x;
-        }
-        return;
-    }
-    if (n_empty > 0) {  // step 6 at the few empty pixels, one warp each
-        // E is only written here (at empty pixels); large_fill_at reads C
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int j = warp; j < n_empty; j += kThreadsB / 32) {
-            const int k = elist[j] >> 16, l = elist[j] & 0xFFFF;
-            const float m = large_fill_at(T, p, T.y0 - 4 + k, T.x0 - 4 + l, lane);
-            if (lane == 0) E[k * kES + l] = m;
+
+    while (true) {
+        const int H = T.fd.H, W = T.fd.W;
+        // step 5 while storing the prefetched region; note empty pixels
+#pragma unroll
+        for (int j = 0; j < kChunksPerThread; ++j) {
+            const int ch = tid + j * kThreadsB;
+            const int k = ch / kChunksPerRow, q = ch - k * kChunksPerRow;
+            const int y = T.y0 - 4 + k, xs = T.x0 - 4 + 4 * q;
+            if (ch < kChunks && y >= 0 && y < H && xs >= 0 && xs < W) {
+                const float raw[4] = {pre[j].x, pre[j].y, pre[j].z, pre[j].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int l = 4 * q + e;
+                    if (xs + e >= W) break;
+                    const int top = ctop[l];
+                    const bool above = (top != kNoTop) && y < top &&
+                                       (p.extend_rows < 0 || y >= top - p.extend_rows);
+                    const float v = above ? cval[l] : raw[e];
+                    E[k * kES + l] = v;
+                    if (p.large_fill_on && is_empty(v)) {
+                        const int slot = atomicAdd(&ecount, 1);
+                        if (slot < kMaxSparseFill) elist[slot] = (k << 16) | l;
+                    }
+                }
+            }
         }
         __syncthreads();
-    }
-    // replicate the frame border into the out-of-frame part (the median's rule)
-    if (T.y0 < 4 || T.x0 < 4 || T.y0 + kTBH + 4 > H || T.x0 + kTBW + 4 > W) {
-        for (int i = tid; i < kER * kEC; i += kThreadsB) {
-            const int k = i / kEC, l = i - k * kEC;
-            const int y = T.y0 - 4 + k, x = T.x0 - 4 + l;
-            if (y >= 0 && y < H && x >= 0 && x < W) continue;
-            const int sk = clampi(y, H) - (T.y0 - 4), sl = clampi(x, W) - (T.x0 - 4);
-            E[i] = E[sk * kES + sl];
+        const int n_empty = ecount;
+
+        // prefetch the next tile while this one is computed
+        const int tn = t + gridDim.x;
+        const bool more = tn < total_tiles;
+        Tile Tn = T;
+        int ntop = kNoTop;
+        if (more) {
+            Tn = tile_of(frames, n_frames, tn);
+            prefetch_region(Tn, pre);
+            if (tid < kEC && p.extend_top) {
+                const int t2 = __ldcg(Tn.fd.top + clampi(Tn.x0 - 4 + tid, Tn.fd.W));
+                ntop = t2 < Tn.fd.H ? t2 : kNoTop;
+            }
         }
+
+        auto store_tile = [&](const float* buf) {
+            for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
+                const int a = i / kTBW, b = i - a * kTBW;
+                const int y = T.y0 + a, x = T.x0 + b;
+                if (y < H && x < W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = buf[(a + 4) * kES + b + 4];
+            }
+        };
+        if (p.stop == kStopExtend) {
+            store_tile(E);
+        } else if (n_empty > kMaxSparseFill) {
+            if (tid == 0) {
+                const int slot = atomicAdd(worklist, 1);
+                worklist[1 + slot] = t;
+            }
+        } else {
+            if (n_empty > 0) {  // step 6 at the few empty pixels, one warp each
+                // E is only written here (at empty pixels); large_fill_at reads C
+                const int warp = tid >> 5, lane = tid & 31;
+                for (int j = warp; j < n_empty; j += kThreadsB / 32) {
+                    const int k = elist[j] >> 16, l = elist[j] & 0xFFFF;
+                    const float m = large_fill_at(T, p, T.y0 - 4 + k, T.x0 - 4 + l, lane);
+                    if (lane == 0) E[k * kES + l] = m;
+                }
+                __syncthreads();
+            }
+            // replicate the frame border into the out-of-frame part (the median's rule)
+            if (T.y0 < 4 || T.x0 < 4 || T.y0 + kTBH + 4 > H || T.x0 + kTBW + 4 > W) {
+                for (int i = tid; i < kER * kEC; i += kThreadsB) {
+                    const int k = i / kEC, l = i - k * kEC;
+                    const int y = T.y0 - 4 + k, x = T.x0 - 4 + l;
+                    if (y >= 0 && y < H && x >= 0 && x < W) continue;
+                    const int sk = clampi(y, H) - (T.y0 - 4), sl = clampi(x, W) - (T.x0 - 4);
+                    E[i] = E[sk * kES + sl];
+                }
+                __syncthreads();
+            }
+            if (p.stop == kStopFillLarge) store_tile(E);
+            else median_blur_store(T, p, E, M, R);
+        }
+
+        float ntopval = 0.0f;
+        if (more && tid < kEC && ntop != kNoTop)
+            ntopval = __ldcg(Tn.fd.c + (size_t)ntop * Tn.fd.c_pitch + clampi(Tn.x0 - 4 + tid, Tn.fd.W));
+        __syncthreads();  // E, M, ctop of this tile no longer read
+        if (!more) break;
+        if (tid < kEC) {
+            ctop[tid] = ntop;
+            cval[tid] = ntopval;
+        }
+        if (tid == 0) ecount = 0;
+        T = Tn;
+        t = tn;
         __syncthreads();
     }
-    if (p.stop == kStopFillLarge) { store_tile(E); return; }
-    median_blur_store(T, p, E, M, R);
 }
 
 // Phase 2: tiles from the worklist, with step 6.
@@ -429,7 +503,8 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
         configured_dev = dev;
     }
     if (total_tiles < 1) return cudaSuccess;
-    stage_b_main<<<total_tiles, kThreadsB, 0, stream>>>(d_frames, n_frames, p, worklist);
+    const int main_grid = total_tiles < 2 * sm_count ? total_tiles : 2 * sm_count;
+    stage_b_main<<<main_grid, kThreadsB, 0, stream>>>(d_frames, n_frames, total_tiles, p, worklist);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !p.large_fill_on || p.stop == kStopExtend) return e;
     int grid = 2 * sm_count;
