@@ -67,6 +67,48 @@ struct Tile {
     int y0, x0;  // first output pixel
 };
 
+// Positions of a rows x cols region (origin at tile pixel - w) that lie
+// outside the frame but within w of it: up to w rows above and below (all
+// columns), and up to w columns left and right of the in-frame rows.
+struct Ring {
+    int top, bot0, bot1, left, right0, right1, rows, cols, in0, in1;
+    __device__ __forceinline__ int count() const
+    {
+        return (top + (bot1 - bot0)) * cols + (left + (right1 - right0)) * (in1 - in0);
+    }
+    __device__ __forceinline__ void at(int i, int& a, int& b) const
+    {
+        const int nr = (top + (bot1 - bot0)) * cols;
+        if (i < nr) {
+            const int r = i / cols;
+            b = i - r * cols;
+            a = r < top ? r : bot0 + (r - top);
+        } else {
+            i -= nr;
+            const int span = in1 - in0;
+            const int c = i / span;
+            a = in0 + (i - c * span);
+            b = c < left ? c : right0 + (c - left);
+        }
+    }
+};
+
+__device__ __forceinline__ Ring ring_of(const Tile& T, int w, int rows, int cols)
+{
+    Ring r;
+    r.rows = rows;
+    r.cols = cols;
+    r.top = T.y0 < w ? w - T.y0 : 0;                 // region rows [0, top) are above the frame
+    r.bot0 = min(T.fd.H - T.y0 + w, rows);           // first region row below the frame
+    r.bot1 = min(r.bot0 + w, rows);
+    r.left = T.x0 < w ? w - T.x0 : 0;
+    r.right0 = min(T.fd.W - T.x0 + w, cols);
+    r.right1 = min(r.right0 + w, cols);
+    r.in0 = r.top;                                   // in-frame region rows
+    r.in1 = r.bot0;
+    return r;
+}
+
 __device__ __forceinline__ Tile tile_of(const FrameDesc* __restrict__ frames, int n_frames, int t)
 {
     Tile T;
@@ -148,17 +190,18 @@ __device__ void median_blur_store(const Tile& T, const StageBParams& p, const fl
         }
     }
     __syncthreads();
-    // -- mirror the ring outside the frame (the blur's reflect-101 border)
+    // -- mirror the ring outside the frame (the blur's reflect-101 border):
+    // only the two rows / columns beyond each edge are read by the blur
     const bool edge = T.y0 < 2 || T.x0 < 2 || T.y0 + kTBH + 2 > H || T.x0 + kTBW + 2 > W;
     if (edge) {
-        for (int i = tid; i < kMR * kMC; i += kThreadsB) {
-            const int a = i / kMC, b = i - a * kMC;
+        Ring ring = ring_of(T, 2, kMR, kMC);
+        for (int i = tid; i < ring.count(); i += kThreadsB) {
+            int a, b;
+            ring.at(i, a, b);
             const int y = T.y0 - 2 + a, x = T.x0 - 2 + b;
-            const bool in = y >= 0 && y < H && x >= 0 && x < W;
-            if (!in && y >= -2 && y < H + 2 && x >= -2 && x < W + 2) {
-                const int sy = reflect101(y, H) - (T.y0 - 2), sx = reflect101(x, W) - (T.x0 - 2);
-                M[a * kMS + b] = M[sy * kMS + sx];
-            }
+            if (y < -2 || y >= H + 2 || x < -2 || x >= W + 2) continue;
+            const int sy = reflect101(y, H) - (T.y0 - 2), sx = reflect101(x, W) - (T.x0 - 2);
+            M[a * kMS + b] = M[sy * kMS + sx];
         }
         __syncthreads();
     }
@@ -175,10 +218,9 @@ __device__ void median_blur_store(const Tile& T, const StageBParams& p, const fl
         // row pass over all kMR rows of M, the tile's kTBW columns -> R
         for (int i = tid; i < kMR * (kTBW / 4); i += kThreadsB) {
             const int a = i / (kTBW / 4), b0 = 4 * (i - a * (kTBW / 4));
-            const float* s = M + a * kMS + b0;
-            float v[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = s[k];
+            const float4 lo = *reinterpret_cast<const float4*>(M + a * kMS + b0);
+            const float4 hi = *reinterpret_cast<const float4*>(M + a * kMS + b0 + 4);
+            const float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
             float o[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -193,43 +235,58 @@ __device__ void median_blur_store(const Tile& T, const StageBParams& p, const fl
         }
         __syncthreads();
     }
-    // column pass / bilateral, masked by the median, inverted, stored
-    for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
-        const int a = i / kTBW, b = i - a * kTBW;
-        const int y = T.y0 + a, x = T.x0 + b;
-        if (y >= H || x >= W) continue;
-        const float m = M[(a + 2) * kMS + b + 2];
-        float g = m;
-        if (!is_empty(m)) {
-            if (p.blur == kBlurGauss) {
-                const float* s = R + a * kRS + b;
-                float acc = w0 * s[0];
-                acc = fmaf(w1, s[kRS], acc);
-                acc = fmaf(w2, s[2 * kRS], acc);
-                acc = fmaf(w1, s[3 * kRS], acc);
-                acc = fmaf(w0, s[4 * kRS], acc);
-                g = acc;
-            } else if (p.blur == kBlurBilateral) {
-                float num = 0.0f, den = 0.0f;
+    // column pass / bilateral, masked by the median, inverted, stored: each
+    // thread takes kStripRows rows of one column
+    constexpr int kStrips = kThreadsB / 64;
+    constexpr int kStripRows = kTBH / kStrips;
+    static_assert(kTBW <= 64 && kTBH % kStrips == 0, "column-pass mapping");
+    const int b = tid & 63, a0 = (tid >> 6) * kStripRows;
+    const int x = T.x0 + b;
+    if (b < kTBW && x < W) {
+        if (p.blur == kBlurGauss) {
+            float r[kStripRows + 4];
 #pragma unroll
-                for (int dy = -2; dy <= 2; ++dy)
+            for (int k = 0; k < kStripRows + 4; ++k) r[k] = R[(a0 + k) * kRS + b];
 #pragma unroll
-                    for (int dx = -2; dx <= 2; ++dx) {
-                        const int r2 = dy * dy + dx * dx;
-                        if (r2 > 4) continue;
-                        const float v = M[(a + 2 + dy) * kMS + b + 2 + dx];
-                        const float d = v - m;
-                        const float wgt = p.ws[r2] * expf(-(d * d) * p.inv_2sc2);
-                        num = fmaf(v, wgt, num);
-                        den += wgt;
-                    }
-                g = num / den;
+            for (int k = 0; k < kStripRows; ++k) {
+                const int y = T.y0 + a0 + k;
+                if (y >= H) break;
+                const float m = M[(a0 + k + 2) * kMS + b + 2];
+                float acc = w0 * r[k];
+                acc = fmaf(w1, r[k + 1], acc);
+                acc = fmaf(w2, r[k + 2], acc);
+                acc = fmaf(w1, r[k + 3], acc);
+                acc = fmaf(w0, r[k + 4], acc);
+                const float g = is_empty(m) ? m : acc;
+                const float o = (p.stop == kStopBlur) ? g : (is_empty(m) ? 0.0f : __fsub_rn(kInvertFrom, g));
+                T.fd.out[(size_t)y * T.fd.out_pitch + x] = o;
+            }
+        } else {
+            for (int k = 0; k < kStripRows; ++k) {
+                const int a = a0 + k, y = T.y0 + a;
+                if (y >= H) break;
+                const float m = M[(a + 2) * kMS + b + 2];
+                float g = m;
+                if (!is_empty(m) && p.blur == kBlurBilateral) {
+                    float num = 0.0f, den = 0.0f;
+#pragma unroll
+                    for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+                        for (int dx = -2; dx <= 2; ++dx) {
+                            const int r2 = dy * dy + dx * dx;
+                            if (r2 > 4) continue;
+                            const float v = M[(a + 2 + dy) * kMS + b + 2 + dx];
+                            const float d = v - m;
+                            const float wgt = p.ws[r2] * expf(-(d * d) * p.inv_2sc2);
+                            num = fmaf(v, wgt, num);
+                            den += wgt;
+                        }
+                    g = num / den;
+                }
+                const float o = (p.stop == kStopBlur) ? g : (is_empty(m) ? 0.0f : __fsub_rn(kInvertFrom, g));
+                T.fd.out[(size_t)y * T.fd.out_pitch + x] = o;
             }
         }
-        float o;
-        if (p.stop == kStopBlur) o = g;
-        else o = is_empty(m) ? 0.0f : __fsub_rn(kInvertFrom, g);
-        T.fd.out[(size_t)y * T.fd.out_pitch + x] = o;
     }
 }
 
@@ -314,6 +371,8 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
     load_tops(T, p, T.x0 - 4, kEC, ctop, cval);
     if (tid == 0) ecount = 0;
     __syncthreads();
+    // does step 5 reach this tile's region (some column's top below its first row)?
+    bool ext_tile = __syncthreads_or(tid < kEC && ctop[tid] != kNoTop && ctop[tid] > T.y0 - 4);
 
     while (true) {
         const int H = T.fd.H, W = T.fd.W;
@@ -324,19 +383,33 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
             const int k = ch / kChunksPerRow, q = ch - k * kChunksPerRow;
             const int y = T.y0 - 4 + k, xs = T.x0 - 4 + 4 * q;
             if (ch < kChunks && y >= 0 && y < H && xs >= 0 && xs < W) {
-                const float raw[4] = {pre[j].x, pre[j].y, pre[j].z, pre[j].w};
+                if (!ext_tile && xs + 4 <= W) {
+                    *reinterpret_cast<float4*>(E + k * kES + 4 * q) = pre[j];
+                    if (p.large_fill_on && (is_empty(pre[j].x) || is_empty(pre[j].y) || is_empty(pre[j].z) ||
+                                            is_empty(pre[j].w))) {
+                        const float raw[4] = {pre[j].x, pre[j].y, pre[j].z, pre[j].w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int l = 4 * q + e;
-                    if (xs + e >= W) break;
-                    const int top = ctop[l];
-                    const bool above = (top != kNoTop) && y < top &&
-                                       (p.extend_rows < 0 || y >= top - p.extend_rows);
-                    const float v = above ? cval[l] : raw[e];
-                    E[k * kES + l] = v;
-                    if (p.large_fill_on && is_empty(v)) {
-                        const int slot = atomicAdd(&ecount, 1);
-                        if (slot < kMaxSparseFill) elist[slot] = (k << 16) | l;
+                        for (int e = 0; e < 4; ++e)
+                            if (is_empty(raw[e])) {
+                                const int slot = atomicAdd(&ecount, 1);
+                                if (slot < kMaxSparseFill) elist[slot] = (k << 16) | (4 * q + e);
+                            }
+                    }
+                } else {
+                    const float raw[4] = {pre[j].x, pre[j].y, pre[j].z, pre[j].w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int l = 4 * q + e;
+                        if (xs + e >= W) break;
+                        const int top = ctop[l];
+                        const bool above = (top != kNoTop) && y < top &&
+                                           (p.extend_rows < 0 || y >= top - p.extend_rows);
+                        const float v = above ? cval[l] : raw[e];
+                        E[k * kES + l] = v;
+                        if (p.large_fill_on && is_empty(v)) {
+                            const int slot = atomicAdd(&ecount, 1);
+                            if (slot < kMaxSparseFill) elist[slot] = (k << 16) | l;
+                        }
                     }
                 }
             }
@@ -383,14 +456,18 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
                 }
                 __syncthreads();
             }
-            // replicate the frame border into the out-of-frame part (the median's rule)
-            if (T.y0 < 4 || T.x0 < 4 || T.y0 + kTBH + 4 > H || T.x0 + kTBW + 4 > W) {
-                for (int i = tid; i < kER * kEC; i += kThreadsB) {
-                    const int k = i / kEC, l = i - k * kEC;
+            // replicate the frame border into the two rows / columns beyond each
+            // edge (the median's rule; farther ones feed only mirrored outputs)
+            if (T.y0 < 2 || T.x0 < 2 || T.y0 + kTBH + 2 > H || T.x0 + kTBW + 2 > W) {
+                // region origin is tile - 4: the ring of width 2 starts 2 further in
+                Ring ring = ring_of(T, 4, kER, kEC);
+                for (int i = tid; i < ring.count(); i += kThreadsB) {
+                    int k, l;
+                    ring.at(i, k, l);
                     const int y = T.y0 - 4 + k, x = T.x0 - 4 + l;
-                    if (y >= 0 && y < H && x >= 0 && x < W) continue;
+                    if (y < -2 || y >= H + 2 || x < -2 || x >= W + 2) continue;
                     const int sk = clampi(y, H) - (T.y0 - 4), sl = clampi(x, W) - (T.x0 - 4);
-                    E[i] = E[sk * kES + sl];
+                    E[k * kES + l] = E[sk * kES + sl];
                 }
                 __syncthreads();
             }
@@ -410,7 +487,7 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
         if (tid == 0) ecount = 0;
         T = Tn;
         t = tn;
-        __syncthreads();
+        ext_tile = __syncthreads_or(tid < kEC && ntop != kNoTop && ntop > T.y0 - 4);
     }
 }
 
