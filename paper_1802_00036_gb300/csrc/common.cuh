@@ -28,7 +28,7 @@ constexpr int kThreadsA = 128;
 // Stage B output tile (median blocks of 2 x 8 over the tile + 2 ring).
 constexpr int kTileBH = 60;
 constexpr int kTileBW = 60;
-constexpr int kThreadsB = 256;
+constexpr int kThreadsB = 128;
 
 // Largest step-6 square side the kernels accept.
 constexpr int kMaxLargeFill = 63;

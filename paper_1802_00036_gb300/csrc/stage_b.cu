@@ -1,20 +1,26 @@
 // stage_b.cu -- steps 5-8 of arXiv 1802.00036, Section IV, fused per tile.
 //
-// Output tile kTBH x kTBW.  Phase 1 (every tile) loads the step-5 map E over
-// the tile plus a 4-pixel ring (median 2 + blur 2) into shared memory,
-// applying step 5 on the fly (a pixel above its column's top row takes
-// C(top, x), which is what copying the topmost value to row 0 gives).
-// Step 6 changes only empty pixels: a tile with a few of them in that region
-// fills each with one warp (the maximum over its (2 Rl + 1)^2 window, read
-// from C); a tile with many goes on a worklist for phase 2, which loads the
-// wider ring, takes row then column maxima and fills the empty pixels.  The
-// frame border is then replicated around the region (the median's rule).
-// Both phases then run the same tail:
+// Output tile kTBH x kTBW.  Phase 1 (persistent CTAs) brings the step-4 map
+// C over the tile plus a 4-pixel ring (median 2 + blur 2) into shared memory
+// with cp.async, one tile ahead, and applies step 5 in place (a pixel above
+// its column's top row takes C(top, x), which is what copying the topmost
+// value to row 0 gives).  Step 6 changes only empty pixels: a tile with a
+// few of them in that region fills each with one warp (the maximum over its
+// (2 Rl + 1)^2 window, read from C); a tile with many goes on a worklist for
+// phase 2, which loads the wider ring, takes row then column maxima and
+// fills the empty pixels.  The frame border is replicated around the region
+// (the median's rule).  Then:
 //   step 7  5x5 median on the tile + 2 ring by the generated network of
-//           median_net.cuh (2 x 8 outputs per thread), the ring mirrored
-//           (reflect-101) for the blur; then the Gaussian [1 4 6 4 1]/16 as
-//           a row pass and a column pass (FMA chains, dyadic weights), or
-//           the 13-tap bilateral; both only where the median is non-empty;
+//           median_net.cuh, two 2 x 8 output blocks per thread.  When every
+//           value of the tile is k/256 m for an integer k < 65536 (KITTI
+//           stores depth as 16-bit fixed point, depth x 256), the values are
+//           replaced by their 16-bit keys k -- an exact, order-preserving
+//           encoding -- and both blocks run at once in the two halves of
+//           32-bit registers (packed min/max, 3-input); otherwise the float
+//           network runs per block.  The ring is mirrored (reflect-101) for
+//           the blur; then the Gaussian [1 4 6 4 1]/16 as a row pass and a
+//           column pass (FMA chains, dyadic weights), or the 13-tap
+//           bilateral; both only where the median is non-empty;
 //   step 8  100 - value where the median is non-empty, 0 elsewhere.
 #include "common.cuh"
 #include "median_net.cuh"
@@ -28,12 +34,14 @@ constexpr int kMR = kTBH + 4;       // median region rows (tile + 2 ring)
 constexpr int kMC = kTBW + 4;       // median region columns
 constexpr int kER = kTBH + 8;       // median input rows (tile + 4 ring)
 constexpr int kEC = kTBW + 8;       // median input columns
-constexpr int kES = kEC;            // stride of the median input buffer
+constexpr int kES = kEC;            // stride of the median input buffers
 constexpr int kMS = kMC;            // stride of the median output buffer
 constexpr int kRS = kTBW;           // stride of the Gaussian row-pass buffer
-static_assert(kMR % 2 == 0 && kMC % 8 == 0, "median blocks are 2 x 8");
-static_assert((kMR / 2) * (kMC / 8) == kThreadsB, "one median block per thread");
-static_assert(kES % 4 == 0, "rows of the median input are 16-byte aligned");
+constexpr int kHalf = kMR / 2;      // median-region rows per block half (A: top, B: bottom)
+constexpr int kPR = kHalf + 4;      // packed key rows: input rows of one half
+static_assert(kMR % 4 == 0 && kMC % 8 == 0, "median blocks are 2 x 8, two per thread");
+static_assert((kHalf / 2) * (kMC / 8) == kThreadsB, "two median blocks per thread");
+static_assert(kES % 4 == 0 && kEC % 4 == 0 && kTBW % 4 == 0, "16-byte rows and chunks");
 
 struct FloatOps {
     static __device__ __forceinline__ float min2(float a, float b) { return fminf(a, b); }
@@ -51,6 +59,37 @@ struct FloatOps {
         return r;
     }
 };
+
+// Two unsigned 16-bit keys per register.
+struct PackedKeyOps {
+    static __device__ __forceinline__ unsigned min2(unsigned a, unsigned b) { return __vminu2(a, b); }
+    static __device__ __forceinline__ unsigned max2(unsigned a, unsigned b) { return __vmaxu2(a, b); }
+    static __device__ __forceinline__ unsigned min3(unsigned a, unsigned b, unsigned c)
+    {
+        return __vimin3_u16x2(a, b, c);
+    }
+    static __device__ __forceinline__ unsigned max3(unsigned a, unsigned b, unsigned c)
+    {
+        return __vimax3_u16x2(a, b, c);
+    }
+};
+
+// 16-bit key of v: k with v == k / 256 exactly, k < 65536; `ok` is cleared
+// when v has no such key.  fma(v, 256, 2^23) holds 2^23 + k exactly iff
+// v * 256 is an integer in [0, 2^23).
+__device__ __forceinline__ unsigned key_of(float v, bool& ok)
+{
+    const float scaled = v * 256.0f;
+    const unsigned kb = __float_as_uint(fmaf(v, 256.0f, 8388608.0f));
+    ok = ok && (kb >> 16) == 0x4B00u && (__uint_as_float(kb) - 8388608.0f) == scaled;
+    return kb & 0xFFFFu;
+}
+
+// The float value of a 16-bit key: exactly k / 256.
+__device__ __forceinline__ float value_of(unsigned k)
+{
+    return (__uint_as_float(0x4B000000u | k) - 8388608.0f) * 0.00390625f;
+}
 
 __device__ __forceinline__ int clampi(int p, int n) { return p < 0 ? 0 : (p >= n ? n - 1 : p); }
 
@@ -71,7 +110,7 @@ struct Tile {
 // outside the frame but within w of it: up to w rows above and below (all
 // columns), and up to w columns left and right of the in-frame rows.
 struct Ring {
-    int top, bot0, bot1, left, right0, right1, rows, cols, in0, in1;
+    int top, bot0, bot1, left, right0, right1, cols, in0, in1;
     __device__ __forceinline__ int count() const
     {
         return (top + (bot1 - bot0)) * cols + (left + (right1 - right0)) * (in1 - in0);
@@ -96,7 +135,6 @@ struct Ring {
 __device__ __forceinline__ Ring ring_of(const Tile& T, int w, int rows, int cols)
 {
     Ring r;
-    r.rows = rows;
     r.cols = cols;
     r.top = T.y0 < w ? w - T.y0 : 0;                 // region rows [0, top) are above the frame
     r.bot0 = min(T.fd.H - T.y0 + w, rows);           // first region row below the frame
@@ -142,51 +180,93 @@ __device__ __forceinline__ void load_tops(const Tile& T, const StageBParams& p, 
     }
 }
 
+__device__ __forceinline__ bool above_top(const StageBParams& p, int y, int top)
+{
+    return (top != kNoTop) && y < top && (p.extend_rows < 0 || y >= top - p.extend_rows);
+}
+
 // E at frame pixel (y, x) (in frame), from C and the column's top.
 __device__ __forceinline__ float extended(const Tile& T, const StageBParams& p, int y, int x,
                                           int top, float topval)
 {
-    const bool above = (top != kNoTop) && y < top && (p.extend_rows < 0 || y >= top - p.extend_rows);
-    return above ? topval : T.fd.c[(size_t)y * T.fd.c_pitch + x];
+    return above_top(p, y, top) ? topval : T.fd.c[(size_t)y * T.fd.c_pitch + x];
 }
 
-// The shared tail: median of F (kER x kEC, border replicated) into M
-// (kMR x kMC), mirrored ring, blur, inversion, store.
+// The shared tail.  F: the median input (kER x kES floats, border
+// replicated).  K: the same values as packed 16-bit keys (row k of the top
+// half in the low halves of K row k, row k + kHalf in the high halves) when
+// `keys` is set.  Median into M (kMR x kMS), mirrored ring, blur, inversion,
+// store.  R (kMR x kRS floats) may alias F.
 __device__ void median_blur_store(const Tile& T, const StageBParams& p, const float* __restrict__ F,
-                                  float* __restrict__ M, float* __restrict__ R)
+                                  const unsigned* __restrict__ K, bool keys, float* __restrict__ M,
+                                  float* __restrict__ R)
 {
     const int H = T.fd.H, W = T.fd.W;
     const int tid = threadIdx.x;
-    // -- step 7: median, one 2 x 8 block per thread
+    // -- step 7: median, blocks (rb, cb) and (rb + kHalf / 2, cb) of 2 x 8
     {
         const int rb = tid / (kMC / 8), cb = tid % (kMC / 8);
-        float x[6][12];
-        const float* src = F + (2 * rb) * kES + 8 * cb;
+        if (!p.median) {
 #pragma unroll
-        for (int r = 0; r < 6; ++r) {
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const float4 v = *reinterpret_cast<const float4*>(src + r * kES + 4 * q);
-                x[r][4 * q + 0] = v.x;
-                x[r][4 * q + 1] = v.y;
-                x[r][4 * q + 2] = v.z;
-                x[r][4 * q + 3] = v.w;
-            }
-        }
-        float m[2][8];
-        if (p.median) {
-            median_block_2x8<float, FloatOps>(x, m);
+                for (int r = 0; r < 2; ++r)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int a = 2 * rb + h * kHalf + r, b = 8 * cb + j;
+                        M[a * kMS + b] = F[(a + 2) * kES + b + 2];
+                    }
+        } else if (keys) {
+            unsigned x[6][12];
+            const unsigned* src = K + (2 * rb) * kES + 8 * cb;
+#pragma unroll
+            for (int r = 0; r < 6; ++r)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const uint4 v = *reinterpret_cast<const uint4*>(src + r * kES + 4 * q);
+                    x[r][4 * q + 0] = v.x;
+                    x[r][4 * q + 1] = v.y;
+                    x[r][4 * q + 2] = v.z;
+                    x[r][4 * q + 3] = v.w;
+                }
+            unsigned m[2][8];
+            median_block_2x8<unsigned, PackedKeyOps>(x, m);
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    float o[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) o[j] = value_of(h ? (m[r][j] >> 16) : (m[r][j] & 0xFFFFu));
+                    float* dst = M + (2 * rb + h * kHalf + r) * kMS + 8 * cb;
+                    *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+                    *reinterpret_cast<float4*>(dst + 4) = make_float4(o[4], o[5], o[6], o[7]);
+                }
         } else {
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                float x[6][12];
+                const float* src = F + (2 * rb + h * kHalf) * kES + 8 * cb;
 #pragma unroll
-            for (int r = 0; r < 2; ++r)
+                for (int r = 0; r < 6; ++r)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) m[r][j] = x[r + 2][j + 2];
-        }
-        float* dst = M + (2 * rb) * kMS + 8 * cb;
+                    for (int q = 0; q < 3; ++q) {
+                        const float4 v = *reinterpret_cast<const float4*>(src + r * kES + 4 * q);
+                        x[r][4 * q + 0] = v.x;
+                        x[r][4 * q + 1] = v.y;
+                        x[r][4 * q + 2] = v.z;
+                        x[r][4 * q + 3] = v.w;
+                    }
+                float m[2][8];
+                median_block_2x8<float, FloatOps>(x, m);
+                float* dst = M + (2 * rb + h * kHalf) * kMS + 8 * cb;
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            *reinterpret_cast<float4*>(dst + r * kMS) = make_float4(m[r][0], m[r][1], m[r][2], m[r][3]);
-            *reinterpret_cast<float4*>(dst + r * kMS + 4) = make_float4(m[r][4], m[r][5], m[r][6], m[r][7]);
+                for (int r = 0; r < 2; ++r) {
+                    *reinterpret_cast<float4*>(dst + r * kMS) = make_float4(m[r][0], m[r][1], m[r][2], m[r][3]);
+                    *reinterpret_cast<float4*>(dst + r * kMS + 4) =
+                        make_float4(m[r][4], m[r][5], m[r][6], m[r][7]);
+                }
+            }
         }
     }
     __syncthreads();
@@ -194,7 +274,7 @@ __device__ void median_blur_store(const Tile& T, const StageBParams& p, const fl
     // only the two rows / columns beyond each edge are read by the blur
     const bool edge = T.y0 < 2 || T.x0 < 2 || T.y0 + kTBH + 2 > H || T.x0 + kTBW + 2 > W;
     if (edge) {
-        Ring ring = ring_of(T, 2, kMR, kMC);
+        const Ring ring = ring_of(T, 2, kMR, kMC);
         for (int i = tid; i < ring.count(); i += kThreadsB) {
             int a, b;
             ring.at(i, a, b);
@@ -328,108 +408,125 @@ constexpr int kMaxSparseFill = 160;
 // of 60) and rows of C are 128-byte aligned, so every chunk is aligned.
 constexpr int kChunksPerRow = kEC / 4;
 constexpr int kChunks = kER * kChunksPerRow;
-constexpr int kChunksPerThread = (kChunks + kThreadsB - 1) / kThreadsB;
-static_assert(kEC % 4 == 0 && kTBW % 4 == 0, "chunked region");
 
-// Prefetch a tile's region of C into registers: the in-frame chunks (a chunk
-// straddling the right edge reads the row padding of C, which is allocated).
-__device__ __forceinline__ void prefetch_region(const Tile& T, float4 (&pre)[kChunksPerThread])
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 {
-#pragma unroll
-    for (int j = 0; j < kChunksPerThread; ++j) {
-        const int ch = threadIdx.x + j * kThreadsB;
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Start copying a tile's region of C into `dst` (kER x kES): the in-frame
+// chunks (a chunk straddling the right edge reads the row padding of C,
+// which is allocated).
+__device__ __forceinline__ void issue_region(const Tile& T, float* dst)
+{
+    for (int ch = threadIdx.x; ch < kChunks; ch += kThreadsB) {
         const int k = ch / kChunksPerRow, q = ch - k * kChunksPerRow;
         const int y = T.y0 - 4 + k, xs = T.x0 - 4 + 4 * q;
-        if (ch < kChunks && y >= 0 && y < T.fd.H && xs >= 0 && xs < T.fd.W)
-            pre[j] = __ldcg(reinterpret_cast<const float4*>(T.fd.c + (size_t)y * T.fd.c_pitch + xs));
+        if (y >= 0 && y < T.fd.H && xs >= 0 && xs < T.fd.W)
+            cp_async16(dst + k * kES + 4 * q, T.fd.c + (size_t)y * T.fd.c_pitch + xs);
     }
+    cp_async_commit();
 }
 
+// Write the key of region position (k, l) into K's half-words.
+__device__ __forceinline__ void put_key(unsigned* K, int k, int l, unsigned key)
+{
+    unsigned short* h = reinterpret_cast<unsigned short*>(K);
+    if (k < kPR) h[2 * (k * kES + l)] = static_cast<unsigned short>(key);
+    if (k >= kHalf) h[2 * ((k - kHalf) * kES + l) + 1] = static_cast<unsigned short>(key);
+}
+
+constexpr size_t kMainSmemFloats = 2 * kER * kES + kPR * kES + kMR * kMS + 2 * kEC + kMaxSparseFill + 4;
+
 // Phase 1, persistent: each CTA walks tiles blockIdx.x, + gridDim.x, ...,
-// prefetching the next tile's region and column tops into registers while
-// it computes the current one.  A tile whose median input holds at most
-// kMaxSparseFill empty pixels fills them itself (step 6, pixel by pixel); a
-// tile with more goes to the worklist.
-__global__ void __launch_bounds__(kThreadsB, 2)
+// copying the next tile's region (cp.async) and column tops while it
+// computes the current one.
+__global__ void __launch_bounds__(kThreadsB, 3)
 stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles, StageBParams p,
              int* __restrict__ worklist)
 {
-    __shared__ __align__(16) float E[kER * kES];
-    __shared__ __align__(16) float M[kMR * kMS];
-    __shared__ int ctop[kEC];
-    __shared__ float cval[kEC];
-    __shared__ int elist[kMaxSparseFill];
-    __shared__ int ecount;
-    float* R = E;  // the Gaussian row pass reuses E once the median has read it
+    extern __shared__ __align__(16) float smem[];
+    float* Ebuf = smem;                                                      // 2 x region
+    unsigned* K = reinterpret_cast<unsigned*>(smem + 2 * kER * kES);         // packed keys
+    float* M = smem + 2 * kER * kES + kPR * kES;
+    int* ctop = reinterpret_cast<int*>(M + kMR * kMS);
+    float* cval = reinterpret_cast<float*>(ctop + kEC);
+    int* elist = reinterpret_cast<int*>(cval + kEC);
+    int* ecount = elist + kMaxSparseFill;
 
     const int tid = threadIdx.x;
     int t = blockIdx.x;
     if (t >= total_tiles) return;
     Tile T = tile_of(frames, n_frames, t);
-    float4 pre[kChunksPerThread];
-    prefetch_region(T, pre);
+    issue_region(T, Ebuf);
     load_tops(T, p, T.x0 - 4, kEC, ctop, cval);
-    if (tid == 0) ecount = 0;
+    if (tid == 0) *ecount = 0;
     __syncthreads();
     // does step 5 reach this tile's region (some column's top below its first row)?
     bool ext_tile = __syncthreads_or(tid < kEC && ctop[tid] != kNoTop && ctop[tid] > T.y0 - 4);
 
-    while (true) {
+    for (int it = 0;; ++it) {
+        float* E = Ebuf + (it & 1) * (kER * kES);
+        float* Enext = Ebuf + ((it + 1) & 1) * (kER * kES);
         const int H = T.fd.H, W = T.fd.W;
-        // step 5 while storing the prefetched region; note empty pixels
-#pragma unroll
-        for (int j = 0; j < kChunksPerThread; ++j) {
-            const int ch = tid + j * kThreadsB;
-            const int k = ch / kChunksPerRow, q = ch - k * kChunksPerRow;
-            const int y = T.y0 - 4 + k, xs = T.x0 - 4 + 4 * q;
-            if (ch < kChunks && y >= 0 && y < H && xs >= 0 && xs < W) {
-                if (!ext_tile && xs + 4 <= W) {
-                    *reinterpret_cast<float4*>(E + k * kES + 4 * q) = pre[j];
-                    if (p.large_fill_on && (is_empty(pre[j].x) || is_empty(pre[j].y) || is_empty(pre[j].z) ||
-                                            is_empty(pre[j].w))) {
-                        const float raw[4] = {pre[j].x, pre[j].y, pre[j].z, pre[j].w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (is_empty(raw[e])) {
-                                const int slot = atomicAdd(&ecount, 1);
-                                if (slot < kMaxSparseFill) elist[slot] = (k << 16) | (4 * q + e);
-                            }
-                    }
-                } else {
-                    const float raw[4] = {pre[j].x, pre[j].y, pre[j].z, pre[j].w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int l = 4 * q + e;
-                        if (xs + e >= W) break;
-                        const int top = ctop[l];
-                        const bool above = (top != kNoTop) && y < top &&
-                                           (p.extend_rows < 0 || y >= top - p.extend_rows);
-                        const float v = above ? cval[l] : raw[e];
-                        E[k * kES + l] = v;
-                        if (p.large_fill_on && is_empty(v)) {
-                            const int slot = atomicAdd(&ecount, 1);
-                            if (slot < kMaxSparseFill) elist[slot] = (k << 16) | l;
-                        }
-                    }
-                }
-            }
-        }
+        cp_async_wait_all();
         __syncthreads();
-        const int n_empty = ecount;
 
-        // prefetch the next tile while this one is computed
+        // copy the next tile while this one is computed
         const int tn = t + gridDim.x;
         const bool more = tn < total_tiles;
         Tile Tn = T;
         int ntop = kNoTop;
         if (more) {
             Tn = tile_of(frames, n_frames, tn);
-            prefetch_region(Tn, pre);
+            issue_region(Tn, Enext);
             if (tid < kEC && p.extend_top) {
                 const int t2 = __ldcg(Tn.fd.top + clampi(Tn.x0 - 4 + tid, Tn.fd.W));
                 ntop = t2 < Tn.fd.H ? t2 : kNoTop;
             }
         }
+
+        // step 5 in place, empty pixels, packed keys: row pairs (kp, kp + kHalf)
+        bool keys_ok = true;
+        for (int i = tid; i < kPR * kChunksPerRow; i += kThreadsB) {
+            const int kp = i / kChunksPerRow, q = i - kp * kChunksPerRow;
+            const int xs = T.x0 - 4 + 4 * q;
+            unsigned key[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = kp + h * kHalf;
+                const int y = T.y0 - 4 + k;
+                if (y < 0 || y >= H || xs < 0 || xs >= W) continue;
+                float4* cell = reinterpret_cast<float4*>(E + k * kES + 4 * q);
+                const float4 c4 = *cell;
+                float v[4] = {c4.x, c4.y, c4.z, c4.w};
+                if (ext_tile) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (above_top(p, y, ctop[4 * q + e])) v[e] = cval[4 * q + e];
+                    *cell = make_float4(v[0], v[1], v[2], v[3]);
+                }
+                // rows kHalf .. kPR - 1 appear in both halves: count them once
+                const bool counted = (h == 0) || (kp >= kPR - kHalf);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (xs + e >= W) break;
+                    key[h][e] = key_of(v[e], keys_ok);
+                    if (counted && p.large_fill_on && is_empty(v[e])) {
+                        const int slot = atomicAdd(ecount, 1);
+                        if (slot < kMaxSparseFill) elist[slot] = (k << 16) | (4 * q + e);
+                    }
+                }
+            }
+            *reinterpret_cast<uint4*>(K + kp * kES + 4 * q) =
+                make_uint4(key[0][0] | (key[1][0] << 16), key[0][1] | (key[1][1] << 16),
+                           key[0][2] | (key[1][2] << 16), key[0][3] | (key[1][3] << 16));
+        }
+        __syncthreads();
+        const int n_empty = *ecount;
 
         auto store_tile = [&](const float* buf) {
             for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
@@ -447,44 +544,48 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
             }
         } else {
             if (n_empty > 0) {  // step 6 at the few empty pixels, one warp each
-                // E is only written here (at empty pixels); large_fill_at reads C
+                // E and K are only written here (at empty pixels); large_fill_at reads C
                 const int warp = tid >> 5, lane = tid & 31;
                 for (int j = warp; j < n_empty; j += kThreadsB / 32) {
                     const int k = elist[j] >> 16, l = elist[j] & 0xFFFF;
                     const float m = large_fill_at(T, p, T.y0 - 4 + k, T.x0 - 4 + l, lane);
-                    if (lane == 0) E[k * kES + l] = m;
+                    if (lane == 0) {
+                        E[k * kES + l] = m;
+                        put_key(K, k, l, key_of(m, keys_ok));
+                    }
                 }
                 __syncthreads();
             }
             // replicate the frame border into the two rows / columns beyond each
             // edge (the median's rule; farther ones feed only mirrored outputs)
             if (T.y0 < 2 || T.x0 < 2 || T.y0 + kTBH + 2 > H || T.x0 + kTBW + 2 > W) {
-                // region origin is tile - 4: the ring of width 2 starts 2 further in
-                Ring ring = ring_of(T, 4, kER, kEC);
+                const Ring ring = ring_of(T, 4, kER, kEC);
                 for (int i = tid; i < ring.count(); i += kThreadsB) {
                     int k, l;
                     ring.at(i, k, l);
                     const int y = T.y0 - 4 + k, x = T.x0 - 4 + l;
                     if (y < -2 || y >= H + 2 || x < -2 || x >= W + 2) continue;
                     const int sk = clampi(y, H) - (T.y0 - 4), sl = clampi(x, W) - (T.x0 - 4);
-                    E[k * kES + l] = E[sk * kES + sl];
+                    const float v = E[sk * kES + sl];
+                    E[k * kES + l] = v;
+                    put_key(K, k, l, key_of(v, keys_ok));
                 }
-                __syncthreads();
             }
+            const bool keys = __syncthreads_and(keys_ok);
             if (p.stop == kStopFillLarge) store_tile(E);
-            else median_blur_store(T, p, E, M, R);
+            else median_blur_store(T, p, E, K, keys, M, E);
         }
 
         float ntopval = 0.0f;
         if (more && tid < kEC && ntop != kNoTop)
             ntopval = __ldcg(Tn.fd.c + (size_t)ntop * Tn.fd.c_pitch + clampi(Tn.x0 - 4 + tid, Tn.fd.W));
-        __syncthreads();  // E, M, ctop of this tile no longer read
+        __syncthreads();  // E, K, M, ctop of this tile no longer read
         if (!more) break;
         if (tid < kEC) {
             ctop[tid] = ntop;
             cval[tid] = ntopval;
         }
-        if (tid == 0) ecount = 0;
+        if (tid == 0) *ecount = 0;
         T = Tn;
         t = tn;
         ext_tile = __syncthreads_or(tid < kEC && ntop != kNoTop && ntop > T.y0 - 4);
@@ -555,7 +656,7 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
             }
             continue;
         }
-        median_blur_store(T, p, F, M, R);
+        median_blur_store(T, p, F, nullptr, false, M, R);
     }
 }
 
@@ -573,15 +674,18 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
     static int configured_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
+    const size_t main_smem = sizeof(float) * kMainSmemFloats;
     if (configured_dev != dev) {
         cudaError_t e = cudaFuncSetAttribute(stage_b_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)stage_b_fill_smem_bytes(kMaxLargeFill / 2));
         if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(stage_b_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)main_smem);
+        if (e != cudaSuccess) return e;
         configured_dev = dev;
     }
     if (total_tiles < 1) return cudaSuccess;
-    const int main_grid = total_tiles < 2 * sm_count ? total_tiles : 2 * sm_count;
-    stage_b_main<<<main_grid, kThreadsB, 0, stream>>>(d_frames, n_frames, total_tiles, p, worklist);
+    const int main_grid = total_tiles < 3 * sm_count ? total_tiles : 3 * sm_count;
+    stage_b_main<<<main_grid, kThreadsB, main_smem, stream>>>(d_frames, n_frames, total_tiles, p, worklist);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !p.large_fill_on || p.stop == kStopExtend) return e;
     int grid = 2 * sm_count;
