@@ -350,12 +350,38 @@ stage_a_stream(const FrameDesc* __restrict__ frames, int n_frames, int total_uni
 #pragma unroll
     for (int q = 0; q < 4; ++q) load_row(t0 + q, raw[q]);
 
+    // Consecutive in-frame input rows with no valid depth.  Every value in the
+    // rings depends on the last 2 * Rh + 2 input rows at most, so once more
+    // than kQuiet such rows have streamed by, the rings hold exactly what an
+    // all-empty history gives (0 on in-frame columns) and an empty row leaves
+    // them unchanged: its outputs are 0 and its arithmetic can be skipped.
+    constexpr int kQuiet = 2 * Rh + 4;
+    int quiet = 0;
+
     auto step = [&](auto phi, int u0) {
         constexpr int PHI = decltype(phi)::value;
         const int t = t0 + u0 + PHI;
+        const bool row_in = t >= 0 && t < H;
+        bool mine_empty = true;
+#pragma unroll
+        for (int v = 0; v < kV; ++v) mine_empty &= is_empty(raw[PHI][v]);
+        quiet = (row_in && __all_sync(0xffffffffu, mine_empty)) ? quiet + 1 : 0;
+        if (quiet > kQuiet) {
+            load_row(t + 4, raw[PHI]);
+            const int r = stop == kStopInvert ? t
+                        : stop == kStopDilate ? t - R1
+                        : stop == kStopClose  ? t - R1 - 4
+                                              : t - Rh;
+            if (r >= r0 && r < r1) {
+                float* dst = (stop == kStopFull ? fd.c + (size_t)r * fd.c_pitch : fd.out + (size_t)r * fd.out_pitch) + cx;
+#pragma unroll
+                for (int v = 0; v < kV; ++v)
+                    if (col_out[v]) dst[v] = 0.0f;
+            }
+            return;
+        }
         // step 1
         Row x;
-        const bool row_in = t >= 0 && t < H;
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
             const float d = raw[PHI][v];

@@ -439,6 +439,98 @@ __device__ __forceinline__ void put_key(unsigned* K, int k, int l, unsigned key)
     if (k >= kHalf) h[2 * ((k - kHalf) * kES + l) + 1] = static_cast<unsigned short>(key);
 }
 
+// A tile whose whole region lies above its columns' top rows (step 5 then
+// makes every row of the region the same: E(y, x) = C(top(x), x)) has
+// row-constant maps: the median of a window is the median of its five column
+// values (each appears five times), and the blur sums identical rows.  This
+// computes one output row with the same operations, in the same order, as
+// the general path, and writes it to every row of the tile.  cval holds the
+// region's top values (border replicated); W (kMC + kTBW floats) is scratch.
+__device__ void constant_tile_store(const Tile& T, const StageBParams& p, const float* __restrict__ cval,
+                                    float* __restrict__ W_)
+{
+    const int H = T.fd.H, W = T.fd.W;
+    const int tid = threadIdx.x;
+    float* Mrow = W_;          // kMC: median region columns
+    float* Orow = W_ + kMC;    // kTBW: the output row
+    float m = 0.0f;
+    if (tid < kMC) {
+        float v[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) v[j] = cval[tid + j];
+        if (p.median) {
+#pragma unroll
+            for (int i = 1; i < 5; ++i)
+#pragma unroll
+                for (int j = 4; j >= i; --j) {
+                    const float lo = fminf(v[j - 1], v[j]), hi = fmaxf(v[j - 1], v[j]);
+                    v[j - 1] = lo;
+                    v[j] = hi;
+                }
+        }
+        m = v[2];
+        Mrow[tid] = m;
+    }
+    __syncthreads();
+    // reflect-101 of the two columns beyond each frame edge
+    if (tid < kMC) {
+        const int x = T.x0 - 2 + tid;
+        if ((x < 0 || x >= W) && x >= -2 && x < W + 2) m = Mrow[reflect101(x, W) - (T.x0 - 2)];
+    }
+    __syncthreads();
+    if (tid < kMC) Mrow[tid] = m;
+    __syncthreads();
+    constexpr float w0 = 0.0625f, w1 = 0.25f, w2 = 0.375f;
+    if (tid < kTBW) {
+        const int b = tid;
+        const float mc = Mrow[b + 2];
+        float o = mc;
+        if (p.stop == kStopExtend || p.stop == kStopFillLarge) {
+            o = cval[b + 4];
+        } else if (p.stop != kStopMedian) {
+            float g = mc;
+            if (!is_empty(mc)) {
+                if (p.blur == kBlurGauss) {
+                    float r = w0 * Mrow[b];
+                    r = fmaf(w1, Mrow[b + 1], r);
+                    r = fmaf(w2, Mrow[b + 2], r);
+                    r = fmaf(w1, Mrow[b + 3], r);
+                    r = fmaf(w0, Mrow[b + 4], r);
+                    float acc = w0 * r;
+                    acc = fmaf(w1, r, acc);
+                    acc = fmaf(w2, r, acc);
+                    acc = fmaf(w1, r, acc);
+                    acc = fmaf(w0, r, acc);
+                    g = acc;
+                } else if (p.blur == kBlurBilateral) {
+                    float num = 0.0f, den = 0.0f;
+#pragma unroll
+                    for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+                        for (int dx = -2; dx <= 2; ++dx) {
+                            const int r2 = dy * dy + dx * dx;
+                            if (r2 > 4) continue;
+                            const float v = Mrow[b + 2 + dx];
+                            const float d = v - mc;
+                            const float wgt = p.ws[r2] * expf(-(d * d) * p.inv_2sc2);
+                            num = fmaf(v, wgt, num);
+                            den += wgt;
+                        }
+                    g = num / den;
+                }
+            }
+            o = (p.stop == kStopBlur) ? g : (is_empty(mc) ? 0.0f : __fsub_rn(kInvertFrom, g));
+        }
+        Orow[b] = o;
+    }
+    __syncthreads();
+    for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
+        const int a = i / kTBW, b = i - a * kTBW;
+        const int y = T.y0 + a, x = T.x0 + b;
+        if (y < H && x < W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = Orow[b];
+    }
+}
+
 constexpr size_t kMainSmemFloats = 2 * kER * kES + kPR * kES + kMR * kMS + 2 * kEC + kMaxSparseFill + 4;
 
 // Phase 1, persistent: each CTA walks tiles blockIdx.x, + gridDim.x, ...,
@@ -489,6 +581,13 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
             }
         }
 
+        // a region entirely above its columns' tops: one row does for all
+        const bool const_tile = __syncthreads_and(
+            p.extend_top && p.extend_rows < 0 &&
+            (tid >= kEC || (ctop[tid] != kNoTop && ctop[tid] > T.y0 - 4 + kER - 1)));
+        if (const_tile) {
+            constant_tile_store(T, p, cval, M);
+        } else {
         // step 5 in place, empty pixels, packed keys: row pairs (kp, kp + kHalf)
         bool keys_ok = true;
         for (int i = tid; i < kPR * kChunksPerRow; i += kThreadsB) {
@@ -574,6 +673,7 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
             const bool keys = __syncthreads_and(keys_ok);
             if (p.stop == kStopFillLarge) store_tile(E);
             else median_blur_store(T, p, E, K, keys, M, E);
+        }
         }
 
         float ntopval = 0.0f;
