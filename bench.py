@@ -61,6 +61,21 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def measured_traffic(stage):
+    """DRAM bytes per launch of a stage from the committed ncu summary, or
+    None if the kernel source changed since that capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            entry = json.load(fh)[stage]
+        with open(os.path.join(ROOT, entry["source"]), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != entry["source_sha256"]:
+                return None
+        return int(entry["dram_read_bytes"]) + int(entry["dram_write_bytes"])
+    except Exception:
+        return None
+
+
 def dist_setup(n_gpus):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -334,7 +349,8 @@ def run_gpu(args, world, rank, local):
             "achieved": round(achieved, 1) if achieved else None,
             "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
             "peak_kind": peak_kind,
-            "traffic": None,
+            "traffic": measured_traffic(dom) if B == BATCH else None,
+            "traffic_unit": "bytes per launch (ncu, profiles/traffic.json)",
             "bytes_per_px": BYTES_PER_PX,
             "path_achieved": round(BYTES_PER_PX * px * fps / 1e9, 1),
             "path_frac": round(BYTES_PER_PX * px * fps / 1e9 / hbm, 4),
