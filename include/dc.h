@@ -131,8 +131,9 @@ dc_status dc_complete_uniform(dc_ctx* ctx, const float* in, float* out, int n,
                               int H, int W, const dc_params* params, void* stream);
 
 /* Same as dc_complete_uniform but `host_in` / `host_out` are HOST buffers
- * (pinned memory gives full copy bandwidth): copies in, runs, copies out
- * on `stream` and returns when the result is in host_out. */
+ * (pinned memory gives full copy bandwidth).  The batch is split into
+ * chunks whose copy in, kernels (on `stream`) and copy out (on two copy
+ * streams of the context) overlap; returns when the result is in host_out. */
 dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, int n,
                            int H, int W, const dc_params* params, void* stream);
 

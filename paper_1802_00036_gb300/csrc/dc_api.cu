@@ -16,6 +16,10 @@ using namespace dcgb;
 // kSlots calls are still in flight; each slot's event marks the end of the
 // call that last used it.
 constexpr int kSlots = 16;
+// dc_complete_host splits a batch into at most this many chunks so that the
+// copy in of chunk i + 1, the kernels of chunk i and the copy out of chunk
+// i - 1 overlap.
+constexpr int kIoChunksMax = 16;
 
 struct TableSlot {
     FrameDesc* d = nullptr;      // device copy read by the kernels
@@ -37,10 +41,12 @@ struct dc_ctx {
     TableSlot slot[kSlots];
     int frames_cap = 0;       // descriptors per slot
     unsigned long long calls = 0;
-    // staging for host calls
+    // staging for host calls: copy streams and events of the chunk pipeline
     float* io_in = nullptr;
     float* io_out = nullptr;
     size_t io_cap = 0;        // floats each
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t io_ev[2 * kIoChunksMax] = {};
     // bookkeeping
     cudaStream_t last_stream = nullptr;
     cudaEvent_t last_done = nullptr;  // event of the latest call, or null
@@ -399,17 +405,42 @@ dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, i
         return DC_ERR_INVALID_ARG;
     if (n == 0) return DC_OK;
     DeviceGuard g(ctx->device);
-    const size_t floats = (size_t)n * H * W;
+    const size_t frame = (size_t)H * W;
+    const size_t floats = (size_t)n * frame;
     dc_status s = grow(ctx, 0, 0, 0, floats);
     if (s != DC_OK) return note(ctx, s);
+    if (!ctx->s_in) {
+        bool ok = cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; ok && i < 2 * kIoChunksMax; ++i)
+            ok = cudaEventCreateWithFlags(&ctx->io_ev[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) return note(ctx, DC_ERR_CUDA);
+    }
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(ctx->io_in, host_in, floats * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    // chunks of about 8 frames (at least 4 MB), at most kIoChunksMax
+    int per = (int)((4u << 20) / (frame * sizeof(float)));
+    if (per < 8) per = 8;
+    if (per * kIoChunksMax < n) per = (n + kIoChunksMax - 1) / kIoChunksMax;
+    if (per > n) per = n;
+    // the copy-in stream starts after earlier work on `stream` (io_in reuse)
+    if (cudaEventRecord(ctx->io_ev[0], st) != cudaSuccess || cudaStreamWaitEvent(ctx->s_in, ctx->io_ev[0], 0) != cudaSuccess)
         return note(ctx, DC_ERR_CUDA);
-    s = dc_complete_uniform(ctx, ctx->io_in, ctx->io_out, n, H, W, params, stream);
-    if (s != DC_OK) return s;
-    if (cudaMemcpyAsync(host_out, ctx->io_out, floats * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    int k = 0;
+    for (int f0 = 0; f0 < n; f0 += per, ++k) {
+        const int m = (n - f0 < per) ? n - f0 : per;
+        const size_t off = (size_t)f0 * frame, bytes = (size_t)m * frame * sizeof(float);
+        cudaEvent_t in_done = ctx->io_ev[2 * k], run_done = ctx->io_ev[2 * k + 1];
+        if (cudaMemcpyAsync(ctx->io_in + off, host_in + off, bytes, cudaMemcpyHostToDevice, ctx->s_in) != cudaSuccess ||
+            cudaEventRecord(in_done, ctx->s_in) != cudaSuccess || cudaStreamWaitEvent(st, in_done, 0) != cudaSuccess)
+            return note(ctx, DC_ERR_CUDA);
+        s = dc_complete_uniform(ctx, ctx->io_in + off, ctx->io_out + off, m, H, W, params, stream);
+        if (s != DC_OK) return s;
+        if (cudaEventRecord(run_done, st) != cudaSuccess || cudaStreamWaitEvent(ctx->s_out, run_done, 0) != cudaSuccess ||
+            cudaMemcpyAsync(host_out + off, ctx->io_out + off, bytes, cudaMemcpyDeviceToHost, ctx->s_out) != cudaSuccess)
+            return note(ctx, DC_ERR_CUDA);
+    }
+    if (cudaStreamSynchronize(ctx->s_out) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
         return note(ctx, DC_ERR_CUDA);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return note(ctx, DC_ERR_CUDA);
     return DC_OK;
 }
 
@@ -494,6 +525,10 @@ void dc_destroy(dc_ctx* ctx)
         }
         cudaFree(ctx->io_in);
         cudaFree(ctx->io_out);
+        for (cudaEvent_t e : ctx->io_ev)
+            if (e) cudaEventDestroy(e);
+        if (ctx->s_in) cudaStreamDestroy(ctx->s_in);
+        if (ctx->s_out) cudaStreamDestroy(ctx->s_out);
         if (ctx->prof_ev) {
             for (int i = 0; i < 3 * DC_PROFILE_CALLS; ++i)
                 if (ctx->prof_ev[i]) cudaEventDestroy(ctx->prof_ev[i]);

@@ -196,6 +196,17 @@ def test_host_buffers_entry_point(ctx):
     assert np.array_equal(out.view(np.uint32), dev.view(np.uint32))
 
 
+def test_host_buffers_pipelined_chunks(ctx):
+    # 20 full-size frames: the copies and kernels run in three overlapped chunks
+    from paper_1802_00036_gb300 import dc
+    frames = synth.make_batch(20, synth.ONE_FRAME, config=7)
+    hin = torch.from_numpy(frames).pin_memory()
+    hout = torch.full_like(hin, -1.0).pin_memory()
+    dc.dc_complete_host(ctx.h, hin.data_ptr(), hout.data_ptr(), 20, 352, 1216, dc.params())
+    dev = gpu_run(ctx, frames)
+    assert np.array_equal(hout.numpy().view(np.uint32), dev.view(np.uint32))
+
+
 def test_invalid_arguments_are_refused(ctx):
     from paper_1802_00036_gb300 import dc
     x = torch.zeros((2, 16, 16), device="cuda")
