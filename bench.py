@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--blur", default="gauss", choices=["gauss", "bilateral"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=1.5,
+                    help="seconds of Poisson arrivals per rate in the serving leg (0: skip)")
     ap.add_argument("--quick", action="store_true",
                     help="timed batched steps only (no per-frame, e2e or CPU legs): for profiling")
     return ap.parse_args()
@@ -324,6 +326,10 @@ def run_gpu(args, world, rank, local):
     e2e_s = barrier_max(e2e_s, world, dev)
     e2e_fps = B * e2e_steps * world / e2e_s
 
+    serving = None
+    if args.serve_seconds > 0:
+        serving = run_serving(args.serve_seconds)
+
     if rank != 0:
         ctx.close()
         return
@@ -362,6 +368,7 @@ def run_gpu(args, world, rank, local):
                 "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
                 "note": "dc_complete_host on pinned host buffers, copies in the timed region"},
         "gpu_launches": launches_per_step * args.steps,
+        "served": serving,
         "clocks": clocks.summary(),
     }
     if not args.no_cpu_baseline and world == 1:
@@ -370,6 +377,41 @@ def run_gpu(args, world, rank, local):
         line["cpu_baseline"] = None
     ctx.close()
     print(json.dumps(line), flush=True)
+
+
+def run_serving(seconds):
+    """The continuous-batching server against one request per launch, on 8
+    simulated sensors (Poisson arrivals) mixing 352x1216 and 512x2048 frames
+    at 3-10 % density, device budget 2 GB, 2 ms batch deadline."""
+    import torch
+
+    from paper_1802_00036_gb300 import synth
+    from paper_1802_00036_gb300.serve import Server, drive
+    sensors = 8
+    pools = []
+    for s in range(sensors):
+        spec = synth.FrameSpec(352, 1216, 64, 0.05) if s % 2 == 0 else synth.FrameSpec(512, 2048, 128, 0.08)
+        pool = []
+        for k in range(3):
+            dens = 0.03 + 0.07 * ((s * 3 + k) % 8) / 7.0
+            f = synth.make_frame(synth.FrameSpec(spec.H, spec.W, spec.beams, dens), 5000 + 10 * s + k)
+            pool.append(torch.from_numpy(f).pin_memory())
+        pools.append(pool)
+    out = {"sensors": sensors, "mix": "50/50 352x1216 / 512x2048, 3-10 % valid", "budget_bytes": 2 << 30,
+           "deadline_ms": 2.0, "seconds_per_rate": seconds, "rates": []}
+    for rate in (125.0, 1000.0, 4000.0):
+        row = {"per_sensor_hz": rate}
+        for name, kw in (("batched", dict(deadline_ms=2.0, max_batch=64, lanes=3)),
+                         ("per_frame", dict(deadline_ms=0.0, max_batch=1, lanes=3))):
+            srv = Server(max_hw=(512, 2048), budget_bytes=2 << 30, copy_results=False, **kw)
+            try:
+                drive(srv, pools, 50.0, 0.2, seed=1)          # warm-up
+                res = drive(srv, pools, rate, seconds, seed=2)
+            finally:
+                srv.close()
+            row[name] = {k: round(v, 3) if isinstance(v, float) else v for k, v in res.items()}
+        out["rates"].append(row)
+    return out
 
 
 def main():
