@@ -141,6 +141,27 @@ dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, i
  * so that later calls of that size do not allocate. */
 dc_status dc_reserve(dc_ctx* ctx, int n_frames, int H, int W);
 
+/* Launch-shape choices of a context (never the results: every pixel's
+ * arithmetic is the same under any tuning).  a_warps_per_sm: stage A (steps
+ * 1-4) splits frames into row bands so that about this many warps per SM
+ * run (more bands = more parallelism but more halo rows recomputed; 1..64,
+ * default 12).  b_ctas_per_sm: persistent CTAs per SM of stage B (steps 5-8;
+ * 1..3, default 3). */
+typedef struct {
+    int a_warps_per_sm;
+    int b_ctas_per_sm;
+} dc_tuning;
+
+dc_status dc_set_tuning(dc_ctx* ctx, const dc_tuning* t);
+dc_status dc_get_tuning(const dc_ctx* ctx, dc_tuning* t);
+
+/* Time dc_complete_uniform on the caller's n packed frames (device `in` /
+ * `out`, as for dc_complete_uniform; `out` is overwritten) under a fixed set
+ * of tunings, keep the fastest in the context and return it in *best.
+ * Synchronous; runs the chain about 80 times. */
+dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, int W,
+                      const dc_params* params, void* stream, dc_tuning* best);
+
 /* Number of kernel launches the last dc_complete* call queued. */
 int dc_last_launch_count(const dc_ctx* ctx);
 

@@ -89,9 +89,16 @@ __device__ __forceinline__ int find_frame(const FrameDesc* __restrict__ d, int n
 // (= vertical delay) for a first element.
 int stage_a_strip_width(int shape);
 int stage_a_halo(int shape);
-// Rows per stage-A band so that a batch with `total_strips` strips gives the
-// GPU enough warps; at least 32 rows.
-int stage_a_band_rows(int H, long long total_strips, int sm_count);
+// Rows per stage-A band so that a batch with `total_strips` strips gives
+// about `target_warps` warps; at least 32 rows.
+int stage_a_band_rows(int H, long long total_strips, long long target_warps);
+
+// Launch-shape choices (the results never depend on them).
+struct Tuning {
+    int a_warps_per_sm;  // stage A: warps in flight per SM the bands aim for
+    int b_ctas_per_sm;   // stage B: persistent CTAs per SM (1..3)
+};
+constexpr Tuning kDefaultTuning{12, 3};
 
 // Launchers (stage_a.cu, stage_b.cu).  Return cudaGetLastError().
 // `worklist` holds 1 + (stage B tiles) ints: a count that stage A zeroes,
@@ -99,6 +106,7 @@ int stage_a_band_rows(int H, long long total_strips, int sm_count);
 cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_tiles,
                            int shape, int stop, int* worklist, int sm_count, cudaStream_t stream);
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,
-                           const StageBParams& p, int* worklist, int sm_count, cudaStream_t stream);
+                           const StageBParams& p, int* worklist, int sm_count, int ctas_per_sm,
+                           cudaStream_t stream);
 
 }  // namespace dcgb

@@ -31,6 +31,7 @@ struct dc_ctx {
     int device = 0;
     int sm_count = 0;
     size_t budget = 0;  // 0 = unlimited
+    Tuning tune = kDefaultTuning;
     // scratch
     float* c = nullptr;       // step-4 maps, all frames
     size_t c_cap = 0;         // floats
@@ -200,7 +201,7 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         d.out_pitch = f.out_pitch;
         d.c_pitch = (int)round_up((size_t)f.W, 32);
         d.tiles_x_a = ceil_div(f.W, strip_w);
-        d.band_a = stage_a_band_rows(f.H, total_strips, ctx->sm_count);
+        d.band_a = stage_a_band_rows(f.H, total_strips, (long long)ctx->tune.a_warps_per_sm * ctx->sm_count);
         d.tiles_x_b = ceil_div(f.W, kTileBW);
         d.base_a = (int)tiles_a;
         d.base_b = (int)tiles_b;
@@ -264,7 +265,7 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         const double sc = p->blur == DC_BLUR_BILATERAL ? p->sigma_color : 1.0;
         for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));
         bp.inv_2sc2 = (float)(1.0 / (2.0 * sc * sc));
-        e = launch_stage_b(sl.d, n, (int)tiles_b, bp, ctx->work, ctx->sm_count, stream);
+        e = launch_stage_b(sl.d, n, (int)tiles_b, bp, ctx->work, ctx->sm_count, ctx->tune.b_ctas_per_sm, stream);
         if (e != cudaSuccess) return DC_ERR_CUDA;
         // stage B is one kernel, plus the step-6 pass when step 6 can run
         ctx->last_launches = (bp.large_fill_on && bp.stop != kStopExtend) ? 3 : 2;
@@ -417,10 +418,10 @@ dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, i
         if (!ok) return note(ctx, DC_ERR_CUDA);
     }
     cudaStream_t st = (cudaStream_t)stream;
-    // chunks of about 8 frames (at least 4 MB), at most kIoChunksMax
-    int per = (int)((4u << 20) / (frame * sizeof(float)));
+    // up to 4 chunks of at least 8 frames: enough overlap of the copies with
+    // the kernels while each chunk still fills the GPU
+    int per = (n + 3) / 4;
     if (per < 8) per = 8;
-    if (per * kIoChunksMax < n) per = (n + kIoChunksMax - 1) / kIoChunksMax;
     if (per > n) per = n;
     // the copy-in stream starts after earlier work on `stream` (io_in reuse)
     if (cudaEventRecord(ctx->io_ev[0], st) != cudaSuccess || cudaStreamWaitEvent(ctx->s_in, ctx->io_ev[0], 0) != cudaSuccess)
@@ -445,6 +446,69 @@ dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, i
 }
 
 int dc_last_launch_count(const dc_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+dc_status dc_set_tuning(dc_ctx* ctx, const dc_tuning* t)
+{
+    if (!ctx || !t || t->a_warps_per_sm < 1 || t->a_warps_per_sm > 64 || t->b_ctas_per_sm < 1 ||
+        t->b_ctas_per_sm > 3)
+        return DC_ERR_INVALID_ARG;
+    ctx->tune = Tuning{t->a_warps_per_sm, t->b_ctas_per_sm};
+    return DC_OK;
+}
+
+dc_status dc_get_tuning(const dc_ctx* ctx, dc_tuning* t)
+{
+    if (!ctx || !t) return DC_ERR_INVALID_ARG;
+    t->a_warps_per_sm = ctx->tune.a_warps_per_sm;
+    t->b_ctas_per_sm = ctx->tune.b_ctas_per_sm;
+    return DC_OK;
+}
+
+dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, int W, const dc_params* params,
+                      void* stream, dc_tuning* best)
+{
+    if (!ctx || !best || n < 1) return DC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    static const int a_cand[] = {3, 4, 6, 8, 12, 16, 24};
+    static const int b_cand[] = {1, 2, 3};
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return DC_ERR_CUDA;
+    }
+    const Tuning saved = ctx->tune;
+    float best_ms = 1e30f;
+    Tuning best_t = saved;
+    dc_status s = DC_OK;
+    for (int a : a_cand) {
+        for (int b : b_cand) {
+            ctx->tune = Tuning{a, b};
+            s = dc_complete_uniform(ctx, in, out, n, H, W, params, stream);  // warm-up, also checks args
+            if (s != DC_OK) break;
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3 && s == DC_OK; ++r) s = dc_complete_uniform(ctx, in, out, n, H, W, params, stream);
+            cudaEventRecord(e1, st);
+            float ms = 0.0f;
+            if (s != DC_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                if (s == DC_OK) s = DC_ERR_CUDA;
+                break;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_t = ctx->tune;
+            }
+        }
+        if (s != DC_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tune = (s == DC_OK) ? best_t : saved;
+    best->a_warps_per_sm = ctx->tune.a_warps_per_sm;
+    best->b_ctas_per_sm = ctx->tune.b_ctas_per_sm;
+    return s;
+}
 
 dc_status dc_set_profiling(dc_ctx* ctx, int on)
 {

@@ -132,7 +132,8 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     const bool need_b = (params->stop_after == DC_STOP_FULL || params->stop_after >= DC_STOP_EXTEND);
     const int strip_w = stage_a_strip_width(params->first_kernel);
     const int tiles_x_a = (W + strip_w - 1) / strip_w;
-    const int band_a = stage_a_band_rows(H, (long long)tiles_x_a * n, sms);
+    const int band_a = stage_a_band_rows(H, (long long)tiles_x_a * n,
+                                         (long long)kDefaultTuning.a_warps_per_sm * sms);
     const int tiles_a = tiles_x_a * ((H + band_a - 1) / band_a);
     const int tiles_x_b = (W + kTileBW - 1) / kTileBW;
     const int tiles_b = tiles_x_b * ((H + kTileBH - 1) / kTileBH);
@@ -166,7 +167,8 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
         const double sc = params->blur == DC_BLUR_BILATERAL ? params->sigma_color : 1.0;
         for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));
         bp.inv_2sc2 = (float)(1.0 / (2.0 * sc * sc));
-        if (launch_stage_b(table, n, tiles_b * n, bp, work, sms, st) != cudaSuccess) return DC_ERR_CUDA;
+        if (launch_stage_b(table, n, tiles_b * n, bp, work, sms, kDefaultTuning.b_ctas_per_sm, st) != cudaSuccess)
+            return DC_ERR_CUDA;
     }
     return DC_OK;
 }

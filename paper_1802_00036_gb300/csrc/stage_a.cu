@@ -489,9 +489,9 @@ int stage_a_halo(int shape)
 
 int stage_a_strip_width(int shape) { return kSW - 2 * stage_a_halo(shape); }
 
-int stage_a_band_rows(int H, long long total_strips, int sm_count)
+int stage_a_band_rows(int H, long long total_strips, long long target_warps)
 {
-    const long long target = 12LL * (sm_count > 0 ? sm_count : 1);  // warps in flight
+    const long long target = target_warps > 0 ? target_warps : 1;
     long long bands = total_strips > 0 ? (target + total_strips - 1) / total_strips : 1;
     if (bands < 1) bands = 1;
     long long rows = (H + bands - 1) / bands;

@@ -769,7 +769,8 @@ size_t stage_b_fill_smem_bytes(int large_radius)
 }
 
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,
-                           const StageBParams& p, int* worklist, int sm_count, cudaStream_t stream)
+                           const StageBParams& p, int* worklist, int sm_count, int ctas_per_sm,
+                           cudaStream_t stream)
 {
     static int configured_dev = -1;
     int dev = 0;
@@ -784,7 +785,9 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
         configured_dev = dev;
     }
     if (total_tiles < 1) return cudaSuccess;
-    const int main_grid = total_tiles < 3 * sm_count ? total_tiles : 3 * sm_count;
+    if (ctas_per_sm < 1) ctas_per_sm = 1;
+    if (ctas_per_sm > 3) ctas_per_sm = 3;  // shared memory holds three per SM
+    const int main_grid = total_tiles < ctas_per_sm * sm_count ? total_tiles : ctas_per_sm * sm_count;
     stage_b_main<<<main_grid, kThreadsB, main_smem, stream>>>(d_frames, n_frames, total_tiles, p, worklist);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !p.large_fill_on || p.stop == kStopExtend) return e;

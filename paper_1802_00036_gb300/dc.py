@@ -46,6 +46,10 @@ class dc_params(ctypes.Structure):
     ]
 
 
+class dc_tuning(ctypes.Structure):
+    _fields_ = [("a_warps_per_sm", ctypes.c_int), ("b_ctas_per_sm", ctypes.c_int)]
+
+
 class dc_frame(ctypes.Structure):
     _fields_ = [
         ("in_", ctypes.c_void_p),
@@ -73,6 +77,11 @@ SIGNATURES = [
                                         ctypes.POINTER(dc_params), ctypes.c_void_p]),
     ("dc_reserve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     ("dc_last_launch_count", ctypes.c_int, [ctypes.c_void_p]),
+    ("dc_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dc_tuning)]),
+    ("dc_get_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dc_tuning)]),
+    ("dc_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, ctypes.POINTER(dc_params), ctypes.c_void_p,
+                                   ctypes.POINTER(dc_tuning)]),
     ("dc_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("dc_kernel_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int)]),
@@ -172,6 +181,25 @@ def dc_complete_noalloc(in_ptr: int, out_ptr: int, n: int, H: int, W: int, p: dc
 
 def dc_reserve(ctx, n_frames: int, H: int, W: int) -> None:
     _check(load().dc_reserve(ctx, n_frames, H, W), "dc_reserve")
+
+
+def dc_set_tuning(ctx, a_warps_per_sm: int, b_ctas_per_sm: int) -> None:
+    t = dc_tuning(int(a_warps_per_sm), int(b_ctas_per_sm))
+    _check(load().dc_set_tuning(ctx, ctypes.byref(t)), "dc_set_tuning")
+
+
+def dc_get_tuning(ctx) -> tuple[int, int]:
+    t = dc_tuning()
+    _check(load().dc_get_tuning(ctx, ctypes.byref(t)), "dc_get_tuning")
+    return t.a_warps_per_sm, t.b_ctas_per_sm
+
+
+def dc_autotune(ctx, in_ptr: int, out_ptr: int, n: int, H: int, W: int, p: dc_params,
+                stream: int = 0) -> tuple[int, int]:
+    t = dc_tuning()
+    _check(load().dc_autotune(ctx, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), n, H, W, ctypes.byref(p),
+                              ctypes.c_void_p(stream), ctypes.byref(t)), "dc_autotune")
+    return t.a_warps_per_sm, t.b_ctas_per_sm
 
 
 def dc_last_launch_count(ctx) -> int:

@@ -1,0 +1,83 @@
+"""Autotuning of libdc's launch shapes, with a persistent JSON cache.
+
+`dc_autotune` (C-ABI) times the chain on the caller's frames under a fixed
+set of tunings -- stage-A warps per SM (how many row bands the streaming
+kernel cuts a batch into) and stage-B persistent CTAs per SM -- and keeps
+the fastest.  This module caches the result per (GPU, SM count, batch size,
+frame size, chain parameters) so that a later process reuses it.  Results
+never depend on the tuning; only the time does.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+from . import dc
+
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    p = os.environ.get("DCGB_TUNE_CACHE")
+    if p:
+        return p
+    base = os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache")
+    return os.path.join(base, "dcgb", "autotune.json")
+
+
+def cache_key(gpu: str, sms: int, n: int, H: int, W: int, p: dc.dc_params) -> str:
+    fields = (p.first_kernel, p.large_fill, p.median, p.blur, p.extend_top, p.extend_rows,
+              p.large_fill_on, p.stop_after)
+    return f"{gpu}|{sms}|n{n}|{H}x{W}|" + ",".join(str(v) for v in fields)
+
+
+def load_cache(path: str | None = None) -> dict:
+    path = path or cache_path()
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+        return data if isinstance(data, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(data: dict, path: str | None = None) -> None:
+    path = path or cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def tuned(ctx, inp, out, p: dc.dc_params | None = None, stream=None, use_cache: bool = True):
+    """Apply the best tuning for this workload to `ctx` (from the cache, or by
+    running dc_autotune on `inp` -> `out`, (n, H, W) float32 CUDA tensors) and
+    return (a_warps_per_sm, b_ctas_per_sm, source)."""
+    import torch
+    p = p if p is not None else dc.params()
+    n, H, W = inp.shape
+    props = torch.cuda.get_device_properties(inp.device)
+    key = cache_key(props.name, props.multi_processor_count, n, H, W, p)
+    with _lock:
+        data = load_cache() if use_cache else {}
+        if key in data:
+            a, b = data[key]
+            dc.dc_set_tuning(ctx.h, a, b)
+            return a, b, "cache"
+    s = Context_stream(stream)
+    a, b = dc.dc_autotune(ctx.h, inp.data_ptr(), out.data_ptr(), n, H, W, p, s)
+    if use_cache:
+        with _lock:
+            data = load_cache()
+            data[key] = [a, b]
+            save_cache(data)
+    return a, b, "measured"
+
+
+def Context_stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)

@@ -62,6 +62,18 @@ def test_params_default_is_the_papers_design(lib):
     assert (p.extend_top, p.extend_rows, p.large_fill_on, p.stop_after) == (1, -1, 1, 0)
 
 
+def test_tune_cache_round_trip(tmp_path, monkeypatch):
+    from paper_1802_00036_gb300 import tune
+    monkeypatch.setenv("DCGB_TUNE_CACHE", str(tmp_path / "t.json"))
+    p = dc.params()
+    k = tune.cache_key("GB300", 152, 64, 352, 1216, p)
+    assert k != tune.cache_key("GB300", 152, 64, 352, 1216, dc.params(blur="bilateral"))
+    tune.save_cache({k: [6, 3]})
+    assert tune.load_cache()[k] == [6, 3]
+    (tmp_path / "t.json").write_text("not json")
+    assert tune.load_cache() == {}
+
+
 def test_params_struct_layout_matches_header():
     # ten 4-byte fields, no padding
     assert ctypes.sizeof(dc.dc_params) == 40

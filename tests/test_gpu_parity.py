@@ -207,6 +207,28 @@ def test_host_buffers_pipelined_chunks(ctx):
     assert np.array_equal(hout.numpy().view(np.uint32), dev.view(np.uint32))
 
 
+def test_results_do_not_depend_on_tuning(ctx):
+    from paper_1802_00036_gb300 import dc
+    frames = synth.make_batch(6, synth.UNIFORM_375, config=4)
+    x = torch.from_numpy(frames).cuda()
+    ref = None
+    for a, b in ((12, 3), (1, 1), (3, 2), (64, 1)):
+        dc.dc_set_tuning(ctx.h, a, b)
+        y = torch.full_like(x, -2.0)
+        ctx.complete(x, y)
+        torch.cuda.synchronize()
+        got = y.cpu().numpy().view(np.uint32)
+        if ref is None:
+            ref = got
+        assert np.array_equal(got, ref), (a, b)
+    y = torch.empty_like(x)
+    a, b = dc.dc_autotune(ctx.h, x.data_ptr(), y.data_ptr(), 6, 375, 1242, dc.params())
+    assert 1 <= a <= 64 and 1 <= b <= 3 and dc.dc_get_tuning(ctx.h) == (a, b)
+    dc.dc_set_tuning(ctx.h, 12, 3)
+    with pytest.raises(dc.DcError):
+        dc.dc_set_tuning(ctx.h, 0, 3)
+
+
 def test_invalid_arguments_are_refused(ctx):
     from paper_1802_00036_gb300 import dc
     x = torch.zeros((2, 16, 16), device="cuda")
