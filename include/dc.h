@@ -141,6 +141,19 @@ dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, i
  * so that later calls of that size do not allocate. */
 dc_status dc_reserve(dc_ctx* ctx, int n_frames, int H, int W);
 
+/* Accuracy of n completed depth maps against ground truth: the KITTI
+ * depth-completion measures the paper reports (Section V, Tables 1-3).  Over
+ * pixels whose ground truth is valid (>= 0.1 m), per frame i:
+ *   out[5i+0] RMSE (mm), out[5i+1] MAE (mm), out[5i+2] iRMSE (1/km),
+ *   out[5i+3] iMAE (1/km), out[5i+4] number of valid pixels;
+ * the inverse of an empty prediction (< 0.1) is taken as 0; all four
+ * measures are 0 for a frame without valid pixels.  `pred` and `gt` are
+ * device arrays of n packed H x W maps (metres); `out` is a HOST array of
+ * 5 n doubles.  Sums per thread in float over 32 pixels, then in double.
+ * Synchronous: returns when `out` is filled. */
+dc_status dc_metrics(dc_ctx* ctx, const float* pred, const float* gt, int n, int H, int W,
+                     double* out, void* stream);
+
 /* Launch-shape choices of a context (never the results: every pixel's
  * arithmetic is the same under any tuning).  a_warps_per_sm: stage A (steps
  * 1-4) splits frames into row bands so that about this many warps per SM

@@ -82,6 +82,7 @@ def _load():
             "dco_median5": [f, f, i, i],
             "dco_gauss5": [f, d, i, i],
             "dco_bilateral5": [f, d, i, i, ctypes.c_double, ctypes.c_double],
+            "dco_metrics": [f, f, i, i, d],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -201,3 +202,14 @@ def bilateral5(m, sigma_space=1.5, sigma_color=0.5) -> np.ndarray:
     _check(_load().dco_bilateral5(_fptr(m), _dptr(g), m.shape[0], m.shape[1],
                                   float(sigma_space), float(sigma_color)), "bilateral5")
     return g
+
+
+def metrics(pred, gt) -> dict:
+    """KITTI-style accuracy of `pred` against `gt` (H x W, metres)."""
+    p, g = _as_map(pred), _as_map(gt)
+    if p.shape != g.shape:
+        raise ValueError("shape mismatch")
+    out = np.zeros(5, dtype=np.float64)
+    _check(_load().dco_metrics(_fptr(p), _fptr(g), p.shape[0], p.shape[1], _dptr(out)), "metrics")
+    return {"rmse_mm": out[0], "mae_mm": out[1], "irmse_per_km": out[2], "imae_per_km": out[3],
+            "valid": int(out[4])}

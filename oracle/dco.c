@@ -341,3 +341,33 @@ int dco_complete(const float* in, float* out, int H, int W, const dco_params* p)
     free(g);
     return rc;
 }
+
+/* ---- accuracy against ground truth (Section V, Tables 1-3) --------------- */
+
+int dco_metrics(const float* pred, const float* gt, int H, int W, double out[5])
+{
+    if (!pred || !gt || !out || bad_dims(H, W)) return -1;
+    double se = 0.0, ae = 0.0, ise = 0.0, iae = 0.0;
+    long n = 0;
+    for (long i = 0; i < (long)H * W; ++i) {
+        if (is_empty(gt[i])) continue;
+        const double g = gt[i], p = pred[i];
+        const double ip = is_empty(pred[i]) ? 0.0 : 1.0 / p;
+        const double d = p - g, id = ip - 1.0 / g;
+        se += d * d;
+        ae += fabs(d);
+        ise += id * id;
+        iae += fabs(id);
+        ++n;
+    }
+    if (n == 0) {
+        out[0] = out[1] = out[2] = out[3] = 0.0;
+    } else {
+        out[0] = 1000.0 * sqrt(se / n);
+        out[1] = 1000.0 * (ae / n);
+        out[2] = 1000.0 * sqrt(ise / n);
+        out[3] = 1000.0 * (iae / n);
+    }
+    out[4] = (double)n;
+    return 0;
+}

@@ -85,6 +85,18 @@ int dco_gauss5(const float* m, double* g, int H, int W);                /* 7 */
 int dco_bilateral5(const float* m, double* g, int H, int W,
                    double sigma_space, double sigma_color);             /* 7 */
 
+/* Accuracy of a depth map against ground truth (the KITTI depth-completion
+ * measures of Section V, Tables 1-3; defined by the benchmark the paper cites):
+ * over pixels whose ground truth is valid (>= 0.1 m),
+ *   out[0] RMSE  (mm)   = 1000 sqrt(mean((p - g)^2))
+ *   out[1] MAE   (mm)   = 1000 mean(|p - g|)
+ *   out[2] iRMSE (1/km) = 1000 sqrt(mean((1/p - 1/g)^2))
+ *   out[3] iMAE  (1/km) = 1000 mean(|1/p - 1/g|)
+ *   out[4] number of valid pixels
+ * with 1/p taken as 0 where the prediction is empty (< 0.1).  All four are 0
+ * when no pixel is valid.  Sums in double. */
+int dco_metrics(const float* pred, const float* gt, int H, int W, double out[5]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -109,4 +109,9 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
                            const StageBParams& p, int* worklist, int sm_count, int ctas_per_sm,
                            cudaStream_t stream);
 
+// Accuracy measures (metrics.cu): acc holds 5 n doubles of scratch, out
+// (device) receives 5 n doubles.
+cudaError_t launch_metrics(const float* pred, const float* gt, int n, int H, int W, double* acc, double* out,
+                           cudaStream_t stream);
+
 }  // namespace dcgb

@@ -39,6 +39,8 @@ struct dc_ctx {
     size_t top_cap = 0;       // ints
     int* work = nullptr;      // stage-B worklist: count, then tile indices
     size_t work_cap = 0;      // ints
+    double* acc = nullptr;    // accuracy sums and results, 10 doubles per frame
+    int acc_cap = 0;          // frames
     TableSlot slot[kSlots];
     int frames_cap = 0;       // descriptors per slot
     unsigned long long calls = 0;
@@ -447,6 +449,37 @@ dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, i
 
 int dc_last_launch_count(const dc_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
 
+dc_status dc_metrics(dc_ctx* ctx, const float* pred, const float* gt, int n, int H, int W, double* out,
+                     void* stream)
+{
+    if (!ctx || n < 0 || (n > 0 && (!pred || !gt || !out || H < 1 || W < 1))) return DC_ERR_INVALID_ARG;
+    if (n == 0) return DC_OK;
+    if (((uintptr_t)pred % sizeof(float)) != 0 || ((uintptr_t)gt % sizeof(float)) != 0) return DC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (n > ctx->acc_cap) {
+        if (ctx->budget && (size_t)n * 10 * sizeof(double) > ctx->budget) return DC_ERR_OOM;
+        if (cudaDeviceSynchronize() != cudaSuccess) return note(ctx, DC_ERR_CUDA);
+        cudaFree(ctx->acc);
+        ctx->acc = nullptr;
+        ctx->acc_cap = 0;
+        if (cudaMalloc(&ctx->acc, sizeof(double) * 10 * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            return DC_ERR_OOM;
+        }
+        ctx->acc_cap = n;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ctx->last_done && st != ctx->last_stream && cudaStreamWaitEvent(st, ctx->last_done, 0) != cudaSuccess)
+        return note(ctx, DC_ERR_CUDA);
+    double* res = ctx->acc + 5 * (size_t)n;
+    if (launch_metrics(pred, gt, n, H, W, ctx->acc, res, st) != cudaSuccess) return note(ctx, DC_ERR_CUDA);
+    ctx->last_launches = 2;
+    if (cudaMemcpyAsync(out, res, sizeof(double) * 5 * (size_t)n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return note(ctx, DC_ERR_CUDA);
+    return DC_OK;
+}
+
 dc_status dc_set_tuning(dc_ctx* ctx, const dc_tuning* t)
 {
     if (!ctx || !t || t->a_warps_per_sm < 1 || t->a_warps_per_sm > 64 || t->b_ctas_per_sm < 1 ||
@@ -582,6 +615,7 @@ void dc_destroy(dc_ctx* ctx)
         cudaFree(ctx->c);
         cudaFree(ctx->top);
         cudaFree(ctx->work);
+        cudaFree(ctx->acc);
         for (TableSlot& sl : ctx->slot) {
             cudaFree(sl.d);
             cudaFreeHost(sl.h);

@@ -77,6 +77,8 @@ SIGNATURES = [
                                         ctypes.POINTER(dc_params), ctypes.c_void_p]),
     ("dc_reserve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     ("dc_last_launch_count", ctypes.c_int, [ctypes.c_void_p]),
+    ("dc_metrics", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     ("dc_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dc_tuning)]),
     ("dc_get_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dc_tuning)]),
     ("dc_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -181,6 +183,14 @@ def dc_complete_noalloc(in_ptr: int, out_ptr: int, n: int, H: int, W: int, p: dc
 
 def dc_reserve(ctx, n_frames: int, H: int, W: int) -> None:
     _check(load().dc_reserve(ctx, n_frames, H, W), "dc_reserve")
+
+
+def dc_metrics(ctx, pred_ptr: int, gt_ptr: int, n: int, H: int, W: int, stream: int = 0):
+    """[(rmse_mm, mae_mm, irmse_per_km, imae_per_km, valid), ...] per frame."""
+    out = (ctypes.c_double * (5 * max(1, n)))()
+    _check(load().dc_metrics(ctx, ctypes.c_void_p(pred_ptr), ctypes.c_void_p(gt_ptr), n, H, W, out,
+                             ctypes.c_void_p(stream)), "dc_metrics")
+    return [tuple(out[5 * i:5 * i + 5]) for i in range(n)]
 
 
 def dc_set_tuning(ctx, a_warps_per_sm: int, b_ctas_per_sm: int) -> None:
