@@ -328,6 +328,8 @@ def run_gpu(args, world, rank, local):
     e2e_s = barrier_max(e2e_s, world, dev)
     e2e_fps = B * e2e_steps * world / e2e_s
 
+    next_rows = run_next_rows(ctx, ins, outs, stream, B)
+
     serving = None
     if args.serve_seconds > 0:
         serving = run_serving(args.serve_seconds)
@@ -372,6 +374,7 @@ def run_gpu(args, world, rank, local):
                 "note": "dc_complete_host on pinned host buffers, copies in the timed region"},
         "gpu_launches": launches_per_step * args.steps,
         "served": serving,
+        "next_rows": next_rows,
         "clocks": clocks.summary(),
     }
     if not args.no_cpu_baseline and world == 1:
@@ -380,6 +383,53 @@ def run_gpu(args, world, rank, local):
         line["cpu_baseline"] = None
     ctx.close()
     print(json.dumps(line), flush=True)
+
+
+def run_next_rows(ctx, ins, outs, stream, B):
+    """The steps around the chain: accuracy measures of a completed batch
+    against ground truth (8 B/px read) and LIDAR-to-image projection
+    (12 B/point read, 4 B/px written), timed with CUDA events."""
+    import numpy as np
+    import torch
+
+    from paper_1802_00036_gb300 import dc, synth
+    hbm, _ = peaks()
+    sp = stream.cuda_stream
+    res = {}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # accuracy measures over the batch (outputs against inputs: only the time matters here)
+    for _ in range(3):
+        dc.dc_metrics(ctx.h, outs[0].data_ptr(), ins[1].data_ptr(), B, H, W, sp)
+    reps = 20
+    ev0.record(stream)
+    for _ in range(reps):
+        dc.dc_metrics(ctx.h, outs[0].data_ptr(), ins[1].data_ptr(), B, H, W, sp)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    gbs = 8.0 * B * H * W / (ms / 1e3) / 1e9
+    res["metrics"] = {"frames_per_s": round(B / (ms / 1e3), 1), "ms_per_batch": round(ms, 4),
+                      "achieved_GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
+                      "note": "includes the synchronous copy of the results to the host"}
+    # projection of one frame's point cloud (its returns lifted to 3D + 50k stray points)
+    pts = synth.point_cloud(synth.ONE_FRAME, 4242, extra=50000)
+    dpts = torch.from_numpy(pts).cuda()
+    depth = torch.empty((H, W), device=outs[0].device)
+    P = synth.camera_matrix(synth.ONE_FRAME).ravel()
+    for _ in range(3):
+        dc.dc_project(ctx.h, dpts.data_ptr(), len(pts), P, H, W, 0.1, 1e4, depth.data_ptr(), W, sp)
+    reps = 200
+    ev0.record(stream)
+    for _ in range(reps):
+        dc.dc_project(ctx.h, dpts.data_ptr(), len(pts), P, H, W, 0.1, 1e4, depth.data_ptr(), W, sp)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    gbs = (12.0 * len(pts) + 4.0 * H * W) / (ms / 1e3) / 1e9
+    res["project"] = {"points": len(pts), "frames_per_s": round(1.0 / (ms / 1e3), 1),
+                      "points_per_s": round(len(pts) / (ms / 1e3), 1), "ms_per_frame": round(ms, 5),
+                      "achieved_GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+    return res
 
 
 def run_serving(seconds):

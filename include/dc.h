@@ -141,6 +141,18 @@ dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, i
  * so that later calls of that size do not allocate. */
 dc_status dc_reserve(dc_ctx* ctx, int n_frames, int H, int W);
 
+/* LIDAR points to a sparse depth map, the step before the chain (Section
+ * V: the benchmark projects the scans into the image with the camera
+ * calibration).  Point i is (xyz[3i], xyz[3i+1], xyz[3i+2]) (device floats,
+ * metres); P is a HOST array of 12 doubles, the row-major 3 x 4 projection.
+ * (u, v, w) = P (x, y, z, 1) is evaluated in double in that order; a point
+ * with w > 0 and d_min <= w <= d_max lands in pixel (floor(v/w), floor(u/w))
+ * if inside H x W.  Each pixel of `depth` (device, row pitch `pitch`
+ * floats) receives the smallest depth (float of w) of its points, others 0.
+ * Asynchronous on `stream`. */
+dc_status dc_project(dc_ctx* ctx, const float* xyz, long long n_points, const double* P, int H, int W,
+                     double d_min, double d_max, float* depth, int pitch, void* stream);
+
 /* Accuracy of n completed depth maps against ground truth: the KITTI
  * depth-completion measures the paper reports (Section V, Tables 1-3).  Over
  * pixels whose ground truth is valid (>= 0.1 m), per frame i:

@@ -83,6 +83,7 @@ def _load():
             "dco_gauss5": [f, d, i, i],
             "dco_bilateral5": [f, d, i, i, ctypes.c_double, ctypes.c_double],
             "dco_metrics": [f, f, i, i, d],
+            "dco_project": [f, ctypes.c_long, d, i, i, ctypes.c_double, ctypes.c_double, f],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -213,3 +214,14 @@ def metrics(pred, gt) -> dict:
     _check(_load().dco_metrics(_fptr(p), _fptr(g), p.shape[0], p.shape[1], _dptr(out)), "metrics")
     return {"rmse_mm": out[0], "mae_mm": out[1], "irmse_per_km": out[2], "imae_per_km": out[3],
             "valid": int(out[4])}
+
+
+def project(xyz, P, H: int, W: int, d_min: float = 0.1, d_max: float = 1e30) -> np.ndarray:
+    """Nearest depth per pixel of the points `xyz` (N x 3) under the 3 x 4
+    projection `P` (Section V: scans projected with the camera calibration)."""
+    pts = np.ascontiguousarray(xyz, dtype=np.float32).reshape(-1, 3)
+    Pm = np.ascontiguousarray(P, dtype=np.float64).reshape(12)
+    out = np.empty((H, W), dtype=np.float32)
+    _check(_load().dco_project(_fptr(pts), len(pts), _dptr(Pm), H, W, float(d_min), float(d_max), _fptr(out)),
+           "project")
+    return out

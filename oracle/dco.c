@@ -371,3 +371,25 @@ int dco_metrics(const float* pred, const float* gt, int H, int W, double out[5])
     out[4] = (double)n;
     return 0;
 }
+
+/* ---- LIDAR points to a sparse map (Section V) ----------------------------- */
+
+int dco_project(const float* xyz, long n, const double P[12], int H, int W,
+                double d_min, double d_max, float* depth)
+{
+    if ((!xyz && n > 0) || !P || !depth || bad_dims(H, W) || n < 0) return -1;
+    for (long i = 0; i < (long)H * W; ++i) depth[i] = 0.0f;
+    for (long i = 0; i < n; ++i) {
+        const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        const double u = P[0] * x + P[1] * y + P[2] * z + P[3];
+        const double v = P[4] * x + P[5] * y + P[6] * z + P[7];
+        const double w = P[8] * x + P[9] * y + P[10] * z + P[11];
+        if (!(w > 0.0) || w < d_min || w > d_max) continue;
+        const double col = floor(u / w), row = floor(v / w);
+        if (!(col >= 0.0 && col < W && row >= 0.0 && row < H)) continue;
+        const long k = (long)row * W + (long)col;
+        const float d = (float)w;
+        if (depth[k] == 0.0f || d < depth[k]) depth[k] = d;
+    }
+    return 0;
+}

@@ -97,6 +97,15 @@ int dco_bilateral5(const float* m, double* g, int H, int W,
  * when no pixel is valid.  Sums in double. */
 int dco_metrics(const float* pred, const float* gt, int H, int W, double out[5]);
 
+/* LIDAR points to a sparse depth map (Section V: the benchmark projects the
+ * scans into the image with the camera calibration).  Point i is
+ * (xyz[3i], xyz[3i+1], xyz[3i+2]); (u, v, w) = P (x, y, z, 1) with the 3 x 4
+ * row-major matrix P, in double.  A point with w > 0 lands in pixel
+ * (floor(v / w), floor(u / w)) if that is inside H x W and its depth w is in
+ * [d_min, d_max]; each pixel keeps its smallest depth (as float), others 0. */
+int dco_project(const float* xyz, long n, const double P[12], int H, int W,
+                double d_min, double d_max, float* depth);
+
 #ifdef __cplusplus
 }
 #endif

@@ -114,4 +114,8 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
 cudaError_t launch_metrics(const float* pred, const float* gt, int n, int H, int W, double* acc, double* out,
                            cudaStream_t stream);
 
+// LIDAR points to a sparse map (project.cu); P is a host array of 12 doubles.
+cudaError_t launch_project(const float* xyz, long long n, const double* P, int H, int W, double d_min,
+                           double d_max, float* depth, int pitch, cudaStream_t stream);
+
 }  // namespace dcgb

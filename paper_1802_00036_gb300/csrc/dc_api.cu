@@ -449,6 +449,23 @@ dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, i
 
 int dc_last_launch_count(const dc_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
 
+dc_status dc_project(dc_ctx* ctx, const float* xyz, long long n_points, const double* P, int H, int W,
+                     double d_min, double d_max, float* depth, int pitch, void* stream)
+{
+    if (!ctx || !P || !depth || n_points < 0 || (n_points > 0 && !xyz) || H < 1 || W < 1 || pitch < W ||
+        !(d_min >= 0.0) || !(d_max >= d_min))
+        return DC_ERR_INVALID_ARG;
+    for (int k = 0; k < 12; ++k)
+        if (!std::isfinite(P[k])) return DC_ERR_INVALID_ARG;
+    if (((uintptr_t)depth % sizeof(float)) != 0 || ((uintptr_t)xyz % sizeof(float)) != 0) return DC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (launch_project(xyz, n_points, P, H, W, d_min, d_max, depth, pitch, st) != cudaSuccess)
+        return note(ctx, DC_ERR_CUDA);
+    ctx->last_launches = n_points > 0 ? 2 : 1;
+    return DC_OK;
+}
+
 dc_status dc_metrics(dc_ctx* ctx, const float* pred, const float* gt, int n, int H, int W, double* out,
                      void* stream)
 {

@@ -77,6 +77,9 @@ SIGNATURES = [
                                         ctypes.POINTER(dc_params), ctypes.c_void_p]),
     ("dc_reserve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     ("dc_last_launch_count", ctypes.c_int, [ctypes.c_void_p]),
+    ("dc_project", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     ("dc_metrics", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     ("dc_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dc_tuning)]),
@@ -183,6 +186,16 @@ def dc_complete_noalloc(in_ptr: int, out_ptr: int, n: int, H: int, W: int, p: dc
 
 def dc_reserve(ctx, n_frames: int, H: int, W: int) -> None:
     _check(load().dc_reserve(ctx, n_frames, H, W), "dc_reserve")
+
+
+def dc_project(ctx, xyz_ptr: int, n_points: int, P, H: int, W: int, d_min: float, d_max: float,
+               depth_ptr: int, pitch: int | None = None, stream: int = 0) -> None:
+    """Nearest-depth projection of device points (N x 3 float32) into a
+    device H x W map; P: 12 numbers (3 x 4, row-major)."""
+    pm = (ctypes.c_double * 12)(*[float(v) for v in list(P)])
+    _check(load().dc_project(ctx, ctypes.c_void_p(xyz_ptr), int(n_points), pm, H, W, float(d_min), float(d_max),
+                             ctypes.c_void_p(depth_ptr), W if pitch is None else int(pitch),
+                             ctypes.c_void_p(stream)), "dc_project")
 
 
 def dc_metrics(ctx, pred_ptr: int, gt_ptr: int, n: int, H: int, W: int, stream: int = 0):

@@ -203,3 +203,27 @@ def random_sparse(H: int, W: int, density: float, seed: int, d_min=0.5, d_max=99
     if quantize:
         vals = np.rint(vals * 256.0) / 256.0
     return np.where(keep, vals, 0.0).astype(np.float32)
+
+
+def camera_matrix(spec: FrameSpec) -> np.ndarray:
+    """3 x 4 projection of the synthetic camera (pixel centres at +0.5)."""
+    f, cx, cy = _camera(spec)
+    return np.array([[f, 0.0, cx, 0.0], [0.0, f, cy, 0.0], [0.0, 0.0, 1.0, 0.0]])
+
+
+def point_cloud(spec: FrameSpec, seed: int, extra: int = 20000) -> np.ndarray:
+    """N x 3 float32 camera-frame points: every return of `make_frame`
+    lifted to 3D at its pixel centre, plus `extra` points behind the camera,
+    outside the field of view or beyond the depth range."""
+    frame = make_frame(spec, seed)
+    f, cx, cy = _camera(spec)
+    r, c = np.nonzero(frame)
+    z = frame[r, c].astype(np.float64)
+    x = (c + 0.5 - cx) / f * z
+    y = (r + 0.5 - cy) / f * z
+    pts = np.stack([x, y, z], axis=1)
+    rng = Stream(seed, 9)
+    far = rng.uniform((extra, 3), -120.0, 120.0)
+    pts = np.concatenate([pts, far])
+    order = np.argsort(rng.uniform((len(pts),)))
+    return pts[order].astype(np.float32)

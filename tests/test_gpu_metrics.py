@@ -53,3 +53,29 @@ def test_metrics_empty_truth_and_ragged_size(ctx):
     got = dc.dc_metrics(ctx.h, dp.data_ptr(), dg.data_ptr(), 2, H, W)
     assert got[0] == (0.0, 0.0, 0.0, 0.0, 0.0)
     assert got[1][4] == 4 * 33 and got[1][0] == pytest.approx(1000.0) and got[1][1] == pytest.approx(1000.0)
+
+
+def test_projection_matches_oracle_bit_exact(ctx):
+    from paper_1802_00036_gb300 import dc
+    for spec, seed in ((synth.ONE_FRAME, 11), (synth.FrameSpec(375, 1242, 64, 0.06, 1.0, 90.0), 12)):
+        pts = synth.point_cloud(spec, seed, extra=50000)
+        P = synth.camera_matrix(spec)
+        want = oracle.project(pts, P, spec.H, spec.W, spec.d_min, spec.d_max)
+        dpts = torch.from_numpy(pts).cuda()
+        out = torch.full((spec.H, spec.W + 8), -1.0, device="cuda")      # pitched output
+        dc.dc_project(ctx.h, dpts.data_ptr(), len(pts), P.ravel(), spec.H, spec.W, spec.d_min, spec.d_max,
+                      out.data_ptr(), spec.W + 8)
+        torch.cuda.synchronize()
+        got = out[:, :spec.W].cpu().numpy()
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+        assert np.all(out[:, spec.W:].cpu().numpy() == -1.0)          # padding untouched
+        # and the projected map feeds the chain like the sparse frame it came from
+        np.testing.assert_array_equal(got[synth.make_frame(spec, seed) > 0] > 0, True)
+
+
+def test_projection_of_no_points_is_empty(ctx):
+    from paper_1802_00036_gb300 import dc
+    out = torch.full((9, 13), 5.0, device="cuda")
+    dc.dc_project(ctx.h, 0, 0, np.eye(3, 4).ravel(), 9, 13, 0.1, 100.0, out.data_ptr())
+    torch.cuda.synchronize()
+    assert torch.all(out == 0)
