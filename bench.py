@@ -352,7 +352,8 @@ def run_gpu(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(B, args.blur),
                        parallelism="replicas" if world > 1 else "single",
-                       tuning={"a_warps_per_sm": tuning[0], "b_ctas_per_sm": tuning[1], "source": tuning[2]},
+                       tuning={"a_warps_per_sm": tuning[0][0], "b_ctas_per_sm": tuning[0][1],
+                               "b_sparse_fill": tuning[0][2], "source": tuning[1]},
                        l2=f"inputs rotate over {ROTATE} resident batches "
                           f"({ROTATE * B * px * 4 / 1e6:.0f} MB in + same out > 129 MB L2)"),
         "roofline": {

@@ -170,11 +170,15 @@ dc_status dc_metrics(dc_ctx* ctx, const float* pred, const float* gt, int n, int
  * arithmetic is the same under any tuning).  a_warps_per_sm: stage A (steps
  * 1-4) splits frames into row bands so that about this many warps per SM
  * run (more bands = more parallelism but more halo rows recomputed; 1..64,
- * default 12).  b_ctas_per_sm: persistent CTAs per SM of stage B (steps 5-8;
- * 1..3, default 3). */
+ * default 6).  b_ctas_per_sm: persistent CTAs per SM of stage B (steps 5-8;
+ * 1..3, default 3).  b_sparse_fill: a stage-B tile with at most this many
+ * empty pixels near it fills them itself (step 6); a
+ * tile with more goes to a second kernel that works on the whole window
+ * region (0..160, default 160). */
 typedef struct {
     int a_warps_per_sm;
     int b_ctas_per_sm;
+    int b_sparse_fill;
 } dc_tuning;
 
 dc_status dc_set_tuning(dc_ctx* ctx, const dc_tuning* t);
@@ -182,8 +186,8 @@ dc_status dc_get_tuning(const dc_ctx* ctx, dc_tuning* t);
 
 /* Time dc_complete_uniform on the caller's n packed frames (device `in` /
  * `out`, as for dc_complete_uniform; `out` is overwritten) under a fixed set
- * of tunings, keep the fastest in the context and return it in *best.
- * Synchronous; runs the chain about 80 times. */
+ * of tunings (two rounds of one knob at a time), keep the fastest in the
+ * context and return it in *best.  Synchronous; runs the chain ~150 times. */
 dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, int W,
                       const dc_params* params, void* stream, dc_tuning* best);
 

@@ -63,6 +63,7 @@ struct StageBParams {
     int extend_top;
     int extend_rows;    // < 0: unlimited
     int stop;
+    int sparse_fill_max;  // a tile with more empty pixels goes to the step-6 worklist
     float ws[5];        // bilateral spatial weight for dy^2+dx^2 = 0,1,2,(3),4
     float inv_2sc2;     // 1 / (2 sigma_color^2)
 };
@@ -95,14 +96,16 @@ int stage_a_band_rows(int H, long long total_strips, long long target_warps);
 
 // Launch-shape choices (the results never depend on them).
 struct Tuning {
-    int a_warps_per_sm;  // stage A: warps in flight per SM the bands aim for
-    int b_ctas_per_sm;   // stage B: persistent CTAs per SM (1..3)
+    int a_warps_per_sm;   // stage A: warps in flight per SM the bands aim for
+    int b_ctas_per_sm;    // stage B: persistent CTAs per SM (1..3)
+    int b_sparse_fill;    // stage B: most empty pixels a tile fills itself (0..160)
 };
-constexpr Tuning kDefaultTuning{12, 3};
+constexpr Tuning kDefaultTuning{6, 3, 160};
 
 // Launchers (stage_a.cu, stage_b.cu).  Return cudaGetLastError().
-// `worklist` holds 1 + (stage B tiles) ints: a count that stage A zeroes,
-// then the stage-B tiles that need step 6.
+// `worklist` holds 2 + (stage B tiles) ints: the number of stage-B tiles
+// that need the step-6 kernel and the counter from which persistent stage-B
+// CTAs take tiles (both zeroed by stage A), then those tiles.
 cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_tiles,
                            int shape, int stop, int* worklist, int sm_count, cudaStream_t stream);
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,

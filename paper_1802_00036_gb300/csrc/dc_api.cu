@@ -218,7 +218,7 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
 
     const bool need_b = (p->stop_after == DC_STOP_FULL || p->stop_after >= DC_STOP_EXTEND);
     dc_status s = grow(ctx, need_b ? c_off : 0, need_b ? top_off : 0, n, 0,
-                       need_b ? (size_t)tiles_b + 1 : 0);
+                       need_b ? (size_t)tiles_b + 2 : 0);
     if (s != DC_OK) return s;
     for (auto& d : desc) {
         d.c = need_b ? ctx->c + reinterpret_cast<size_t>(d.c) : nullptr;
@@ -263,6 +263,7 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         bp.extend_top = p->extend_top ? 1 : 0;
         bp.extend_rows = p->extend_rows;
         bp.stop = p->stop_after;
+        bp.sparse_fill_max = ctx->tune.b_sparse_fill;
         const double ss = p->blur == DC_BLUR_BILATERAL ? p->sigma_space : 1.0;
         const double sc = p->blur == DC_BLUR_BILATERAL ? p->sigma_color : 1.0;
         for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));
@@ -361,7 +362,7 @@ dc_status dc_reserve(dc_ctx* ctx, int n_frames, int H, int W)
     DeviceGuard g(ctx->device);
     const size_t tiles = (size_t)ceil_div(W, kTileBW) * (size_t)ceil_div(H, kTileBH) * (size_t)n_frames;
     return note(ctx, grow(ctx, frame_c_floats(H, W) * (size_t)n_frames,
-                          frame_top_ints(W) * (size_t)n_frames, n_frames, 0, tiles + 1));
+                          frame_top_ints(W) * (size_t)n_frames, n_frames, 0, tiles + 2));
 }
 
 dc_status dc_complete(dc_ctx* ctx, const dc_frame* frames, int n_frames, const dc_params* params,
@@ -500,9 +501,9 @@ dc_status dc_metrics(dc_ctx* ctx, const float* pred, const float* gt, int n, int
 dc_status dc_set_tuning(dc_ctx* ctx, const dc_tuning* t)
 {
     if (!ctx || !t || t->a_warps_per_sm < 1 || t->a_warps_per_sm > 64 || t->b_ctas_per_sm < 1 ||
-        t->b_ctas_per_sm > 3)
+        t->b_ctas_per_sm > 3 || t->b_sparse_fill < 0 || t->b_sparse_fill > 160)
         return DC_ERR_INVALID_ARG;
-    ctx->tune = Tuning{t->a_warps_per_sm, t->b_ctas_per_sm};
+    ctx->tune = Tuning{t->a_warps_per_sm, t->b_ctas_per_sm, t->b_sparse_fill};
     return DC_OK;
 }
 
@@ -511,6 +512,7 @@ dc_status dc_get_tuning(const dc_ctx* ctx, dc_tuning* t)
     if (!ctx || !t) return DC_ERR_INVALID_ARG;
     t->a_warps_per_sm = ctx->tune.a_warps_per_sm;
     t->b_ctas_per_sm = ctx->tune.b_ctas_per_sm;
+    t->b_sparse_fill = ctx->tune.b_sparse_fill;
     return DC_OK;
 }
 
@@ -519,8 +521,6 @@ dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, in
 {
     if (!ctx || !best || n < 1) return DC_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
-    static const int a_cand[] = {3, 4, 6, 8, 12, 16, 24};
-    static const int b_cand[] = {1, 2, 3};
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -529,34 +529,50 @@ dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, in
         return DC_ERR_CUDA;
     }
     const Tuning saved = ctx->tune;
-    float best_ms = 1e30f;
-    Tuning best_t = saved;
     dc_status s = DC_OK;
-    for (int a : a_cand) {
-        for (int b : b_cand) {
-            ctx->tune = Tuning{a, b};
-            s = dc_complete_uniform(ctx, in, out, n, H, W, params, stream);  // warm-up, also checks args
-            if (s != DC_OK) break;
-            cudaEventRecord(e0, st);
-            for (int r = 0; r < 3 && s == DC_OK; ++r) s = dc_complete_uniform(ctx, in, out, n, H, W, params, stream);
-            cudaEventRecord(e1, st);
-            float ms = 0.0f;
-            if (s != DC_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                if (s == DC_OK) s = DC_ERR_CUDA;
-                break;
-            }
-            if (ms < best_ms) {
-                best_ms = ms;
-                best_t = ctx->tune;
-            }
+    // time one tuning: a warm-up call (which also checks the arguments), then three
+    auto measure = [&](Tuning t, float* ms) -> dc_status {
+        ctx->tune = t;
+        dc_status r = dc_complete_uniform(ctx, in, out, n, H, W, params, stream);
+        if (r != DC_OK) return r;
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < 3 && r == DC_OK; ++k) r = dc_complete_uniform(ctx, in, out, n, H, W, params, stream);
+        cudaEventRecord(e1, st);
+        if (r != DC_OK) return r;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+            return DC_ERR_CUDA;
+        return DC_OK;
+    };
+    // coordinate descent: each knob in turn over its candidates, the others fixed
+    static const int a_cand[] = {2, 3, 4, 6, 8, 12, 16, 24};
+    static const int b_cand[] = {1, 2, 3};
+    static const int f_cand[] = {0, 4, 8, 16, 32, 64, 160};
+    Tuning best_t = saved;
+    float best_ms = 1e30f;
+    s = measure(best_t, &best_ms);
+    for (int round = 0; round < 2 && s == DC_OK; ++round) {
+        for (int a : a_cand) {
+            float ms;
+            if ((s = measure(Tuning{a, best_t.b_ctas_per_sm, best_t.b_sparse_fill}, &ms)) != DC_OK) break;
+            if (ms < best_ms) { best_ms = ms; best_t.a_warps_per_sm = a; }
         }
-        if (s != DC_OK) break;
+        for (int b : b_cand) {
+            float ms;
+            if (s != DC_OK || (s = measure(Tuning{best_t.a_warps_per_sm, b, best_t.b_sparse_fill}, &ms)) != DC_OK) break;
+            if (ms < best_ms) { best_ms = ms; best_t.b_ctas_per_sm = b; }
+        }
+        for (int f : f_cand) {
+            float ms;
+            if (s != DC_OK || (s = measure(Tuning{best_t.a_warps_per_sm, best_t.b_ctas_per_sm, f}, &ms)) != DC_OK) break;
+            if (ms < best_ms) { best_ms = ms; best_t.b_sparse_fill = f; }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->tune = (s == DC_OK) ? best_t : saved;
     best->a_warps_per_sm = ctx->tune.a_warps_per_sm;
     best->b_ctas_per_sm = ctx->tune.b_ctas_per_sm;
+    best->b_sparse_fill = ctx->tune.b_sparse_fill;
     return s;
 }
 

@@ -137,7 +137,7 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     const int tiles_a = tiles_x_a * ((H + band_a - 1) / band_a);
     const int tiles_x_b = (W + kTileBW - 1) / kTileBW;
     const int tiles_b = tiles_x_b * ((H + kTileBH - 1) / kTileBH);
-    if ((long long)tiles_a * n > INT32_MAX / 2 || (long long)tiles_b * n + 1 > DC_NOALLOC_WORK_INTS)
+    if ((long long)tiles_a * n > INT32_MAX / 2 || (long long)tiles_b * n + 2 > DC_NOALLOC_WORK_INTS)
         return DC_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
 
@@ -163,6 +163,7 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
         bp.extend_top = params->extend_top ? 1 : 0;
         bp.extend_rows = params->extend_rows;
         bp.stop = params->stop_after;
+        bp.sparse_fill_max = kDefaultTuning.b_sparse_fill;
         const double ss = params->blur == DC_BLUR_BILATERAL ? params->sigma_space : 1.0;
         const double sc = params->blur == DC_BLUR_BILATERAL ? params->sigma_color : 1.0;
         for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));

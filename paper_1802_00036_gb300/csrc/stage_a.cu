@@ -300,7 +300,7 @@ stage_a_stream(const FrameDesc* __restrict__ frames, int n_frames, int total_uni
     constexpr int OW = kSW - 2 * Rh;  // output columns per strip
     const int lane = threadIdx.x & 31;
     const int unit = blockIdx.x * (kThreadsA / 32) + (threadIdx.x >> 5);
-    if (worklist && unit == 0 && lane == 0) worklist[0] = 0;
+    if (worklist && unit == 0 && lane < 2) worklist[lane] = 0;  // step-6 count, tile counter
     if (unit >= total_units) return;  // whole warps only
 
     const int f = find_frame<true>(frames, n_frames, unit);

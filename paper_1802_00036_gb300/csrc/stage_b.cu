@@ -371,8 +371,8 @@ __device__ void median_blur_store(const Tile& T, const StageBParams& p, const fl
 }
 
 // Step 6 at one empty pixel (y, x): the maximum of E over the in-frame part
-// of its (2 Rl + 1)^2 window, read from C (L2) with step 5 applied.  One
-// warp per pixel, lane = column offset; returns the maximum in every lane.
+// of its (2 Rl + 1)^2 window, read from C with step 5 applied.  One warp per
+// pixel, lane = column offset; returns the maximum in every lane.
 __device__ float large_fill_at(const Tile& T, const StageBParams& p, int y, int x, int lane)
 {
     const int Rl = p.large_radius, H = T.fd.H, W = T.fd.W;
@@ -400,7 +400,8 @@ __device__ float large_fill_at(const Tile& T, const StageBParams& p, int y, int 
     return m;
 }
 
-// Empty pixels a tile fills itself; more go to the worklist (phase 2).
+// Capacity of the list of empty pixels a tile fills itself; a tile with
+// more than StageBParams::sparse_fill_max (<= this) goes to the worklist.
 constexpr int kMaxSparseFill = 160;
 
 // The median input region as 16-byte chunks: kER rows x kChunksPerRow.  The
@@ -533,9 +534,9 @@ __device__ void constant_tile_store(const Tile& T, const StageBParams& p, const 
 
 constexpr size_t kMainSmemFloats = 2 * kER * kES + kPR * kES + kMR * kMS + 2 * kEC + kMaxSparseFill + 4;
 
-// Phase 1, persistent: each CTA walks tiles blockIdx.x, + gridDim.x, ...,
-// copying the next tile's region (cp.async) and column tops while it
-// computes the current one.
+// Phase 1, persistent: CTA i starts with tile i and then takes the next
+// unclaimed tile from a counter, copying that tile's region (cp.async) and
+// column tops while it computes the current one.
 __global__ void __launch_bounds__(kThreadsB, 3)
 stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles, StageBParams p,
              int* __restrict__ worklist)
@@ -548,6 +549,7 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
     float* cval = reinterpret_cast<float*>(ctop + kEC);
     int* elist = reinterpret_cast<int*>(cval + kEC);
     int* ecount = elist + kMaxSparseFill;
+    __shared__ int ebox[4];  // region rows / columns spanned by the empty pixels: kmin, kmax, lmin, lmax
 
     const int tid = threadIdx.x;
     int t = blockIdx.x;
@@ -555,20 +557,28 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
     Tile T = tile_of(frames, n_frames, t);
     issue_region(T, Ebuf);
     load_tops(T, p, T.x0 - 4, kEC, ctop, cval);
-    if (tid == 0) *ecount = 0;
+    if (tid == 0) {
+        *ecount = 0;
+        ebox[0] = ebox[2] = 1 << 20;
+        ebox[1] = ebox[3] = -1;
+    }
     __syncthreads();
     // does step 5 reach this tile's region (some column's top below its first row)?
     bool ext_tile = __syncthreads_or(tid < kEC && ctop[tid] != kNoTop && ctop[tid] > T.y0 - 4);
 
+    __shared__ int s_next;
     for (int it = 0;; ++it) {
         float* E = Ebuf + (it & 1) * (kER * kES);
         float* Enext = Ebuf + ((it + 1) & 1) * (kER * kES);
         const int H = T.fd.H, W = T.fd.W;
+        // tiles after the first gridDim.x go to whichever CTA is free first,
+        // so one slow tile (many empty pixels) does not hold up others
+        if (tid == 0) s_next = (int)gridDim.x + atomicAdd(worklist + 1, 1);
         cp_async_wait_all();
         __syncthreads();
 
         // copy the next tile while this one is computed
-        const int tn = t + gridDim.x;
+        const int tn = s_next;
         const bool more = tn < total_tiles;
         Tile Tn = T;
         int ntop = kNoTop;
@@ -617,6 +627,10 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
                     if (counted && p.large_fill_on && is_empty(v[e])) {
                         const int slot = atomicAdd(ecount, 1);
                         if (slot < kMaxSparseFill) elist[slot] = (k << 16) | (4 * q + e);
+                        atomicMin(ebox + 0, k);
+                        atomicMax(ebox + 1, k);
+                        atomicMin(ebox + 2, 4 * q + e);
+                        atomicMax(ebox + 3, 4 * q + e);
                     }
                 }
             }
@@ -636,21 +650,69 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
         };
         if (p.stop == kStopExtend) {
             store_tile(E);
-        } else if (n_empty > kMaxSparseFill) {
+        } else if (n_empty > p.sparse_fill_max) {
             if (tid == 0) {
                 const int slot = atomicAdd(worklist, 1);
-                worklist[1 + slot] = t;
+                worklist[2 + slot] = t;
             }
         } else {
-            if (n_empty > 0) {  // step 6 at the few empty pixels, one warp each
-                // E and K are only written here (at empty pixels); large_fill_at reads C
-                const int warp = tid >> 5, lane = tid & 31;
-                for (int j = warp; j < n_empty; j += kThreadsB / 32) {
-                    const int k = elist[j] >> 16, l = elist[j] & 0xFFFF;
-                    const float m = large_fill_at(T, p, T.y0 - 4 + k, T.x0 - 4 + l, lane);
-                    if (lane == 0) {
+            if (n_empty > 0) {
+                // step 6 at the few empty pixels.  E and K are only written here (at
+                // empty pixels); the window maxima read C.
+                const int Rl = p.large_radius;
+                // the union of their windows: frame rows [by0, by1], columns [bx0, bx1]
+                const int by0 = max(0, T.y0 - 4 + ebox[0] - Rl), by1 = min(H - 1, T.y0 - 4 + ebox[1] + Rl);
+                const int bx0 = max(0, T.x0 - 4 + ebox[2] - Rl), bx1 = min(W - 1, T.x0 - 4 + ebox[3] + Rl);
+                const int ex0 = T.x0 - 4 + ebox[2], ex1 = T.x0 - 4 + ebox[3];  // columns with empty pixels
+                const int BR = by1 - by0 + 1, BC = bx1 - bx0 + 1, EC = ex1 - ex0 + 1;
+                if (BR * BC + BR * EC <= kMR * kMS) {
+                    // the union box in M (idle until the median): E with step 5 ...
+                    float* box = M;
+                    float* rmax = M + BR * BC;
+                    for (int i = tid; i < BR * BC; i += kThreadsB) {
+                        const int r = i / BC, c = i - r * BC;
+                        const int y = by0 + r, x = bx0 + c;
+                        int top = kNoTop;
+                        float tv = 0.0f;
+                        if (p.extend_top) {
+                            const int t2 = __ldg(T.fd.top + x);
+                            if (t2 < H) {
+                                top = t2;
+                                tv = __ldg(T.fd.c + (size_t)t2 * T.fd.c_pitch + x);
+                            }
+                        }
+                        box[i] = extended(T, p, y, x, top, tv);
+                    }
+                    __syncthreads();
+                    // ... row maxima over the window width at the empty columns ...
+                    for (int i = tid; i < BR * EC; i += kThreadsB) {
+                        const int r = i / EC, c = ex0 + (i - r * EC);
+                        const int lo = max(c - Rl, bx0) - bx0, hi = min(c + Rl, bx1) - bx0;
+                        float m = ninf();
+                        for (int x = lo; x <= hi; ++x) m = fmaxf(m, box[r * BC + x]);
+                        rmax[i] = m;
+                    }
+                    __syncthreads();
+                    // ... and column maxima at each empty pixel
+                    for (int j = tid; j < n_empty; j += kThreadsB) {
+                        const int k = elist[j] >> 16, l = elist[j] & 0xFFFF;
+                        const int y = T.y0 - 4 + k, x = T.x0 - 4 + l;
+                        const int lo = max(y - Rl, by0) - by0, hi = min(y + Rl, by1) - by0;
+                        float m = ninf();
+                        for (int r = lo; r <= hi; ++r) m = fmaxf(m, rmax[r * EC + (x - ex0)]);
                         E[k * kES + l] = m;
                         put_key(K, k, l, key_of(m, keys_ok));
+                    }
+                } else {
+                    // too wide for the box: one warp per pixel, windows read from C
+                    const int warp = tid >> 5, lane = tid & 31;
+                    for (int j = warp; j < n_empty; j += kThreadsB / 32) {
+                        const int k = elist[j] >> 16, l = elist[j] & 0xFFFF;
+                        const float m = large_fill_at(T, p, T.y0 - 4 + k, T.x0 - 4 + l, lane);
+                        if (lane == 0) {
+                            E[k * kES + l] = m;
+                            put_key(K, k, l, key_of(m, keys_ok));
+                        }
                     }
                 }
                 __syncthreads();
@@ -685,7 +747,11 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
             ctop[tid] = ntop;
             cval[tid] = ntopval;
         }
-        if (tid == 0) *ecount = 0;
+        if (tid == 0) {
+            *ecount = 0;
+            ebox[0] = ebox[2] = 1 << 20;
+            ebox[1] = ebox[3] = -1;
+        }
         T = Tn;
         t = tn;
         ext_tile = __syncthreads_or(tid < kEC && ntop != kNoTop && ntop > T.y0 - 4);
@@ -712,7 +778,7 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
     const int tid = threadIdx.x;
     for (int w = blockIdx.x; w < count; w += gridDim.x) {
         __syncthreads();
-        const Tile T = tile_of(frames, n_frames, worklist[1 + w]);
+        const Tile T = tile_of(frames, n_frames, worklist[2 + w]);
         const int H = T.fd.H, W = T.fd.W;
         const int gy = T.y0 - 4 - Rl, gx = T.x0 - 4 - Rl;  // frame position of G(0, 0)
         load_tops(T, p, gx, GC, ctop, cval);

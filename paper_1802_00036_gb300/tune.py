@@ -54,7 +54,7 @@ def save_cache(data: dict, path: str | None = None) -> None:
 def tuned(ctx, inp, out, p: dc.dc_params | None = None, stream=None, use_cache: bool = True):
     """Apply the best tuning for this workload to `ctx` (from the cache, or by
     running dc_autotune on `inp` -> `out`, (n, H, W) float32 CUDA tensors) and
-    return (a_warps_per_sm, b_ctas_per_sm, source)."""
+    return ((a_warps_per_sm, b_ctas_per_sm, b_sparse_fill), source)."""
     import torch
     p = p if p is not None else dc.params()
     n, H, W = inp.shape
@@ -62,18 +62,18 @@ def tuned(ctx, inp, out, p: dc.dc_params | None = None, stream=None, use_cache: 
     key = cache_key(props.name, props.multi_processor_count, n, H, W, p)
     with _lock:
         data = load_cache() if use_cache else {}
-        if key in data:
-            a, b = data[key]
-            dc.dc_set_tuning(ctx.h, a, b)
-            return a, b, "cache"
+        if key in data and len(data[key]) == 3:
+            a, b, f = data[key]
+            dc.dc_set_tuning(ctx.h, a, b, f)
+            return (a, b, f), "cache"
     s = Context_stream(stream)
-    a, b = dc.dc_autotune(ctx.h, inp.data_ptr(), out.data_ptr(), n, H, W, p, s)
+    t = dc.dc_autotune(ctx.h, inp.data_ptr(), out.data_ptr(), n, H, W, p, s)
     if use_cache:
         with _lock:
             data = load_cache()
-            data[key] = [a, b]
+            data[key] = list(t)
             save_cache(data)
-    return a, b, "measured"
+    return t, "measured"
 
 
 def Context_stream(stream) -> int:

@@ -68,8 +68,8 @@ def test_tune_cache_round_trip(tmp_path, monkeypatch):
     p = dc.params()
     k = tune.cache_key("GB300", 152, 64, 352, 1216, p)
     assert k != tune.cache_key("GB300", 152, 64, 352, 1216, dc.params(blur="bilateral"))
-    tune.save_cache({k: [6, 3]})
-    assert tune.load_cache()[k] == [6, 3]
+    tune.save_cache({k: [6, 3, 16]})
+    assert tune.load_cache()[k] == [6, 3, 16]
     (tmp_path / "t.json").write_text("not json")
     assert tune.load_cache() == {}
 

@@ -212,8 +212,8 @@ def test_results_do_not_depend_on_tuning(ctx):
     frames = synth.make_batch(6, synth.UNIFORM_375, config=4)
     x = torch.from_numpy(frames).cuda()
     ref = None
-    for a, b in ((12, 3), (1, 1), (3, 2), (64, 1)):
-        dc.dc_set_tuning(ctx.h, a, b)
+    for a, b, f in ((12, 3, 16), (1, 1, 0), (3, 2, 160), (64, 1, 4)):
+        dc.dc_set_tuning(ctx.h, a, b, f)
         y = torch.full_like(x, -2.0)
         ctx.complete(x, y)
         torch.cuda.synchronize()
@@ -222,9 +222,9 @@ def test_results_do_not_depend_on_tuning(ctx):
             ref = got
         assert np.array_equal(got, ref), (a, b)
     y = torch.empty_like(x)
-    a, b = dc.dc_autotune(ctx.h, x.data_ptr(), y.data_ptr(), 6, 375, 1242, dc.params())
-    assert 1 <= a <= 64 and 1 <= b <= 3 and dc.dc_get_tuning(ctx.h) == (a, b)
-    dc.dc_set_tuning(ctx.h, 12, 3)
+    a, b, f = dc.dc_autotune(ctx.h, x.data_ptr(), y.data_ptr(), 6, 375, 1242, dc.params())
+    assert 1 <= a <= 64 and 1 <= b <= 3 and 0 <= f <= 160 and dc.dc_get_tuning(ctx.h) == (a, b, f)
+    dc.dc_set_tuning(ctx.h, 6, 3, 16)
     with pytest.raises(dc.DcError):
         dc.dc_set_tuning(ctx.h, 0, 3)
 
