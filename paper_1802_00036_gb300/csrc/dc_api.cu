@@ -1,5 +1,5 @@
 // dc_api.cu -- the C-ABI of libdc (include/dc.h): argument checks, scratch,
-// frame tables and the two kernel launches per call.
+// frame tables and the kernel launches of each call.
 #include "../../include/dc.h"
 #include "common.cuh"
 
@@ -12,20 +12,10 @@
 
 using namespace dcgb;
 
-// Calls rotate over kSlots frame tables so that the host only waits when
-// kSlots calls are still in flight; each slot's event marks the end of the
-// call that last used it.
-constexpr int kSlots = 16;
 // dc_complete_host splits a batch into at most this many chunks so that the
 // copy in of chunk i + 1, the kernels of chunk i and the copy out of chunk
 // i - 1 overlap.
 constexpr int kIoChunksMax = 16;
-
-struct TableSlot {
-    FrameDesc* d = nullptr;      // device copy read by the kernels
-    FrameDesc* h = nullptr;      // pinned staging
-    cudaEvent_t done = nullptr;  // recorded after the call's last kernel
-};
 
 struct dc_ctx {
     int device = 0;
@@ -41,8 +31,9 @@ struct dc_ctx {
     size_t work_cap = 0;      // ints
     double* acc = nullptr;    // accuracy sums and results, 10 doubles per frame
     int acc_cap = 0;          // frames
-    TableSlot slot[kSlots];
-    int frames_cap = 0;       // descriptors per slot
+    FrameDesc* table = nullptr;  // frame descriptors of the current call (device)
+    int frames_cap = 0;          // descriptors
+    cudaEvent_t done = nullptr;  // recorded after each call's last kernel
     unsigned long long calls = 0;
     // staging for host calls: copy streams and events of the chunk pipeline
     float* io_in = nullptr;
@@ -84,7 +75,7 @@ size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 size_t scratch_bytes(size_t c_floats, size_t top_ints, int frames, size_t io_floats, size_t work_ints)
 {
     return c_floats * sizeof(float) + top_ints * sizeof(int) + work_ints * sizeof(int) +
-           (size_t)kSlots * (size_t)frames * sizeof(FrameDesc) + 2 * io_floats * sizeof(float);
+           (size_t)frames * sizeof(FrameDesc) + 2 * io_floats * sizeof(float);
 }
 
 bool params_ok(const dc_params* p)
@@ -143,20 +134,10 @@ dc_status grow(dc_ctx* ctx, size_t c_floats, size_t top_ints, int frames, size_t
         ctx->work_cap = nw;
     }
     if (nf > ctx->frames_cap) {
+        cudaFree(ctx->table);
+        ctx->table = nullptr;
         ctx->frames_cap = 0;
-        for (TableSlot& sl : ctx->slot) {
-            cudaFree(sl.d);
-            cudaFreeHost(sl.h);
-            sl.d = nullptr;
-            sl.h = nullptr;
-        }
-        for (TableSlot& sl : ctx->slot) {
-            if (cudaMalloc(&sl.d, nf * sizeof(FrameDesc)) != cudaSuccess ||
-                cudaMallocHost(&sl.h, nf * sizeof(FrameDesc)) != cudaSuccess) {
-                cudaGetLastError();
-                return DC_ERR_OOM;
-            }
-        }
+        if (cudaMalloc(&ctx->table, nf * sizeof(FrameDesc)) != cudaSuccess) { cudaGetLastError(); return DC_ERR_OOM; }
         ctx->frames_cap = nf;
     }
     if (ni > ctx->io_cap) {
@@ -175,6 +156,60 @@ dc_status grow(dc_ctx* ctx, size_t c_floats, size_t top_ints, int frames, size_t
 }
 
 int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// The frame descriptors reach the device as kernel parameters, K at a time,
+// and a kernel stores them; the same launch resets the column tops.  A
+// host-to-device copy would queue on the copy engine behind whatever large
+// transfers the caller has in flight (dc_complete_host's own copy-in of the
+// next chunk), holding back the kernels of this call.
+template <int K>
+struct TableChunk {
+    FrameDesc d[K];
+};
+static_assert(sizeof(TableChunk<384>) + 64 <= 32764, "kernel parameter space");
+
+template <int K>
+__global__ void table_put(const __grid_constant__ TableChunk<K> src, FrameDesc* __restrict__ dst, int n,
+                          int* __restrict__ top, size_t top_ints)
+{
+    const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = tid; i < (size_t)n; i += stride) dst[i] = src.d[i];
+    if (top)
+        for (size_t i = tid; i < top_ints; i += stride) top[i] = kNoTop;
+}
+
+template <int K>
+cudaError_t table_put_chunk(const FrameDesc* desc, int n, FrameDesc* dst, int* top, size_t top_ints, int sms,
+                            cudaStream_t stream)
+{
+    TableChunk<K> c;
+    std::memcpy(c.d, desc, (size_t)n * sizeof(FrameDesc));
+    size_t blocks = (top_ints + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > (size_t)2 * sms) blocks = (size_t)2 * sms;
+    table_put<K><<<(unsigned)blocks, 256, 0, stream>>>(c, dst, n, top, top_ints);
+    return cudaGetLastError();
+}
+
+// Store n descriptors at dst (chunks of up to 384 per launch) and reset
+// top_ints column tops; returns the number of launches through *launches.
+cudaError_t put_table(const FrameDesc* desc, int n, FrameDesc* dst, int* top, size_t top_ints, int sms,
+                      cudaStream_t stream, int* launches)
+{
+    *launches = 0;
+    for (int i = 0; i < n; i += 384) {
+        const int m = n - i < 384 ? n - i : 384;
+        int* t = i == 0 ? top : nullptr;
+        const size_t ti = i == 0 ? top_ints : 0;
+        cudaError_t e = m <= 8    ? table_put_chunk<8>(desc + i, m, dst + i, t, ti, sms, stream)
+                      : m <= 64   ? table_put_chunk<64>(desc + i, m, dst + i, t, ti, sms, stream)
+                                  : table_put_chunk<384>(desc + i, m, dst + i, t, ti, sms, stream);
+        if (e != cudaSuccess) return e;
+        ++*launches;
+    }
+    return cudaSuccess;
+}
 
 // Scratch one frame needs: step-4 map rows padded to 32 floats, tops padded.
 size_t frame_c_floats(int H, int W) { return round_up((size_t)W, 32) * (size_t)H; }
@@ -225,19 +260,14 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         d.top = need_b ? ctx->top + reinterpret_cast<size_t>(d.top) : nullptr;
     }
 
-    // frame table: take the next slot once the call that last used it is done
-    TableSlot& sl = ctx->slot[ctx->calls % kSlots];
-    if (cudaEventSynchronize(sl.done) != cudaSuccess) return DC_ERR_CUDA;
     // calls share the scratch: order this one after the previous call
     if (ctx->last_done && stream != ctx->last_stream &&
         cudaStreamWaitEvent(stream, ctx->last_done, 0) != cudaSuccess)
         return DC_ERR_CUDA;
-    std::memcpy(sl.h, desc.data(), desc.size() * sizeof(FrameDesc));
-    if (cudaMemcpyAsync(sl.d, sl.h, desc.size() * sizeof(FrameDesc), cudaMemcpyHostToDevice, stream) !=
-        cudaSuccess)
-        return DC_ERR_CUDA;
-
-    if (need_b && cudaMemsetAsync(ctx->top, 0x7F, top_off * sizeof(int), stream) != cudaSuccess)
+    // the descriptors and the reset of the tops, written by a kernel
+    int table_launches = 0;
+    if (put_table(desc.data(), n, ctx->table, need_b ? ctx->top : nullptr, need_b ? top_off : 0, ctx->sm_count,
+                  stream, &table_launches) != cudaSuccess)
         return DC_ERR_CUDA;
 
     cudaEvent_t* ev = nullptr;
@@ -249,10 +279,10 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         if (cudaEventRecord(ev[0], stream) != cudaSuccess) return DC_ERR_CUDA;
     }
     const int stop_a = need_b ? kStopFull : p->stop_after;
-    cudaError_t e = launch_stage_a(sl.d, n, (int)tiles_a, p->first_kernel, stop_a,
+    cudaError_t e = launch_stage_a(ctx->table, n, (int)tiles_a, p->first_kernel, stop_a,
                                    need_b ? ctx->work : nullptr, ctx->sm_count, stream);
     if (e != cudaSuccess) return DC_ERR_CUDA;
-    ctx->last_launches = 1;
+    ctx->last_launches = table_launches + 1;
     if (ev && cudaEventRecord(ev[1], stream) != cudaSuccess) return DC_ERR_CUDA;
     if (need_b) {
         StageBParams bp{};
@@ -268,14 +298,14 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         const double sc = p->blur == DC_BLUR_BILATERAL ? p->sigma_color : 1.0;
         for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));
         bp.inv_2sc2 = (float)(1.0 / (2.0 * sc * sc));
-        e = launch_stage_b(sl.d, n, (int)tiles_b, bp, ctx->work, ctx->sm_count, ctx->tune.b_ctas_per_sm, stream);
+        e = launch_stage_b(ctx->table, n, (int)tiles_b, bp, ctx->work, ctx->sm_count, ctx->tune.b_ctas_per_sm, stream);
         if (e != cudaSuccess) return DC_ERR_CUDA;
         // stage B is one kernel, plus the step-6 pass when step 6 can run
-        ctx->last_launches = (bp.large_fill_on && bp.stop != kStopExtend) ? 3 : 2;
+        ctx->last_launches = table_launches + ((bp.large_fill_on && bp.stop != kStopExtend) ? 3 : 2);
     }
     if (ev && cudaEventRecord(ev[2], stream) != cudaSuccess) return DC_ERR_CUDA;
-    if (cudaEventRecord(sl.done, stream) != cudaSuccess) return DC_ERR_CUDA;
-    ctx->last_done = sl.done;
+    if (cudaEventRecord(ctx->done, stream) != cudaSuccess) return DC_ERR_CUDA;
+    ctx->last_done = ctx->done;
     ctx->last_stream = stream;
     ++ctx->calls;
     return DC_OK;
@@ -345,8 +375,7 @@ dc_status dc_create(dc_ctx** out, int device, size_t scratch_budget_bytes)
     ctx->budget = scratch_budget_bytes;
     DeviceGuard g(device);
     bool ok = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) == cudaSuccess;
-    for (TableSlot& sl : ctx->slot)
-        ok = ok && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&ctx->done, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         dc_destroy(ctx);
@@ -649,11 +678,8 @@ void dc_destroy(dc_ctx* ctx)
         cudaFree(ctx->top);
         cudaFree(ctx->work);
         cudaFree(ctx->acc);
-        for (TableSlot& sl : ctx->slot) {
-            cudaFree(sl.d);
-            cudaFreeHost(sl.h);
-            if (sl.done) cudaEventDestroy(sl.done);
-        }
+        cudaFree(ctx->table);
+        if (ctx->done) cudaEventDestroy(ctx->done);
         cudaFree(ctx->io_in);
         cudaFree(ctx->io_out);
         for (cudaEvent_t e : ctx->io_ev)
