@@ -100,7 +100,7 @@ struct Tuning {
     int b_ctas_per_sm;    // stage B: persistent CTAs per SM (1..3)
     int b_sparse_fill;    // stage B: most empty pixels a tile fills itself (0..160)
 };
-constexpr Tuning kDefaultTuning{6, 3, 160};
+constexpr Tuning kDefaultTuning{8, 5, 160};
 
 // Launchers (stage_a.cu, stage_b.cu).  Return cudaGetLastError().
 // `worklist` holds 2 + (stage B tiles) ints: the number of stage-B tiles

@@ -530,7 +530,7 @@ dc_status dc_metrics(dc_ctx* ctx, const float* pred, const float* gt, int n, int
 dc_status dc_set_tuning(dc_ctx* ctx, const dc_tuning* t)
 {
     if (!ctx || !t || t->a_warps_per_sm < 1 || t->a_warps_per_sm > 64 || t->b_ctas_per_sm < 1 ||
-        t->b_ctas_per_sm > 3 || t->b_sparse_fill < 0 || t->b_sparse_fill > 160)
+        t->b_ctas_per_sm > 5 || t->b_sparse_fill < 0 || t->b_sparse_fill > 160)
         return DC_ERR_INVALID_ARG;
     ctx->tune = Tuning{t->a_warps_per_sm, t->b_ctas_per_sm, t->b_sparse_fill};
     return DC_OK;
@@ -574,7 +574,7 @@ dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, in
     };
     // coordinate descent: each knob in turn over its candidates, the others fixed
     static const int a_cand[] = {2, 3, 4, 6, 8, 12, 16, 24};
-    static const int b_cand[] = {1, 2, 3};
+    static const int b_cand[] = {1, 2, 3, 4, 5};
     static const int f_cand[] = {0, 4, 8, 16, 32, 64, 160};
     Tuning best_t = saved;
     float best_ms = 1e30f;

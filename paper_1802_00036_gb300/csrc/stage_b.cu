@@ -2,7 +2,7 @@
 //
 // Output tile kTBH x kTBW.  Phase 1 (persistent CTAs) brings the step-4 map
 // C over the tile plus a 4-pixel ring (median 2 + blur 2) into shared memory
-// with cp.async, one tile ahead, and applies step 5 in place (a pixel above
+// with cp.async and applies step 5 in place (a pixel above
 // its column's top row takes C(top, x), which is what copying the topmost
 // value to row 0 gives).  Step 6 changes only empty pixels: a tile with a
 // few of them in that region fills each with one warp (the maximum over its
@@ -88,7 +88,7 @@ __device__ __forceinline__ unsigned key_of(float v, bool& ok)
 // The float value of a 16-bit key: exactly k / 256.
 __device__ __forceinline__ float value_of(unsigned k)
 {
-    return (__uint_as_float(0x4B000000u | k) - 8388608.0f) * 0.00390625f;
+    return __uint_as_float(0x47000000u | k) - 32768.0f;  // (2^15 + k / 256) - 2^15
 }
 
 __device__ __forceinline__ int clampi(int p, int n) { return p < 0 ? 0 : (p >= n ? n - 1 : p); }
@@ -192,84 +192,45 @@ __device__ __forceinline__ float extended(const Tile& T, const StageBParams& p, 
     return above_top(p, y, top) ? topval : T.fd.c[(size_t)y * T.fd.c_pitch + x];
 }
 
-// The shared tail.  F: the median input (kER x kES floats, border
-// replicated).  K: the same values as packed 16-bit keys (row k of the top
-// half in the low halves of K row k, row k + kHalf in the high halves) when
-// `keys` is set.  Median into M (kMR x kMS), mirrored ring, blur, inversion,
-// store.  R (kMR x kRS floats) may alias F.
-__device__ void median_blur_store(const Tile& T, const StageBParams& p, const float* __restrict__ F,
-                                  const unsigned* __restrict__ K, bool keys, float* __restrict__ M,
-                                  float* __restrict__ R)
+// The median output region M (kMR x kMS): 16-bit keys (Mk) after the packed
+// median, floats (Mf) otherwise.  These read one value as a float.
+template <bool KEYS>
+__device__ __forceinline__ float m_at(const float* __restrict__ Mf, const unsigned short* __restrict__ Mk, int i)
+{
+    if constexpr (KEYS) return value_of(Mk[i]);
+    else return Mf[i];
+}
+
+// Eight consecutive values of M from index i (a multiple of 4).
+template <bool KEYS>
+__device__ __forceinline__ void m_row8(const float* __restrict__ Mf, const unsigned short* __restrict__ Mk, int i,
+                                       float (&v)[8])
+{
+    if constexpr (KEYS) {
+        const uint2 lo = *reinterpret_cast<const uint2*>(Mk + i);
+        const uint2 hi = *reinterpret_cast<const uint2*>(Mk + i + 4);
+        const unsigned w[4] = {lo.x, lo.y, hi.x, hi.y};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[2 * j] = value_of(w[j] & 0xFFFFu);
+            v[2 * j + 1] = value_of(w[j] >> 16);
+        }
+    } else {
+        const float4 lo = *reinterpret_cast<const float4*>(Mf + i);
+        const float4 hi = *reinterpret_cast<const float4*>(Mf + i + 4);
+        v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+        v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+    }
+}
+
+// After the median: mirrored ring, blur, inversion, store.  R (kMR x kRS
+// floats) is the Gaussian row-pass buffer; it must not overlap M.
+template <bool KEYS>
+__device__ void blur_store(const Tile& T, const StageBParams& p, float* __restrict__ Mf,
+                           unsigned short* __restrict__ Mk, float* __restrict__ R)
 {
     const int H = T.fd.H, W = T.fd.W;
     const int tid = threadIdx.x;
-    // -- step 7: median, blocks (rb, cb) and (rb + kHalf / 2, cb) of 2 x 8
-    {
-        const int rb = tid / (kMC / 8), cb = tid % (kMC / 8);
-        if (!p.median) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int r = 0; r < 2; ++r)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int a = 2 * rb + h * kHalf + r, b = 8 * cb + j;
-                        M[a * kMS + b] = F[(a + 2) * kES + b + 2];
-                    }
-        } else if (keys) {
-            unsigned x[6][12];
-            const unsigned* src = K + (2 * rb) * kES + 8 * cb;
-#pragma unroll
-            for (int r = 0; r < 6; ++r)
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const uint4 v = *reinterpret_cast<const uint4*>(src + r * kES + 4 * q);
-                    x[r][4 * q + 0] = v.x;
-                    x[r][4 * q + 1] = v.y;
-                    x[r][4 * q + 2] = v.z;
-                    x[r][4 * q + 3] = v.w;
-                }
-            unsigned m[2][8];
-            median_block_2x8<unsigned, PackedKeyOps>(x, m);
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    float o[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) o[j] = value_of(h ? (m[r][j] >> 16) : (m[r][j] & 0xFFFFu));
-                    float* dst = M + (2 * rb + h * kHalf + r) * kMS + 8 * cb;
-                    *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
-                    *reinterpret_cast<float4*>(dst + 4) = make_float4(o[4], o[5], o[6], o[7]);
-                }
-        } else {
-#pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                float x[6][12];
-                const float* src = F + (2 * rb + h * kHalf) * kES + 8 * cb;
-#pragma unroll
-                for (int r = 0; r < 6; ++r)
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const float4 v = *reinterpret_cast<const float4*>(src + r * kES + 4 * q);
-                        x[r][4 * q + 0] = v.x;
-                        x[r][4 * q + 1] = v.y;
-                        x[r][4 * q + 2] = v.z;
-                        x[r][4 * q + 3] = v.w;
-                    }
-                float m[2][8];
-                median_block_2x8<float, FloatOps>(x, m);
-                float* dst = M + (2 * rb + h * kHalf) * kMS + 8 * cb;
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    *reinterpret_cast<float4*>(dst + r * kMS) = make_float4(m[r][0], m[r][1], m[r][2], m[r][3]);
-                    *reinterpret_cast<float4*>(dst + r * kMS + 4) =
-                        make_float4(m[r][4], m[r][5], m[r][6], m[r][7]);
-                }
-            }
-        }
-    }
-    __syncthreads();
     // -- mirror the ring outside the frame (the blur's reflect-101 border):
     // only the two rows / columns beyond each edge are read by the blur
     const bool edge = T.y0 < 2 || T.x0 < 2 || T.y0 + kTBH + 2 > H || T.x0 + kTBW + 2 > W;
@@ -281,7 +242,8 @@ __device__ void median_blur_store(const Tile& T, const StageBParams& p, const fl
             const int y = T.y0 - 2 + a, x = T.x0 - 2 + b;
             if (y < -2 || y >= H + 2 || x < -2 || x >= W + 2) continue;
             const int sy = reflect101(y, H) - (T.y0 - 2), sx = reflect101(x, W) - (T.x0 - 2);
-            M[a * kMS + b] = M[sy * kMS + sx];
+            if constexpr (KEYS) Mk[a * kMS + b] = Mk[sy * kMS + sx];
+            else Mf[a * kMS + b] = Mf[sy * kMS + sx];
         }
         __syncthreads();
     }
@@ -289,7 +251,7 @@ __device__ void median_blur_store(const Tile& T, const StageBParams& p, const fl
         for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
             const int a = i / kTBW, b = i - a * kTBW;
             const int y = T.y0 + a, x = T.x0 + b;
-            if (y < H && x < W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = M[(a + 2) * kMS + b + 2];
+            if (y < H && x < W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = m_at<KEYS>(Mf, Mk, (a + 2) * kMS + b + 2);
         }
         return;
     }
@@ -298,9 +260,8 @@ __device__ void median_blur_store(const Tile& T, const StageBParams& p, const fl
         // row pass over all kMR rows of M, the tile's kTBW columns -> R
         for (int i = tid; i < kMR * (kTBW / 4); i += kThreadsB) {
             const int a = i / (kTBW / 4), b0 = 4 * (i - a * (kTBW / 4));
-            const float4 lo = *reinterpret_cast<const float4*>(M + a * kMS + b0);
-            const float4 hi = *reinterpret_cast<const float4*>(M + a * kMS + b0 + 4);
-            const float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+            float v[8];
+            m_row8<KEYS>(Mf, Mk, a * kMS + b0, v);
             float o[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -331,7 +292,7 @@ __device__ void median_blur_store(const Tile& T, const StageBParams& p, const fl
             for (int k = 0; k < kStripRows; ++k) {
                 const int y = T.y0 + a0 + k;
                 if (y >= H) break;
-                const float m = M[(a0 + k + 2) * kMS + b + 2];
+                const float m = m_at<KEYS>(Mf, Mk, (a0 + k + 2) * kMS + b + 2);
                 float acc = w0 * r[k];
                 acc = fmaf(w1, r[k + 1], acc);
                 acc = fmaf(w2, r[k + 2], acc);
@@ -345,7 +306,7 @@ __device__ void median_blur_store(const Tile& T, const StageBParams& p, const fl
             for (int k = 0; k < kStripRows; ++k) {
                 const int a = a0 + k, y = T.y0 + a;
                 if (y >= H) break;
-                const float m = M[(a + 2) * kMS + b + 2];
+                const float m = m_at<KEYS>(Mf, Mk, (a + 2) * kMS + b + 2);
                 float g = m;
                 if (!is_empty(m) && p.blur == kBlurBilateral) {
                     float num = 0.0f, den = 0.0f;
@@ -355,7 +316,7 @@ __device__ void median_blur_store(const Tile& T, const StageBParams& p, const fl
                         for (int dx = -2; dx <= 2; ++dx) {
                             const int r2 = dy * dy + dx * dx;
                             if (r2 > 4) continue;
-                            const float v = M[(a + 2 + dy) * kMS + b + 2 + dx];
+                            const float v = m_at<KEYS>(Mf, Mk, (a + 2 + dy) * kMS + b + 2 + dx);
                             const float d = v - m;
                             const float wgt = p.ws[r2] * expf(-(d * d) * p.inv_2sc2);
                             num = fmaf(v, wgt, num);
@@ -368,6 +329,87 @@ __device__ void median_blur_store(const Tile& T, const StageBParams& p, const fl
             }
         }
     }
+}
+
+// The shared tail.  F: the median input (kER x kES floats, border
+// replicated).  K: the same values as packed 16-bit keys (row k of the top
+// half in the low halves of K row k, row k + kHalf in the high halves) when
+// `keys` is set.  The median goes to Mk as 16-bit keys when it ran on keys,
+// else to Mf as floats (Mf may alias K and Mk, which are then idle), then
+// blur_store.  R (kMR x kRS floats) may alias F, not Mf or Mk.
+__device__ void median_blur_store(const Tile& T, const StageBParams& p, const float* __restrict__ F,
+                                  const unsigned* __restrict__ K, bool keys, float* __restrict__ Mf,
+                                  unsigned short* __restrict__ Mk, float* __restrict__ R)
+{
+    const int tid = threadIdx.x;
+    const bool use_keys = keys && p.median;
+    // -- step 7: median, blocks (rb, cb) and (rb + kHalf / 2, cb) of 2 x 8
+    const int rb = tid / (kMC / 8), cb = tid % (kMC / 8);
+    if (!p.median) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int a = 2 * rb + h * kHalf + r, b = 8 * cb + j;
+                    Mf[a * kMS + b] = F[(a + 2) * kES + b + 2];
+                }
+    } else if (use_keys) {
+        unsigned x[6][12];
+        const unsigned* src = K + (2 * rb) * kES + 8 * cb;
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const uint4 v = *reinterpret_cast<const uint4*>(src + r * kES + 4 * q);
+                x[r][4 * q + 0] = v.x;
+                x[r][4 * q + 1] = v.y;
+                x[r][4 * q + 2] = v.z;
+                x[r][4 * q + 3] = v.w;
+            }
+        unsigned m[2][8];
+        median_block_2x8<unsigned, PackedKeyOps>(x, m);
+        // low halves: the block in the top half, high halves: the bottom one
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const unsigned sel = h ? 0x7632u : 0x5410u;
+                unsigned short* dst = Mk + (2 * rb + h * kHalf + r) * kMS + 8 * cb;
+                *reinterpret_cast<uint4*>(dst) =
+                    make_uint4(__byte_perm(m[r][0], m[r][1], sel), __byte_perm(m[r][2], m[r][3], sel),
+                               __byte_perm(m[r][4], m[r][5], sel), __byte_perm(m[r][6], m[r][7], sel));
+            }
+    } else {
+        // Mf may alias K and Mk: the float network reads only F
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            float x[6][12];
+            const float* src = F + (2 * rb + h * kHalf) * kES + 8 * cb;
+#pragma unroll
+            for (int r = 0; r < 6; ++r)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float4 v = *reinterpret_cast<const float4*>(src + r * kES + 4 * q);
+                    x[r][4 * q + 0] = v.x;
+                    x[r][4 * q + 1] = v.y;
+                    x[r][4 * q + 2] = v.z;
+                    x[r][4 * q + 3] = v.w;
+                }
+            float m[2][8];
+            median_block_2x8<float, FloatOps>(x, m);
+            float* dst = Mf + (2 * rb + h * kHalf) * kMS + 8 * cb;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                *reinterpret_cast<float4*>(dst + r * kMS) = make_float4(m[r][0], m[r][1], m[r][2], m[r][3]);
+                *reinterpret_cast<float4*>(dst + r * kMS + 4) = make_float4(m[r][4], m[r][5], m[r][6], m[r][7]);
+            }
+        }
+    }
+    __syncthreads();
+    if (use_keys) blur_store<true>(T, p, Mf, Mk, R);
+    else blur_store<false>(T, p, Mf, Mk, R);
 }
 
 // Step 6 at one empty pixel (y, x): the maximum of E over the in-frame part
@@ -532,20 +574,29 @@ __device__ void constant_tile_store(const Tile& T, const StageBParams& p, const 
     }
 }
 
-constexpr size_t kMainSmemFloats = 2 * kER * kES + kPR * kES + kMR * kMS + 2 * kEC + kMaxSparseFill + 4;
+// Shared memory of phase 1: the region E, the packed keys K, the median
+// output as 16-bit keys Mk (the float median output Mf lies over K and Mk,
+// which are idle on that path), column tops, the list of empty pixels.
+constexpr size_t kMainSmemFloats = kER * kES + kPR * kES + kMR * kMS / 2 + 2 * kEC + kMaxSparseFill + 4;
+static_assert(kPR * kES + kMR * kMS / 2 >= kMR * kMS, "the float median output fits over K and Mk");
+static_assert((kER * kES) % 4 == 0 && (kPR * kES) % 4 == 0 && kMS % 8 == 0, "16-byte aligned buffers and rows");
 
 // Phase 1, persistent: CTA i starts with tile i and then takes the next
-// unclaimed tile from a counter, copying that tile's region (cp.async) and
-// column tops while it computes the current one.
-__global__ void __launch_bounds__(kThreadsB, 3)
+// unclaimed tile from a counter.  One region buffer and 16-bit median output
+// (38 KB of shared memory in all) let five CTAs share an SM: while one waits
+// for its region (cp.async) the others compute, which hides the copy better
+// than a second buffer would (that costs CTAs per SM).
+__global__ void __launch_bounds__(kThreadsB, 5)
 stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles, StageBParams p,
              int* __restrict__ worklist)
 {
     extern __shared__ __align__(16) float smem[];
-    float* Ebuf = smem;                                                      // 2 x region
-    unsigned* K = reinterpret_cast<unsigned*>(smem + 2 * kER * kES);         // packed keys
-    float* M = smem + 2 * kER * kES + kPR * kES;
-    int* ctop = reinterpret_cast<int*>(M + kMR * kMS);
+    float* Ebuf = smem;                                                      // the region
+    unsigned* K = reinterpret_cast<unsigned*>(smem + kER * kES);             // packed keys
+    unsigned short* Mk = reinterpret_cast<unsigned short*>(K + kPR * kES);   // median output, keys
+    float* Mf = reinterpret_cast<float*>(K);                                 // median output, floats
+    float* scratch = reinterpret_cast<float*>(Mk);  // kMR * kMS / 2 floats, idle until the median
+    int* ctop = reinterpret_cast<int*>(Mk + kMR * kMS);
     float* cval = reinterpret_cast<float*>(ctop + kEC);
     int* elist = reinterpret_cast<int*>(cval + kEC);
     int* ecount = elist + kMaxSparseFill;
@@ -555,48 +606,30 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
     int t = blockIdx.x;
     if (t >= total_tiles) return;
     Tile T = tile_of(frames, n_frames, t);
-    issue_region(T, Ebuf);
-    load_tops(T, p, T.x0 - 4, kEC, ctop, cval);
-    if (tid == 0) {
-        *ecount = 0;
-        ebox[0] = ebox[2] = 1 << 20;
-        ebox[1] = ebox[3] = -1;
-    }
-    __syncthreads();
-    // does step 5 reach this tile's region (some column's top below its first row)?
-    bool ext_tile = __syncthreads_or(tid < kEC && ctop[tid] != kNoTop && ctop[tid] > T.y0 - 4);
-
     __shared__ int s_next;
     for (int it = 0;; ++it) {
-        float* E = Ebuf + (it & 1) * (kER * kES);
-        float* Enext = Ebuf + ((it + 1) & 1) * (kER * kES);
+        float* E = Ebuf;
         const int H = T.fd.H, W = T.fd.W;
-        // tiles after the first gridDim.x go to whichever CTA is free first,
-        // so one slow tile (many empty pixels) does not hold up others
-        if (tid == 0) s_next = (int)gridDim.x + atomicAdd(worklist + 1, 1);
+        issue_region(T, E);
+        load_tops(T, p, T.x0 - 4, kEC, ctop, cval);
+        if (tid == 0) {
+            *ecount = 0;
+            ebox[0] = ebox[2] = 1 << 20;
+            ebox[1] = ebox[3] = -1;
+            s_next = (int)gridDim.x + atomicAdd(worklist + 1, 1);
+        }
         cp_async_wait_all();
         __syncthreads();
-
-        // copy the next tile while this one is computed
+        const bool ext_tile = __syncthreads_or(tid < kEC && ctop[tid] != kNoTop && ctop[tid] > T.y0 - 4);
         const int tn = s_next;
         const bool more = tn < total_tiles;
-        Tile Tn = T;
-        int ntop = kNoTop;
-        if (more) {
-            Tn = tile_of(frames, n_frames, tn);
-            issue_region(Tn, Enext);
-            if (tid < kEC && p.extend_top) {
-                const int t2 = __ldcg(Tn.fd.top + clampi(Tn.x0 - 4 + tid, Tn.fd.W));
-                ntop = t2 < Tn.fd.H ? t2 : kNoTop;
-            }
-        }
 
         // a region entirely above its columns' tops: one row does for all
         const bool const_tile = __syncthreads_and(
             p.extend_top && p.extend_rows < 0 &&
             (tid >= kEC || (ctop[tid] != kNoTop && ctop[tid] > T.y0 - 4 + kER - 1)));
         if (const_tile) {
-            constant_tile_store(T, p, cval, M);
+            constant_tile_store(T, p, cval, scratch);
         } else {
         // step 5 in place, empty pixels, packed keys: row pairs (kp, kp + kHalf)
         bool keys_ok = true;
@@ -665,10 +698,10 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
                 const int bx0 = max(0, T.x0 - 4 + ebox[2] - Rl), bx1 = min(W - 1, T.x0 - 4 + ebox[3] + Rl);
                 const int ex0 = T.x0 - 4 + ebox[2], ex1 = T.x0 - 4 + ebox[3];  // columns with empty pixels
                 const int BR = by1 - by0 + 1, BC = bx1 - bx0 + 1, EC = ex1 - ex0 + 1;
-                if (BR * BC + BR * EC <= kMR * kMS) {
-                    // the union box in M (idle until the median): E with step 5 ...
-                    float* box = M;
-                    float* rmax = M + BR * BC;
+                if (BR * BC + BR * EC <= kMR * kMS / 2) {
+                    // the union box in scratch: E with step 5 ...
+                    float* box = scratch;
+                    float* rmax = scratch + BR * BC;
                     for (int i = tid; i < BR * BC; i += kThreadsB) {
                         const int r = i / BC, c = i - r * BC;
                         const int y = by0 + r, x = bx0 + c;
@@ -734,27 +767,14 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
             }
             const bool keys = __syncthreads_and(keys_ok);
             if (p.stop == kStopFillLarge) store_tile(E);
-            else median_blur_store(T, p, E, K, keys, M, E);
+            else median_blur_store(T, p, E, K, keys, Mf, Mk, E);
         }
         }
 
-        float ntopval = 0.0f;
-        if (more && tid < kEC && ntop != kNoTop)
-            ntopval = __ldcg(Tn.fd.c + (size_t)ntop * Tn.fd.c_pitch + clampi(Tn.x0 - 4 + tid, Tn.fd.W));
-        __syncthreads();  // E, K, M, ctop of this tile no longer read
+        __syncthreads();
         if (!more) break;
-        if (tid < kEC) {
-            ctop[tid] = ntop;
-            cval[tid] = ntopval;
-        }
-        if (tid == 0) {
-            *ecount = 0;
-            ebox[0] = ebox[2] = 1 << 20;
-            ebox[1] = ebox[3] = -1;
-        }
-        T = Tn;
+        T = tile_of(frames, n_frames, tn);
         t = tn;
-        ext_tile = __syncthreads_or(tid < kEC && ntop != kNoTop && ntop > T.y0 - 4);
     }
 }
 
@@ -822,7 +842,7 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
             }
             continue;
         }
-        median_blur_store(T, p, F, nullptr, false, M, R);
+        median_blur_store(T, p, F, nullptr, false, M, nullptr, R);
     }
 }
 
@@ -852,7 +872,7 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
     }
     if (total_tiles < 1) return cudaSuccess;
     if (ctas_per_sm < 1) ctas_per_sm = 1;
-    if (ctas_per_sm > 3) ctas_per_sm = 3;  // shared memory holds three per SM
+    if (ctas_per_sm > 5) ctas_per_sm = 5;  // shared memory and registers hold five per SM
     const int main_grid = total_tiles < ctas_per_sm * sm_count ? total_tiles : ctas_per_sm * sm_count;
     stage_b_main<<<main_grid, kThreadsB, main_smem, stream>>>(d_frames, n_frames, total_tiles, p, worklist);
     cudaError_t e = cudaGetLastError();

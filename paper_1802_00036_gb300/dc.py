@@ -207,7 +207,7 @@ def dc_metrics(ctx, pred_ptr: int, gt_ptr: int, n: int, H: int, W: int, stream: 
     return [tuple(out[5 * i:5 * i + 5]) for i in range(n)]
 
 
-def dc_set_tuning(ctx, a_warps_per_sm: int, b_ctas_per_sm: int, b_sparse_fill: int = 16) -> None:
+def dc_set_tuning(ctx, a_warps_per_sm: int, b_ctas_per_sm: int, b_sparse_fill: int = 160) -> None:
     t = dc_tuning(int(a_warps_per_sm), int(b_ctas_per_sm), int(b_sparse_fill))
     _check(load().dc_set_tuning(ctx, ctypes.byref(t)), "dc_set_tuning")
 

@@ -212,7 +212,7 @@ def test_results_do_not_depend_on_tuning(ctx):
     frames = synth.make_batch(6, synth.UNIFORM_375, config=4)
     x = torch.from_numpy(frames).cuda()
     ref = None
-    for a, b, f in ((12, 3, 16), (1, 1, 0), (3, 2, 160), (64, 1, 4)):
+    for a, b, f in ((12, 3, 16), (1, 1, 0), (3, 2, 160), (64, 1, 4), (8, 4, 160), (2, 5, 8), (8, 5, 160)):
         dc.dc_set_tuning(ctx.h, a, b, f)
         y = torch.full_like(x, -2.0)
         ctx.complete(x, y)
@@ -223,8 +223,8 @@ def test_results_do_not_depend_on_tuning(ctx):
         assert np.array_equal(got, ref), (a, b)
     y = torch.empty_like(x)
     a, b, f = dc.dc_autotune(ctx.h, x.data_ptr(), y.data_ptr(), 6, 375, 1242, dc.params())
-    assert 1 <= a <= 64 and 1 <= b <= 3 and 0 <= f <= 160 and dc.dc_get_tuning(ctx.h) == (a, b, f)
-    dc.dc_set_tuning(ctx.h, 6, 3, 16)
+    assert 1 <= a <= 64 and 1 <= b <= 5 and 0 <= f <= 160 and dc.dc_get_tuning(ctx.h) == (a, b, f)
+    dc.dc_set_tuning(ctx.h, 8, 5, 160)
     with pytest.raises(dc.DcError):
         dc.dc_set_tuning(ctx.h, 0, 3)
 
