@@ -482,6 +482,34 @@ __device__ __forceinline__ void put_key(unsigned* K, int k, int l, unsigned key)
     if (k >= kHalf) h[2 * ((k - kHalf) * kES + l) + 1] = static_cast<unsigned short>(key);
 }
 
+// Keys of the whole region from E (after step 6 on a tile whose scratch
+// took K): the same values the fix pass writes, pairs of rows (kp, kp + kHalf).
+__device__ void build_keys(const Tile& T, const float* __restrict__ E, unsigned* __restrict__ K, bool& ok)
+{
+    const int H = T.fd.H, W = T.fd.W;
+    for (int i = threadIdx.x; i < kPR * kChunksPerRow; i += kThreadsB) {
+        const int kp = i / kChunksPerRow, q = i - kp * kChunksPerRow;
+        const int xs = T.x0 - 4 + 4 * q;
+        unsigned key[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = kp + h * kHalf;
+            const int y = T.y0 - 4 + k;
+            if (y < 0 || y >= H || xs < 0 || xs >= W) continue;
+            const float4 c4 = *reinterpret_cast<const float4*>(E + k * kES + 4 * q);
+            const float v[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (xs + e >= W) break;
+                key[h][e] = key_of(v[e], ok);
+            }
+        }
+        *reinterpret_cast<uint4*>(K + kp * kES + 4 * q) =
+            make_uint4(key[0][0] | (key[1][0] << 16), key[0][1] | (key[1][1] << 16),
+                       key[0][2] | (key[1][2] << 16), key[0][3] | (key[1][3] << 16));
+    }
+}
+
 // A tile whose whole region lies above its columns' top rows (step 5 then
 // makes every row of the region the same: E(y, x) = C(top(x), x)) has
 // row-constant maps: the median of a window is the median of its five column
@@ -576,14 +604,26 @@ __device__ void constant_tile_store(const Tile& T, const StageBParams& p, const 
 
 // Shared memory of phase 1: the region E, the packed keys K, the median
 // output as 16-bit keys Mk (the float median output Mf lies over K and Mk,
-// which are idle on that path), column tops, the list of empty pixels.
-constexpr size_t kMainSmemFloats = kER * kES + kPR * kES + kMR * kMS / 2 + 2 * kEC + kMaxSparseFill + 4;
+// which are idle on that path), extra step-6 scratch X, column tops, the
+// empty pixels (list, and their columns as a bitmap, a list and an index).
+// Before the median, Mk and X are step-6 scratch (kSmallScratch floats); a
+// tile that needs more also takes K and rebuilds its keys afterwards
+// (kBigScratch floats).  The total leaves room for five CTAs per SM
+// (233,472 bytes; allocations in 128-byte units, 1 KB reserved per CTA).
+constexpr int kScratchExtra = 1824;
+constexpr int kSmallScratch = kMR * kMS / 2 + kScratchExtra;
+constexpr int kBigScratch = kPR * kES + kSmallScratch;
+constexpr size_t kMainSmemFloats =
+    kER * kES + kPR * kES + kMR * kMS / 2 + kScratchExtra + 2 * kEC + kMaxSparseFill + 4 + 4 + 2 * kEC;
+constexpr size_t kMainStaticSmem = 32;  // s_next, ebox
 static_assert(kPR * kES + kMR * kMS / 2 >= kMR * kMS, "the float median output fits over K and Mk");
 static_assert((kER * kES) % 4 == 0 && (kPR * kES) % 4 == 0 && kMS % 8 == 0, "16-byte aligned buffers and rows");
+static_assert(5 * ((kMainSmemFloats * 4 + kMainStaticSmem + 127) / 128 * 128 + 1024) <= 233472,
+              "five CTAs per SM");
 
 // Phase 1, persistent: CTA i starts with tile i and then takes the next
 // unclaimed tile from a counter.  One region buffer and 16-bit median output
-// (38 KB of shared memory in all) let five CTAs share an SM: while one waits
+// (45 KB of shared memory in all) let five CTAs share an SM: while one waits
 // for its region (cp.async) the others compute, which hides the copy better
 // than a second buffer would (that costs CTAs per SM).
 __global__ void __launch_bounds__(kThreadsB, 5)
@@ -595,12 +635,15 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
     unsigned* K = reinterpret_cast<unsigned*>(smem + kER * kES);             // packed keys
     unsigned short* Mk = reinterpret_cast<unsigned short*>(K + kPR * kES);   // median output, keys
     float* Mf = reinterpret_cast<float*>(K);                                 // median output, floats
-    float* scratch = reinterpret_cast<float*>(Mk);  // kMR * kMS / 2 floats, idle until the median
-    int* ctop = reinterpret_cast<int*>(Mk + kMR * kMS);
+    float* scratch = reinterpret_cast<float*>(Mk);  // kSmallScratch floats, idle until the median
+    int* ctop = reinterpret_cast<int*>(scratch + kSmallScratch);
     float* cval = reinterpret_cast<float*>(ctop + kEC);
     int* elist = reinterpret_cast<int*>(cval + kEC);
     int* ecount = elist + kMaxSparseFill;
-    __shared__ int ebox[4];  // region rows / columns spanned by the empty pixels: kmin, kmax, lmin, lmax
+    unsigned* ecols = reinterpret_cast<unsigned*>(ecount + 4);  // bitmap of region columns with empties
+    int* ecol_list = reinterpret_cast<int*>(ecols + 4);          // those columns, in order
+    int* ecol_idx = ecol_list + kEC;                             // region column -> position in the list
+    __shared__ int ebox[2];  // region rows spanned by the empty pixels: kmin, kmax
 
     const int tid = threadIdx.x;
     int t = blockIdx.x;
@@ -614,8 +657,9 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
         load_tops(T, p, T.x0 - 4, kEC, ctop, cval);
         if (tid == 0) {
             *ecount = 0;
-            ebox[0] = ebox[2] = 1 << 20;
-            ebox[1] = ebox[3] = -1;
+            ebox[0] = 1 << 20;
+            ebox[1] = -1;
+            ecols[0] = ecols[1] = ecols[2] = 0u;
             s_next = (int)gridDim.x + atomicAdd(worklist + 1, 1);
         }
         cp_async_wait_all();
@@ -662,8 +706,7 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
                         if (slot < kMaxSparseFill) elist[slot] = (k << 16) | (4 * q + e);
                         atomicMin(ebox + 0, k);
                         atomicMax(ebox + 1, k);
-                        atomicMin(ebox + 2, 4 * q + e);
-                        atomicMax(ebox + 3, 4 * q + e);
+                        atomicOr(ecols + ((4 * q + e) >> 5), 1u << ((4 * q + e) & 31));
                     }
                 }
             }
@@ -693,18 +736,39 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
                 // step 6 at the few empty pixels.  E and K are only written here (at
                 // empty pixels); the window maxima read C.
                 const int Rl = p.large_radius;
+                // their columns, in order (warps 0-2 take the bitmap's words)
+                const unsigned w0 = ecols[0], w1 = ecols[1], w2 = ecols[2];
+                if (tid < 96) {
+                    const int w = tid >> 5, lane = tid & 31;
+                    const unsigned bits = w == 0 ? w0 : (w == 1 ? w1 : w2);
+                    const int pos = (w > 0 ? __popc(w0) : 0) + (w > 1 ? __popc(w1) : 0) +
+                                    __popc(bits & ((1u << lane) - 1u));
+                    if ((bits >> lane) & 1u) {
+                        ecol_list[pos] = tid;
+                        ecol_idx[tid] = pos;
+                    }
+                }
+                const int ND = __popc(w0) + __popc(w1) + __popc(w2);
+                const int lmin = w0 ? __ffs(w0) - 1 : (w1 ? 31 + __ffs(w1) : 63 + __ffs(w2));
+                const int lmax = w2 ? 95 - __clz(w2) : (w1 ? 63 - __clz(w1) : 31 - __clz(w0));
                 // the union of their windows: frame rows [by0, by1], columns [bx0, bx1]
                 const int by0 = max(0, T.y0 - 4 + ebox[0] - Rl), by1 = min(H - 1, T.y0 - 4 + ebox[1] + Rl);
-                const int bx0 = max(0, T.x0 - 4 + ebox[2] - Rl), bx1 = min(W - 1, T.x0 - 4 + ebox[3] + Rl);
-                const int ex0 = T.x0 - 4 + ebox[2], ex1 = T.x0 - 4 + ebox[3];  // columns with empty pixels
-                const int BR = by1 - by0 + 1, BC = bx1 - bx0 + 1, EC = ex1 - ex0 + 1;
-                if (BR * BC + BR * EC <= kMR * kMS / 2) {
-                    // the union box in scratch: E with step 5 ...
-                    float* box = scratch;
-                    float* rmax = scratch + BR * BC;
-                    for (int i = tid; i < BR * BC; i += kThreadsB) {
-                        const int r = i / BC, c = i - r * BC;
-                        const int y = by0 + r, x = bx0 + c;
+                const int bx0 = max(0, T.x0 - 4 + lmin - Rl), bx1 = min(W - 1, T.x0 - 4 + lmax + Rl);
+                const int BR = by1 - by0 + 1, BC = bx1 - bx0 + 1;
+                // row maxima at the ND empty columns (BR x ND), each column's top
+                // and top value (2 x BC), then the box, which streams through the
+                // rest of the scratch in bands of rows
+                const int rm = BR * ND;
+                const bool small = rm + 3 * BC <= kSmallScratch;
+                const bool big = !small && rm + 3 * BC <= kBigScratch;
+                if (small || big) {
+                    float* rmax = small ? scratch : reinterpret_cast<float*>(K);
+                    int* btop = reinterpret_cast<int*>(rmax + rm);
+                    float* btv = reinterpret_cast<float*>(btop + BC);
+                    float* band = btv + BC;
+                    const int RB = min(BR, ((small ? kSmallScratch : kBigScratch) - rm - 2 * BC) / BC);
+                    for (int c = tid; c < BC; c += kThreadsB) {
+                        const int x = bx0 + c;
                         int top = kNoTop;
                         float tv = 0.0f;
                         if (p.extend_top) {
@@ -714,27 +778,44 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
                                 tv = __ldg(T.fd.c + (size_t)t2 * T.fd.c_pitch + x);
                             }
                         }
-                        box[i] = extended(T, p, y, x, top, tv);
+                        btop[c] = top;
+                        btv[c] = tv;
                     }
                     __syncthreads();
-                    // ... row maxima over the window width at the empty columns ...
-                    for (int i = tid; i < BR * EC; i += kThreadsB) {
-                        const int r = i / EC, c = ex0 + (i - r * EC);
-                        const int lo = max(c - Rl, bx0) - bx0, hi = min(c + Rl, bx1) - bx0;
-                        float m = ninf();
-                        for (int x = lo; x <= hi; ++x) m = fmaxf(m, box[r * BC + x]);
-                        rmax[i] = m;
+                    for (int r0 = 0; r0 < BR; r0 += RB) {
+                        const int nb = min(RB, BR - r0);
+                        // the band of E (step 5 applied) ...
+                        for (int i = tid; i < nb * BC; i += kThreadsB) {
+                            const int r = i / BC, c = i - r * BC;
+                            band[i] = extended(T, p, by0 + r0 + r, bx0 + c, btop[c], btv[c]);
+                        }
+                        __syncthreads();
+                        // ... its row maxima over the window width at the empty columns
+                        for (int i = tid; i < nb * ND; i += kThreadsB) {
+                            const int r = i / ND, j = i - r * ND;
+                            const int c = T.x0 - 4 + ecol_list[j];
+                            const int lo = max(c - Rl, bx0) - bx0, hi = min(c + Rl, bx1) - bx0;
+                            float m = ninf();
+                            for (int x = lo; x <= hi; ++x) m = fmaxf(m, band[r * BC + x]);
+                            rmax[(r0 + r) * ND + j] = m;
+                        }
+                        __syncthreads();
                     }
-                    __syncthreads();
-                    // ... and column maxima at each empty pixel
+                    // column maxima at each empty pixel
                     for (int j = tid; j < n_empty; j += kThreadsB) {
                         const int k = elist[j] >> 16, l = elist[j] & 0xFFFF;
-                        const int y = T.y0 - 4 + k, x = T.x0 - 4 + l;
+                        const int y = T.y0 - 4 + k;
                         const int lo = max(y - Rl, by0) - by0, hi = min(y + Rl, by1) - by0;
+                        const int jc = ecol_idx[l];
                         float m = ninf();
-                        for (int r = lo; r <= hi; ++r) m = fmaxf(m, rmax[r * EC + (x - ex0)]);
+                        for (int r = lo; r <= hi; ++r) m = fmaxf(m, rmax[r * ND + jc]);
                         E[k * kES + l] = m;
-                        put_key(K, k, l, key_of(m, keys_ok));
+                        if (small) put_key(K, k, l, key_of(m, keys_ok));
+                    }
+                    if (big) {  // K held the row maxima: the keys again, from E
+                        __syncthreads();
+                        keys_ok = true;
+                        build_keys(T, E, K, keys_ok);
                     }
                 } else {
                     // too wide for the box: one warp per pixel, windows read from C

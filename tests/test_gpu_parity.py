@@ -90,6 +90,50 @@ def test_large_fill_holes(ctx, hole, large):
                 oracle.complete(f, large_fill=large, stop_after=stop), stop, f"hole {hole} large {large}")
 
 
+def _step6_box(f, ty, tx, radius=15):
+    """For the stage-B tile at (ty, tx): its empty pixels after step 5 (from
+    the oracle) and the sizes of the step-6 scratch over them: the row
+    maxima (box rows x distinct empty columns) and the box width."""
+    E = oracle.complete(f, stop_after="extend")
+    H, W = E.shape
+    y0, x0 = ty - 4, tx - 4
+    ys, xs = np.nonzero(E[max(0, y0):min(H, y0 + 68), max(0, x0):min(W, x0 + 68)] < 0.1)
+    ys, xs = ys + max(0, y0), xs + max(0, x0)
+    rows = min(H - 1, ys.max() + radius) - max(0, ys.min() - radius) + 1
+    cols = min(W - 1, xs.max() + radius) - max(0, xs.min() - radius) + 1
+    return len(ys), rows * len(set(xs.tolist())), cols
+
+
+# Step-6 scratch of a stage-B CTA (floats): without and with the key buffer;
+# a tile uses it when rows x distinct columns + 3 x box width fits.
+SMALL_SCRATCH, BIG_SCRATCH = 3872, 6320
+
+
+@pytest.mark.parametrize("layout", ["banded", "keys_rebuilt", "per_pixel"])
+def test_step6_scattered_empties(ctx, layout):
+    # holes cut in a dense map keep a core of empty pixels after steps 1-5
+    # (a 13 x 13 hole about 3 x 3, an 11-row slot one row); placed in one
+    # tile's region they give a sparse set of empties that the tile fills
+    # itself: in bands through the small scratch (few distinct columns),
+    # through the scratch that takes the keys' buffer (many columns; keys
+    # rebuilt afterwards), or one warp per pixel when neither fits
+    rects = {
+        "banded": [(62, 75, 64, 77), (62, 75, 104, 117), (104, 117, 64, 77)],
+        "keys_rebuilt": [(60, 71, 58, 118), (110, 121, 58, 118)],
+        "per_pixel": [(52, 63, 50, 130), (116, 127, 50, 130)],
+    }[layout]
+    f = synth.random_sparse(180, 250, 1.0, 5, 2.0, 80.0)
+    for (y0, y1, x0, x1) in rects:
+        f[y0:y1, x0:x1] = 0.0
+    n, rm, bc = _step6_box(f, 60, 60)
+    assert 0 < n <= 160
+    want = ("banded" if rm + 3 * bc <= SMALL_SCRATCH else "keys_rebuilt" if rm + 3 * bc <= BIG_SCRATCH
+            else "per_pixel")
+    assert want == layout, (n, rm, bc)
+    for stop in ("fill_large", "median", "full"):
+        compare(gpu_run(ctx, f[None], stop_after=stop)[0], oracle.complete(f, stop_after=stop), stop, layout)
+
+
 @pytest.mark.parametrize("blur", ["gauss", "bilateral", "none"])
 @pytest.mark.parametrize("median", [True, False])
 def test_blur_variants(ctx, blur, median):
