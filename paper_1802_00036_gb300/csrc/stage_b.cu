@@ -450,7 +450,6 @@ constexpr int kMaxSparseFill = 160;
 // region's first column x0 - 4 is a multiple of 4 (tiles start at multiples
 // of 60) and rows of C are 128-byte aligned, so every chunk is aligned.
 constexpr int kChunksPerRow = kEC / 4;
-constexpr int kChunks = kER * kChunksPerRow;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 {
@@ -460,16 +459,28 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Region work is split by column chunk: thread t < kRowGroups x kChunksPerRow
+// takes chunk t % kChunksPerRow of every kRowGroups-th row from t /
+// kChunksPerRow, so its column bounds and column tops are computed once.
+constexpr int kRowGroups = kThreadsB / kChunksPerRow;
+
 // Start copying a tile's region of C into `dst` (kER x kES): the in-frame
 // chunks (a chunk straddling the right edge reads the row padding of C,
 // which is allocated).
 __device__ __forceinline__ void issue_region(const Tile& T, float* dst)
 {
-    for (int ch = threadIdx.x; ch < kChunks; ch += kThreadsB) {
-        const int k = ch / kChunksPerRow, q = ch - k * kChunksPerRow;
-        const int y = T.y0 - 4 + k, xs = T.x0 - 4 + 4 * q;
-        if (y >= 0 && y < T.fd.H && xs >= 0 && xs < T.fd.W)
-            cp_async16(dst + k * kES + 4 * q, T.fd.c + (size_t)y * T.fd.c_pitch + xs);
+    const int tid = threadIdx.x;
+    if (tid < kRowGroups * kChunksPerRow) {
+        const int g = tid / kChunksPerRow, q = tid - g * kChunksPerRow;
+        const int xs = T.x0 - 4 + 4 * q;
+        if (xs >= 0 && xs < T.fd.W) {
+            const int klo = max(0, 4 - T.y0), khi = min(kER, T.fd.H - T.y0 + 4);  // in-frame rows
+            int k = g;
+            while (k < klo) k += kRowGroups;
+            const float* src = T.fd.c + (size_t)(T.y0 - 4 + k) * T.fd.c_pitch + xs;
+            const size_t step = (size_t)kRowGroups * T.fd.c_pitch;
+            for (; k < khi; k += kRowGroups, src += step) cp_async16(dst + k * kES + 4 * q, src);
+        }
     }
     cp_async_commit();
 }
@@ -595,10 +606,15 @@ __device__ void constant_tile_store(const Tile& T, const StageBParams& p, const 
         Orow[b] = o;
     }
     __syncthreads();
-    for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
-        const int a = i / kTBW, b = i - a * kTBW;
-        const int y = T.y0 + a, x = T.x0 + b;
-        if (y < H && x < W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = Orow[b];
+    // every row the same: thread (half, column) writes half a column
+    static_assert(kThreadsB == 128 && kTBW <= 64 && kTBH % 2 == 0, "two threads per column");
+    const int b = tid & 63, a0 = (tid >> 6) * (kTBH / 2);
+    const int x = T.x0 + b;
+    if (b < kTBW && x < W) {
+        const float o = Orow[b];
+        float* dst = T.fd.out + (size_t)(T.y0 + a0) * T.fd.out_pitch + x;
+        const int rows = min(kTBH / 2, H - (T.y0 + a0));
+        for (int a = 0; a < rows; ++a, dst += T.fd.out_pitch) *dst = o;
     }
 }
 
@@ -676,43 +692,66 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
             constant_tile_store(T, p, cval, scratch);
         } else {
         // step 5 in place, empty pixels, packed keys: row pairs (kp, kp + kHalf)
+        // of one column chunk per thread
         bool keys_ok = true;
-        for (int i = tid; i < kPR * kChunksPerRow; i += kThreadsB) {
-            const int kp = i / kChunksPerRow, q = i - kp * kChunksPerRow;
+        if (tid < kRowGroups * kChunksPerRow) {
+            const int g = tid / kChunksPerRow, q = tid - g * kChunksPerRow;
             const int xs = T.x0 - 4 + 4 * q;
-            unsigned key[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
+            const int ncol = (xs >= 0 && xs < W) ? min(4, W - xs) : 0;  // in-frame columns of the chunk
+            int ct[4];
+            float cv[4];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = kp + h * kHalf;
-                const int y = T.y0 - 4 + k;
-                if (y < 0 || y >= H || xs < 0 || xs >= W) continue;
-                float4* cell = reinterpret_cast<float4*>(E + k * kES + 4 * q);
-                const float4 c4 = *cell;
-                float v[4] = {c4.x, c4.y, c4.z, c4.w};
-                if (ext_tile) {
+            for (int e = 0; e < 4; ++e) {
+                ct[e] = ext_tile ? ctop[4 * q + e] : kNoTop;
+                cv[e] = ext_tile ? cval[4 * q + e] : 0.0f;
+            }
+            for (int kp = g; kp < kPR; kp += kRowGroups) {
+                unsigned key[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = kp + h * kHalf;
+                    const int y = T.y0 - 4 + k;
+                    if (ncol == 0 || y < 0 || y >= H) continue;
+                    float4* cell = reinterpret_cast<float4*>(E + k * kES + 4 * q);
+                    const float4 c4 = *cell;
+                    float v[4] = {c4.x, c4.y, c4.z, c4.w};
+                    if (ext_tile) {
+                        bool moved = false;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (above_top(p, y, ct[e])) {
+                                v[e] = cv[e];
+                                moved = true;
+                            }
+                        if (moved) *cell = make_float4(v[0], v[1], v[2], v[3]);
+                    }
+                    unsigned em = 0u;  // empty in-frame columns of this chunk row
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
-                        if (above_top(p, y, ctop[4 * q + e])) v[e] = cval[4 * q + e];
-                    *cell = make_float4(v[0], v[1], v[2], v[3]);
-                }
-                // rows kHalf .. kPR - 1 appear in both halves: count them once
-                const bool counted = (h == 0) || (kp >= kPR - kHalf);
+                        if (e < ncol) {
+                            key[h][e] = key_of(v[e], keys_ok);
+                            em |= (is_empty(v[e]) ? 1u : 0u) << e;
+                        }
+                    // rows kHalf .. kPR - 1 appear in both halves: count them once
+                    const bool counted = (h == 0) || (kp >= kPR - kHalf);
+                    if (em && counted && p.large_fill_on) {
+                        const int slot0 = atomicAdd(ecount, __popc(em));
+                        int slot = slot0;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    if (xs + e >= W) break;
-                    key[h][e] = key_of(v[e], keys_ok);
-                    if (counted && p.large_fill_on && is_empty(v[e])) {
-                        const int slot = atomicAdd(ecount, 1);
-                        if (slot < kMaxSparseFill) elist[slot] = (k << 16) | (4 * q + e);
+                        for (int e = 0; e < 4; ++e)
+                            if ((em >> e) & 1u) {
+                                if (slot < kMaxSparseFill) elist[slot] = (k << 16) | (4 * q + e);
+                                ++slot;
+                            }
                         atomicMin(ebox + 0, k);
                         atomicMax(ebox + 1, k);
-                        atomicOr(ecols + ((4 * q + e) >> 5), 1u << ((4 * q + e) & 31));
+                        atomicOr(ecols + ((4 * q) >> 5), em << ((4 * q) & 31));
                     }
                 }
+                *reinterpret_cast<uint4*>(K + kp * kES + 4 * q) =
+                    make_uint4(key[0][0] | (key[1][0] << 16), key[0][1] | (key[1][1] << 16),
+                               key[0][2] | (key[1][2] << 16), key[0][3] | (key[1][3] << 16));
             }
-            *reinterpret_cast<uint4*>(K + kp * kES + 4 * q) =
-                make_uint4(key[0][0] | (key[1][0] << 16), key[0][1] | (key[1][1] << 16),
-                           key[0][2] | (key[1][2] << 16), key[0][3] | (key[1][3] << 16));
         }
         __syncthreads();
         const int n_empty = *ecount;
