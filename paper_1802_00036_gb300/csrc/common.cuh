@@ -24,7 +24,7 @@ constexpr int kNoTop = 0x7F7F7F7F;
 
 // Stage A: one warp streams one (strip, band) unit; 4 units per block.
 constexpr int kStageAColsPerLane = 4;
-constexpr int kThreadsA = 128;
+constexpr int kThreadsA = 32;  // one warp per CTA: the block scheduler spreads warps evenly
 // Stage B output tile (median blocks of 2 x 8 over the tile + 2 ring).
 constexpr int kTileBH = 60;
 constexpr int kTileBW = 60;
@@ -97,17 +97,21 @@ int stage_a_band_rows(int H, long long total_strips, long long target_warps);
 // Launch-shape choices (the results never depend on them).
 struct Tuning {
     int a_warps_per_sm;   // stage A: warps in flight per SM the bands aim for
-    int b_ctas_per_sm;    // stage B: persistent CTAs per SM (1..3)
+    int b_ctas_per_sm;    // stage B: persistent CTAs per SM (1..5)
     int b_sparse_fill;    // stage B: most empty pixels a tile fills itself (0..160)
 };
-constexpr Tuning kDefaultTuning{8, 5, 160};
+constexpr Tuning kDefaultTuning{12, 5, 160};
 
 // Launchers (stage_a.cu, stage_b.cu).  Return cudaGetLastError().
-// `worklist` holds 2 + (stage B tiles) ints: the number of stage-B tiles
-// that need the step-6 kernel and the counter from which persistent stage-B
-// CTAs take tiles (both zeroed by stage A), then those tiles.
-cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_tiles,
-                           int shape, int stop, int* worklist, int sm_count, cudaStream_t stream);
+// `work` holds 3 + (stage B tiles) ints: the number of stage-B tiles that
+// need the step-6 kernel and the counter from which persistent stage-B CTAs
+// take tiles (both zeroed by stage A), the counter from which stage-A warps
+// take units (zeroed before stage A starts), then those tiles.  band_stride:
+// the batch's strip count when all frames have one shape (units then go
+// band by band over the whole batch, bottom bands first), else 0.
+cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_units,
+                           int shape, int stop, int* work, int band_stride, int sm_count,
+                           cudaStream_t stream);
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,
                            const StageBParams& p, int* worklist, int sm_count, int ctas_per_sm,
                            cudaStream_t stream);

@@ -27,7 +27,7 @@ struct dc_ctx {
     size_t c_cap = 0;         // floats
     int* top = nullptr;       // per-column tops, all frames
     size_t top_cap = 0;       // ints
-    int* work = nullptr;      // stage-B worklist: count, then tile indices
+    int* work = nullptr;      // counters of both stages, then the step-6 tile list
     size_t work_cap = 0;      // ints
     double* acc = nullptr;    // accuracy sums and results, 10 doubles per frame
     int acc_cap = 0;          // frames
@@ -158,7 +158,8 @@ dc_status grow(dc_ctx* ctx, size_t c_floats, size_t top_ints, int frames, size_t
 int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 // The frame descriptors reach the device as kernel parameters, K at a time,
-// and a kernel stores them; the same launch resets the column tops.  A
+// and a kernel stores them; the same launch resets the column tops and
+// stage A's unit counter.  A
 // host-to-device copy would queue on the copy engine behind whatever large
 // transfers the caller has in flight (dc_complete_host's own copy-in of the
 // next chunk), holding back the kernels of this call.
@@ -170,41 +171,44 @@ static_assert(sizeof(TableChunk<384>) + 64 <= 32764, "kernel parameter space");
 
 template <int K>
 __global__ void table_put(const __grid_constant__ TableChunk<K> src, FrameDesc* __restrict__ dst, int n,
-                          int* __restrict__ top, size_t top_ints)
+                          int* __restrict__ top, size_t top_ints, int* __restrict__ counter)
 {
     const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
+    if (counter && tid == 0) *counter = 0;
     for (size_t i = tid; i < (size_t)n; i += stride) dst[i] = src.d[i];
     if (top)
         for (size_t i = tid; i < top_ints; i += stride) top[i] = kNoTop;
 }
 
 template <int K>
-cudaError_t table_put_chunk(const FrameDesc* desc, int n, FrameDesc* dst, int* top, size_t top_ints, int sms,
-                            cudaStream_t stream)
+cudaError_t table_put_chunk(const FrameDesc* desc, int n, FrameDesc* dst, int* top, size_t top_ints, int* counter,
+                            int sms, cudaStream_t stream)
 {
     TableChunk<K> c;
     std::memcpy(c.d, desc, (size_t)n * sizeof(FrameDesc));
     size_t blocks = (top_ints + 255) / 256;
     if (blocks < 1) blocks = 1;
     if (blocks > (size_t)2 * sms) blocks = (size_t)2 * sms;
-    table_put<K><<<(unsigned)blocks, 256, 0, stream>>>(c, dst, n, top, top_ints);
+    table_put<K><<<(unsigned)blocks, 256, 0, stream>>>(c, dst, n, top, top_ints, counter);
     return cudaGetLastError();
 }
 
-// Store n descriptors at dst (chunks of up to 384 per launch) and reset
-// top_ints column tops; returns the number of launches through *launches.
-cudaError_t put_table(const FrameDesc* desc, int n, FrameDesc* dst, int* top, size_t top_ints, int sms,
-                      cudaStream_t stream, int* launches)
+// Store n descriptors at dst (chunks of up to 384 per launch), reset
+// top_ints column tops and zero *counter; returns the number of launches
+// through *launches.
+cudaError_t put_table(const FrameDesc* desc, int n, FrameDesc* dst, int* top, size_t top_ints, int* counter,
+                      int sms, cudaStream_t stream, int* launches)
 {
     *launches = 0;
     for (int i = 0; i < n; i += 384) {
         const int m = n - i < 384 ? n - i : 384;
         int* t = i == 0 ? top : nullptr;
         const size_t ti = i == 0 ? top_ints : 0;
-        cudaError_t e = m <= 8    ? table_put_chunk<8>(desc + i, m, dst + i, t, ti, sms, stream)
-                      : m <= 64   ? table_put_chunk<64>(desc + i, m, dst + i, t, ti, sms, stream)
-                                  : table_put_chunk<384>(desc + i, m, dst + i, t, ti, sms, stream);
+        int* z = i == 0 ? counter : nullptr;
+        cudaError_t e = m <= 8    ? table_put_chunk<8>(desc + i, m, dst + i, t, ti, z, sms, stream)
+                      : m <= 64   ? table_put_chunk<64>(desc + i, m, dst + i, t, ti, z, sms, stream)
+                                  : table_put_chunk<384>(desc + i, m, dst + i, t, ti, z, sms, stream);
         if (e != cudaSuccess) return e;
         ++*launches;
     }
@@ -253,7 +257,7 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
 
     const bool need_b = (p->stop_after == DC_STOP_FULL || p->stop_after >= DC_STOP_EXTEND);
     dc_status s = grow(ctx, need_b ? c_off : 0, need_b ? top_off : 0, n, 0,
-                       need_b ? (size_t)tiles_b + 2 : 0);
+                       need_b ? (size_t)tiles_b + 3 : 3);
     if (s != DC_OK) return s;
     for (auto& d : desc) {
         d.c = need_b ? ctx->c + reinterpret_cast<size_t>(d.c) : nullptr;
@@ -266,8 +270,8 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         return DC_ERR_CUDA;
     // the descriptors and the reset of the tops, written by a kernel
     int table_launches = 0;
-    if (put_table(desc.data(), n, ctx->table, need_b ? ctx->top : nullptr, need_b ? top_off : 0, ctx->sm_count,
-                  stream, &table_launches) != cudaSuccess)
+    if (put_table(desc.data(), n, ctx->table, need_b ? ctx->top : nullptr, need_b ? top_off : 0, ctx->work + 2,
+                  ctx->sm_count, stream, &table_launches) != cudaSuccess)
         return DC_ERR_CUDA;
 
     cudaEvent_t* ev = nullptr;
@@ -279,8 +283,11 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         if (cudaEventRecord(ev[0], stream) != cudaSuccess) return DC_ERR_CUDA;
     }
     const int stop_a = need_b ? kStopFull : p->stop_after;
+    bool one_shape = true;
+    for (int i = 1; i < n && one_shape; ++i) one_shape = frames[i].H == frames[0].H && frames[i].W == frames[0].W;
+    const int band_stride = one_shape ? (int)total_strips : 0;
     cudaError_t e = launch_stage_a(ctx->table, n, (int)tiles_a, p->first_kernel, stop_a,
-                                   need_b ? ctx->work : nullptr, ctx->sm_count, stream);
+                                   ctx->work, band_stride, ctx->sm_count, stream);
     if (e != cudaSuccess) return DC_ERR_CUDA;
     ctx->last_launches = table_launches + 1;
     if (ev && cudaEventRecord(ev[1], stream) != cudaSuccess) return DC_ERR_CUDA;

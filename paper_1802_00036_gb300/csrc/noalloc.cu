@@ -56,15 +56,16 @@ dc_status setup(int dev, unsigned char** ptr, int* sms)
     return DC_OK;
 }
 
-// Writes the frame table for n packed frames and resets the tops: the only
-// preparation the two stage kernels need, done on the device so that the
-// call copies nothing from the host.
+// Writes the frame table for n packed frames, resets the tops and stage A's
+// unit counter: the only preparation the two stage kernels need, done on
+// the device so that the call copies nothing from the host.
 __global__ void noalloc_prepare(FrameDesc* table, int* top, float* cmap, const float* in, float* out,
                                 int n, int H, int W, int c_pitch, int tiles_x_a, int tiles_a, int band_a,
-                                int tiles_x_b, int tiles_b, int top_ints)
+                                int tiles_x_b, int tiles_b, int top_ints, int* counter)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
+    if (tid == 0) *counter = 0;  // stage A's unit counter
     for (int i = tid; i < n; i += stride) {
         FrameDesc d;
         d.in = in + (size_t)i * H * W;
@@ -137,7 +138,7 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     const int tiles_a = tiles_x_a * ((H + band_a - 1) / band_a);
     const int tiles_x_b = (W + kTileBW - 1) / kTileBW;
     const int tiles_b = tiles_x_b * ((H + kTileBH - 1) / kTileBH);
-    if ((long long)tiles_a * n > INT32_MAX / 2 || (long long)tiles_b * n + 2 > DC_NOALLOC_WORK_INTS)
+    if ((long long)tiles_a * n > INT32_MAX / 2 || (long long)tiles_b * n + 3 > DC_NOALLOC_WORK_INTS)
         return DC_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
 
@@ -147,11 +148,11 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     if (blocks > 1024) blocks = 1024;
     noalloc_prepare<<<blocks, threads, 0, st>>>(table, need_b ? top : nullptr, need_b ? cmap : nullptr,
                                                  in, out, n, H, W, (int)c_pitch, tiles_x_a, tiles_a, band_a,
-                                                 tiles_x_b, tiles_b, top_ints);
+                                                 tiles_x_b, tiles_b, top_ints, work + 2);
     if (cudaGetLastError() != cudaSuccess) return DC_ERR_CUDA;
 
     const int stop_a = need_b ? kStopFull : params->stop_after;
-    if (launch_stage_a(table, n, tiles_a * n, params->first_kernel, stop_a, need_b ? work : nullptr, sms, st) !=
+    if (launch_stage_a(table, n, tiles_a * n, params->first_kernel, stop_a, work, tiles_x_a * n, sms, st) !=
         cudaSuccess)
         return DC_ERR_CUDA;
     if (need_b) {

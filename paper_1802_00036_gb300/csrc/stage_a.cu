@@ -290,25 +290,33 @@ struct Fill7 {
     }
 };
 
+// One unit (a strip of kSW columns over one band of rows) of steps 1-4.
 template <int S>
-__global__ void __launch_bounds__(kThreadsA, 3)
-stage_a_stream(const FrameDesc* __restrict__ frames, int n_frames, int total_units, int stop,
-               int* __restrict__ worklist)
+__device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frames, int n_frames, int unit,
+                                             int stop, int band_stride)
 {
     constexpr int R1 = ShapeInfo<S>::r;
     constexpr int Rh = R1 + 7;        // halo, horizontal and vertical
     constexpr int OW = kSW - 2 * Rh;  // output columns per strip
     const int lane = threadIdx.x & 31;
-    const int unit = blockIdx.x * (kThreadsA / 32) + (threadIdx.x >> 5);
-    if (worklist && unit == 0 && lane < 2) worklist[lane] = 0;  // step-6 count, tile counter
-    if (unit >= total_units) return;  // whole warps only
-
-    const int f = find_frame<true>(frames, n_frames, unit);
+    // Bands from the bottom up (the rows with data, the costly ones, come
+    // first): with frames of one shape (band_stride = strips of the batch)
+    // the batch's bottom bands, then the next ones up; else frame by frame.
+    int f, band, strip;
+    if (band_stride > 0) {
+        const int r = unit / band_stride, g = unit - r * band_stride;
+        f = g / frames[0].tiles_x_a;
+        strip = g - f * frames[0].tiles_x_a;
+        band = (frames[0].H + frames[0].band_a - 1) / frames[0].band_a - 1 - r;
+    } else {
+        f = find_frame<true>(frames, n_frames, unit);
+        const int local = unit - frames[f].base_a;
+        band = (frames[f].H + frames[f].band_a - 1) / frames[f].band_a - 1 - local / frames[f].tiles_x_a;
+        strip = local % frames[f].tiles_x_a;
+    }
     const FrameDesc& fd = frames[f];
     const int H = fd.H, W = fd.W, in_pitch = fd.in_pitch;
     const float* __restrict__ src = fd.in;
-    const int local = unit - fd.base_a;
-    const int band = local / fd.tiles_x_a, strip = local - band * fd.tiles_x_a;
     const int r0 = band * fd.band_a, r1 = min(r0 + fd.band_a, H);
     const int sx = strip * OW - Rh;            // frame column of strip column 0
     const int cx = sx + lane * kV;             // frame column of this lane's first column
@@ -469,14 +477,36 @@ stage_a_stream(const FrameDesc* __restrict__ frames, int n_frames, int total_uni
     }
 }
 
+// Persistent: warp w of the grid starts with unit w and then takes the next
+// unclaimed unit from work[2] (zeroed before the launch), so SMs that drew
+// cheap units (mostly empty rows) take more.  Unit 0 also zeroes work[0]
+// and work[1] for stage B.
 template <int S>
-cudaError_t launch_shape(const FrameDesc* d_frames, int n_frames, int total_units, int stop, int* worklist,
-                         cudaStream_t stream)
+__global__ void __launch_bounds__(kThreadsA, 12)
+stage_a_stream(const FrameDesc* __restrict__ frames, int n_frames, int total_units, int stop,
+               int* __restrict__ work, int band_stride)
+{
+    const int lane = threadIdx.x & 31;
+    int unit = blockIdx.x * (kThreadsA / 32) + (threadIdx.x >> 5);
+    if (unit == 0 && lane < 2) work[lane] = 0;  // step-6 count, stage-B tile counter
+    const int warps = gridDim.x * (kThreadsA / 32);
+    while (unit < total_units) {  // whole warps only
+        stage_a_unit<S>(frames, n_frames, unit, stop, band_stride);
+        int next = 0;
+        if (lane == 0) next = atomicAdd(work + 2, 1);
+        unit = warps + __shfl_sync(0xffffffffu, next, 0);
+    }
+}
+
+template <int S>
+cudaError_t launch_shape(const FrameDesc* d_frames, int n_frames, int total_units, int stop, int* work,
+                         int band_stride, int sm_count, cudaStream_t stream)
 {
     const int per_block = kThreadsA / 32;
-    const int grid = (total_units + per_block - 1) / per_block;
+    int grid = (total_units + per_block - 1) / per_block;
+    if (grid > 12 * sm_count) grid = 12 * sm_count;  // twelve one-warp CTAs per SM (registers), persistent
     if (grid < 1) return cudaSuccess;
-    stage_a_stream<S><<<grid, kThreadsA, 0, stream>>>(d_frames, n_frames, total_units, stop, worklist);
+    stage_a_stream<S><<<grid, kThreadsA, 0, stream>>>(d_frames, n_frames, total_units, stop, work, band_stride);
     return cudaGetLastError();
 }
 
@@ -500,16 +530,15 @@ int stage_a_band_rows(int H, long long total_strips, long long target_warps)
 }
 
 cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_units, int shape, int stop,
-                           int* worklist, int sm_count, cudaStream_t stream)
+                           int* work, int band_stride, int sm_count, cudaStream_t stream)
 {
-    (void)sm_count;
     switch (shape) {
-    case kDiamond5: return launch_shape<kDiamond5>(d_frames, n_frames, total_units, stop, worklist, stream);
-    case kFull5: return launch_shape<kFull5>(d_frames, n_frames, total_units, stop, worklist, stream);
-    case kCross5: return launch_shape<kCross5>(d_frames, n_frames, total_units, stop, worklist, stream);
-    case kFull3: return launch_shape<kFull3>(d_frames, n_frames, total_units, stop, worklist, stream);
-    case kCircle5: return launch_shape<kCircle5>(d_frames, n_frames, total_units, stop, worklist, stream);
-    case kFull7: return launch_shape<kFull7>(d_frames, n_frames, total_units, stop, worklist, stream);
+    case kDiamond5: return launch_shape<kDiamond5>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream);
+    case kFull5: return launch_shape<kFull5>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream);
+    case kCross5: return launch_shape<kCross5>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream);
+    case kFull3: return launch_shape<kFull3>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream);
+    case kCircle5: return launch_shape<kCircle5>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream);
+    case kFull7: return launch_shape<kFull7>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream);
     default: return cudaErrorInvalidValue;
     }
 }

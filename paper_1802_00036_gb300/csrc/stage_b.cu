@@ -768,7 +768,7 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
         } else if (n_empty > p.sparse_fill_max) {
             if (tid == 0) {
                 const int slot = atomicAdd(worklist, 1);
-                worklist[2 + slot] = t;
+                worklist[3 + slot] = t;
             }
         } else {
             if (n_empty > 0) {
@@ -918,7 +918,7 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
     const int tid = threadIdx.x;
     for (int w = blockIdx.x; w < count; w += gridDim.x) {
         __syncthreads();
-        const Tile T = tile_of(frames, n_frames, worklist[2 + w]);
+        const Tile T = tile_of(frames, n_frames, worklist[3 + w]);
         const int H = T.fd.H, W = T.fd.W;
         const int gy = T.y0 - 4 - Rl, gx = T.x0 - 4 - Rl;  // frame position of G(0, 0)
         load_tops(T, p, gx, GC, ctop, cval);
