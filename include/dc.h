@@ -137,6 +137,20 @@ dc_status dc_complete_uniform(dc_ctx* ctx, const float* in, float* out, int n,
 dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, int n,
                            int H, int W, const dc_params* params, void* stream);
 
+/* dc_complete_host without the final wait, for a stream of batches: the
+ * call only enqueues its copies and kernels and returns, so that this
+ * call's copy in runs while the previous call's copy out does (the context
+ * stages through two buffer sets, used by turns).  host_in must stay
+ * unchanged and host_out untouched until dc_host_wait(ctx) returns; work
+ * enqueued later on `stream` is ordered after the kernels, not after the
+ * copy out.  Errors as dc_complete_host. */
+dc_status dc_complete_host_async(dc_ctx* ctx, const float* host_in, float* host_out, int n,
+                                 int H, int W, const dc_params* params, void* stream);
+
+/* Wait until every copy out of earlier dc_complete_host_async calls on this
+ * context has landed in host memory. */
+dc_status dc_host_wait(dc_ctx* ctx);
+
 /* Grow scratch now for batches of up to `n_frames` frames of up to H x W,
  * so that later calls of that size do not allocate. */
 dc_status dc_reserve(dc_ctx* ctx, int n_frames, int H, int W);

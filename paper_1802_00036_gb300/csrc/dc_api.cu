@@ -36,11 +36,18 @@ struct dc_ctx {
     cudaEvent_t done = nullptr;  // recorded after each call's last kernel
     unsigned long long calls = 0;
     // staging for host calls: copy streams and events of the chunk pipeline
-    float* io_in = nullptr;
-    float* io_out = nullptr;
+    // two staging sets, used by turns, so that one call's copy in can run
+    // while the previous call's copy out does; io_read[k] marks the end of
+    // the last kernel reading io_in[k], io_drained[k] the end of the last
+    // copy out of io_out[k]
+    float* io_in[2] = {};
+    float* io_out[2] = {};
     size_t io_cap = 0;        // floats each
     cudaStream_t s_in = nullptr, s_out = nullptr;
     cudaEvent_t io_ev[2 * kIoChunksMax] = {};
+    cudaEvent_t io_read[2] = {}, io_drained[2] = {};
+    bool io_used[2] = {};
+    int io_next = 0;
     // bookkeeping
     cudaStream_t last_stream = nullptr;
     cudaEvent_t last_done = nullptr;  // event of the latest call, or null
@@ -75,7 +82,7 @@ size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 size_t scratch_bytes(size_t c_floats, size_t top_ints, int frames, size_t io_floats, size_t work_ints)
 {
     return c_floats * sizeof(float) + top_ints * sizeof(int) + work_ints * sizeof(int) +
-           (size_t)frames * sizeof(FrameDesc) + 2 * io_floats * sizeof(float);
+           (size_t)frames * sizeof(FrameDesc) + 4 * io_floats * sizeof(float);
 }
 
 bool params_ok(const dc_params* p)
@@ -141,15 +148,18 @@ dc_status grow(dc_ctx* ctx, size_t c_floats, size_t top_ints, int frames, size_t
         ctx->frames_cap = nf;
     }
     if (ni > ctx->io_cap) {
-        cudaFree(ctx->io_in);
-        cudaFree(ctx->io_out);
-        ctx->io_in = ctx->io_out = nullptr;
-        ctx->io_cap = 0;
-        if (cudaMalloc(&ctx->io_in, ni * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&ctx->io_out, ni * sizeof(float)) != cudaSuccess) {
-            cudaGetLastError();
-            return DC_ERR_OOM;
+        for (int k = 0; k < 2; ++k) {
+            cudaFree(ctx->io_in[k]);
+            cudaFree(ctx->io_out[k]);
+            ctx->io_in[k] = ctx->io_out[k] = nullptr;
         }
+        ctx->io_cap = 0;
+        for (int k = 0; k < 2; ++k)
+            if (cudaMalloc(&ctx->io_in[k], ni * sizeof(float)) != cudaSuccess ||
+                cudaMalloc(&ctx->io_out[k], ni * sizeof(float)) != cudaSuccess) {
+                cudaGetLastError();
+                return DC_ERR_OOM;
+            }
         ctx->io_cap = ni;
     }
     return DC_OK;
@@ -438,49 +448,101 @@ dc_status dc_complete_uniform(dc_ctx* ctx, const float* in, float* out, int n, i
     return note(ctx, run(ctx, fr.data(), n, params, (cudaStream_t)stream));
 }
 
-dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, int n, int H, int W,
-                           const dc_params* params, void* stream)
+namespace {
+
+// Enqueue a host-buffer call: copy in, kernels and copy out of up to four
+// chunks, through staging set ctx->io_next.  Nothing waits on the host.
+dc_status host_enqueue(dc_ctx* ctx, const float* host_in, float* host_out, int n, int H, int W,
+                       const dc_params* params, cudaStream_t st)
 {
-    if (!ctx || n < 0 || (n > 0 && (!host_in || !host_out || H < 1 || W < 1)) || !params_ok(params))
-        return DC_ERR_INVALID_ARG;
-    if (n == 0) return DC_OK;
-    DeviceGuard g(ctx->device);
     const size_t frame = (size_t)H * W;
-    const size_t floats = (size_t)n * frame;
-    dc_status s = grow(ctx, 0, 0, 0, floats);
+    dc_status s = grow(ctx, 0, 0, 0, (size_t)n * frame);
     if (s != DC_OK) return note(ctx, s);
     if (!ctx->s_in) {
         bool ok = cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking) == cudaSuccess;
         for (int i = 0; ok && i < 2 * kIoChunksMax; ++i)
             ok = cudaEventCreateWithFlags(&ctx->io_ev[i], cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; ok && k < 2; ++k)
+            ok = cudaEventCreateWithFlags(&ctx->io_read[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ctx->io_drained[k], cudaEventDisableTiming) == cudaSuccess;
         if (!ok) return note(ctx, DC_ERR_CUDA);
     }
-    cudaStream_t st = (cudaStream_t)stream;
+    const int set = ctx->io_next;
+    float* io_in = ctx->io_in[set];
+    float* io_out = ctx->io_out[set];
     // up to 4 chunks of at least 8 frames: enough overlap of the copies with
     // the kernels while each chunk still fills the GPU
     int per = (n + 3) / 4;
     if (per < 8) per = 8;
     if (per > n) per = n;
-    // the copy-in stream starts after earlier work on `stream` (io_in reuse)
-    if (cudaEventRecord(ctx->io_ev[0], st) != cudaSuccess || cudaStreamWaitEvent(ctx->s_in, ctx->io_ev[0], 0) != cudaSuccess)
+    // the copy in follows earlier work on `stream` (which may have produced
+    // host_in) and the last kernel that read this staging set; the kernels
+    // follow the last copy out of this set's output staging
+    cudaEvent_t start = ctx->io_ev[0];
+    if (cudaEventRecord(start, st) != cudaSuccess || cudaStreamWaitEvent(ctx->s_in, start, 0) != cudaSuccess ||
+        (ctx->io_used[set] && (cudaStreamWaitEvent(ctx->s_in, ctx->io_read[set], 0) != cudaSuccess ||
+                               cudaStreamWaitEvent(st, ctx->io_drained[set], 0) != cudaSuccess)))
         return note(ctx, DC_ERR_CUDA);
     int k = 0;
     for (int f0 = 0; f0 < n; f0 += per, ++k) {
         const int m = (n - f0 < per) ? n - f0 : per;
         const size_t off = (size_t)f0 * frame, bytes = (size_t)m * frame * sizeof(float);
         cudaEvent_t in_done = ctx->io_ev[2 * k], run_done = ctx->io_ev[2 * k + 1];
-        if (cudaMemcpyAsync(ctx->io_in + off, host_in + off, bytes, cudaMemcpyHostToDevice, ctx->s_in) != cudaSuccess ||
+        if (cudaMemcpyAsync(io_in + off, host_in + off, bytes, cudaMemcpyHostToDevice, ctx->s_in) != cudaSuccess ||
             cudaEventRecord(in_done, ctx->s_in) != cudaSuccess || cudaStreamWaitEvent(st, in_done, 0) != cudaSuccess)
             return note(ctx, DC_ERR_CUDA);
-        s = dc_complete_uniform(ctx, ctx->io_in + off, ctx->io_out + off, m, H, W, params, stream);
+        s = dc_complete_uniform(ctx, io_in + off, io_out + off, m, H, W, params, st);
         if (s != DC_OK) return s;
         if (cudaEventRecord(run_done, st) != cudaSuccess || cudaStreamWaitEvent(ctx->s_out, run_done, 0) != cudaSuccess ||
-            cudaMemcpyAsync(host_out + off, ctx->io_out + off, bytes, cudaMemcpyDeviceToHost, ctx->s_out) != cudaSuccess)
+            cudaMemcpyAsync(host_out + off, io_out + off, bytes, cudaMemcpyDeviceToHost, ctx->s_out) != cudaSuccess)
             return note(ctx, DC_ERR_CUDA);
     }
+    if (cudaEventRecord(ctx->io_read[set], st) != cudaSuccess ||
+        cudaEventRecord(ctx->io_drained[set], ctx->s_out) != cudaSuccess)
+        return note(ctx, DC_ERR_CUDA);
+    ctx->io_used[set] = true;
+    ctx->io_next = set ^ 1;
+    return DC_OK;
+}
+
+bool host_args_ok(const dc_ctx* ctx, const float* host_in, const float* host_out, int n, int H, int W,
+                  const dc_params* params)
+{
+    return ctx && n >= 0 && (n == 0 || (host_in && host_out && H >= 1 && W >= 1)) && params_ok(params);
+}
+
+}  // namespace
+
+dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, int n, int H, int W,
+                           const dc_params* params, void* stream)
+{
+    if (!host_args_ok(ctx, host_in, host_out, n, H, W, params)) return DC_ERR_INVALID_ARG;
+    if (n == 0) return DC_OK;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    dc_status s = host_enqueue(ctx, host_in, host_out, n, H, W, params, st);
+    if (s != DC_OK) return s;
     if (cudaStreamSynchronize(ctx->s_out) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
         return note(ctx, DC_ERR_CUDA);
+    return DC_OK;
+}
+
+dc_status dc_complete_host_async(dc_ctx* ctx, const float* host_in, float* host_out, int n, int H, int W,
+                                 const dc_params* params, void* stream)
+{
+    if (!host_args_ok(ctx, host_in, host_out, n, H, W, params)) return DC_ERR_INVALID_ARG;
+    if (n == 0) return DC_OK;
+    DeviceGuard g(ctx->device);
+    return host_enqueue(ctx, host_in, host_out, n, H, W, params, (cudaStream_t)stream);
+}
+
+dc_status dc_host_wait(dc_ctx* ctx)
+{
+    if (!ctx) return DC_ERR_INVALID_ARG;
+    if (!ctx->s_out) return DC_OK;
+    DeviceGuard g(ctx->device);
+    if (cudaStreamSynchronize(ctx->s_out) != cudaSuccess) return note(ctx, DC_ERR_CUDA);
     return DC_OK;
 }
 
@@ -687,8 +749,12 @@ void dc_destroy(dc_ctx* ctx)
         cudaFree(ctx->acc);
         cudaFree(ctx->table);
         if (ctx->done) cudaEventDestroy(ctx->done);
-        cudaFree(ctx->io_in);
-        cudaFree(ctx->io_out);
+        for (int k = 0; k < 2; ++k) {
+            cudaFree(ctx->io_in[k]);
+            cudaFree(ctx->io_out[k]);
+            if (ctx->io_read[k]) cudaEventDestroy(ctx->io_read[k]);
+            if (ctx->io_drained[k]) cudaEventDestroy(ctx->io_drained[k]);
+        }
         for (cudaEvent_t e : ctx->io_ev)
             if (e) cudaEventDestroy(e);
         if (ctx->s_in) cudaStreamDestroy(ctx->s_in);

@@ -76,6 +76,10 @@ SIGNATURES = [
     ("dc_complete_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(dc_params), ctypes.c_void_p]),
+    ("dc_complete_host_async", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(dc_params), ctypes.c_void_p]),
+    ("dc_host_wait", ctypes.c_int, [ctypes.c_void_p]),
     ("dc_reserve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     ("dc_last_launch_count", ctypes.c_int, [ctypes.c_void_p]),
     ("dc_project", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
@@ -174,6 +178,16 @@ def dc_complete_host(ctx, host_in: int, host_out: int, n: int, H: int, W: int, p
                      stream: int = 0) -> None:
     _check(load().dc_complete_host(ctx, ctypes.c_void_p(host_in), ctypes.c_void_p(host_out), n, H, W,
                                    ctypes.byref(p), ctypes.c_void_p(stream)), "dc_complete_host")
+
+
+def dc_complete_host_async(ctx, host_in: int, host_out: int, n: int, H: int, W: int, p: dc_params,
+                           stream: int = 0) -> None:
+    _check(load().dc_complete_host_async(ctx, ctypes.c_void_p(host_in), ctypes.c_void_p(host_out), n, H, W,
+                                         ctypes.byref(p), ctypes.c_void_p(stream)), "dc_complete_host_async")
+
+
+def dc_host_wait(ctx) -> None:
+    _check(load().dc_host_wait(ctx), "dc_host_wait")
 
 
 def dc_complete_noalloc(in_ptr: int, out_ptr: int, n: int, H: int, W: int, p: dc_params,

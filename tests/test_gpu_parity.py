@@ -251,6 +251,26 @@ def test_host_buffers_pipelined_chunks(ctx):
     assert np.array_equal(hout.numpy().view(np.uint32), dev.view(np.uint32))
 
 
+def test_host_buffers_async_stream_of_batches(ctx):
+    # five calls in flight before one wait: the two staging sets are each
+    # reused while earlier calls' copies may still run; every batch must
+    # come back as the device path computes it (one of them of another size)
+    from paper_1802_00036_gb300 import dc
+    sizes = (12, 12, 5, 12, 12)
+    batches = [synth.make_batch(n, synth.ONE_FRAME, config=8, first=10 * i) for i, n in enumerate(sizes)]
+    hins = [torch.from_numpy(b).pin_memory() for b in batches]
+    houts = [torch.full_like(h, -1.0).pin_memory() for h in hins]
+    stream = torch.cuda.Stream()
+    for h_in, h_out, n in zip(hins, houts, sizes):
+        dc.dc_complete_host_async(ctx.h, h_in.data_ptr(), h_out.data_ptr(), n, 352, 1216, dc.params(),
+                                  stream.cuda_stream)
+    dc.dc_host_wait(ctx.h)
+    for b, h_out in zip(batches, houts):
+        assert np.array_equal(h_out.numpy().view(np.uint32), gpu_run(ctx, b).view(np.uint32))
+    with pytest.raises(dc.DcError):
+        dc.dc_complete_host_async(ctx.h, 0, 0, 1, 352, 1216, dc.params())
+
+
 def test_results_do_not_depend_on_tuning(ctx):
     from paper_1802_00036_gb300 import dc
     frames = synth.make_batch(6, synth.UNIFORM_375, config=4)
