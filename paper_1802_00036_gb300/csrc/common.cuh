@@ -64,6 +64,7 @@ struct StageBParams {
     int extend_rows;    // < 0: unlimited
     int stop;
     int sparse_fill_max;  // a tile with more empty pixels goes to the step-6 worklist
+    int row_stride;       // frames of one shape: the batch's tiles per tile row (tile order), else 0
     float ws[5];        // bilateral spatial weight for dy^2+dx^2 = 0,1,2,(3),4
     float inv_2sc2;     // 1 / (2 sigma_color^2)
 };

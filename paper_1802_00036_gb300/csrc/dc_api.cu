@@ -311,6 +311,7 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         bp.extend_rows = p->extend_rows;
         bp.stop = p->stop_after;
         bp.sparse_fill_max = ctx->tune.b_sparse_fill;
+        bp.row_stride = one_shape ? (int)(((frames[0].W + kTileBW - 1) / kTileBW) * (long long)n) : 0;
         const double ss = p->blur == DC_BLUR_BILATERAL ? p->sigma_space : 1.0;
         const double sc = p->blur == DC_BLUR_BILATERAL ? p->sigma_color : 1.0;
         for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));

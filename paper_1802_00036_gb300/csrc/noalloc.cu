@@ -165,6 +165,7 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
         bp.extend_rows = params->extend_rows;
         bp.stop = params->stop_after;
         bp.sparse_fill_max = kDefaultTuning.b_sparse_fill;
+        bp.row_stride = tiles_x_b * n;
         const double ss = params->blur == DC_BLUR_BILATERAL ? params->sigma_space : 1.0;
         const double sc = params->blur == DC_BLUR_BILATERAL ? params->sigma_color : 1.0;
         for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));

@@ -147,9 +147,22 @@ __device__ __forceinline__ Ring ring_of(const Tile& T, int w, int rows, int cols
     return r;
 }
 
-__device__ __forceinline__ Tile tile_of(const FrameDesc* __restrict__ frames, int n_frames, int t)
+// Tile t of the batch.  With frames of one shape (row_stride = the batch's
+// tiles per tile row) tiles go by tile rows over the whole batch from the
+// bottom up: the costly rows (data, empty pixels) are handed out first and
+// the cheap ones above every column's top (one computed row) last, so the
+// kernel's tail is short.  Otherwise frame by frame, row-major.
+__device__ __forceinline__ Tile tile_of(const FrameDesc* __restrict__ frames, int n_frames, int t, int row_stride)
 {
     Tile T;
+    if (row_stride > 0) {
+        const int r = t / row_stride, g = t - r * row_stride;
+        const int f = g / frames[0].tiles_x_b;
+        T.fd = frames[f];
+        T.y0 = ((T.fd.H + kTBH - 1) / kTBH - 1 - r) * kTBH;
+        T.x0 = (g - f * T.fd.tiles_x_b) * kTBW;
+        return T;
+    }
     const int f = find_frame<false>(frames, n_frames, t);
     T.fd = frames[f];
     const int local = t - T.fd.base_b;
@@ -664,7 +677,7 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
     const int tid = threadIdx.x;
     int t = blockIdx.x;
     if (t >= total_tiles) return;
-    Tile T = tile_of(frames, n_frames, t);
+    Tile T = tile_of(frames, n_frames, t, p.row_stride);
     __shared__ int s_next;
     for (int it = 0;; ++it) {
         float* E = Ebuf;
@@ -893,7 +906,7 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
 
         __syncthreads();
         if (!more) break;
-        T = tile_of(frames, n_frames, tn);
+        T = tile_of(frames, n_frames, tn, p.row_stride);
         t = tn;
     }
 }
@@ -918,7 +931,7 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
     const int tid = threadIdx.x;
     for (int w = blockIdx.x; w < count; w += gridDim.x) {
         __syncthreads();
-        const Tile T = tile_of(frames, n_frames, worklist[3 + w]);
+        const Tile T = tile_of(frames, n_frames, worklist[3 + w], p.row_stride);
         const int H = T.fd.H, W = T.fd.W;
         const int gy = T.y0 - 4 - Rl, gx = T.x0 - 4 - Rl;  // frame position of G(0, 0)
         load_tops(T, p, gx, GC, ctop, cval);
