@@ -184,7 +184,7 @@ dc_status dc_metrics(dc_ctx* ctx, const float* pred, const float* gt, int n, int
  * arithmetic is the same under any tuning).  a_warps_per_sm: stage A (steps
  * 1-4) splits frames into row bands so that about this many warps per SM
  * run (more bands = more parallelism but more halo rows recomputed; 1..64,
- * default 12).  b_ctas_per_sm: persistent CTAs per SM of stage B (steps 5-8;
+ * default 8).  b_ctas_per_sm: persistent CTAs per SM of stage B (steps 5-8;
  * 1..5, default 5).  b_sparse_fill: a stage-B tile with at most this many
  * empty pixels near it fills them itself (step 6); a
  * tile with more goes to a second kernel that works on the whole window

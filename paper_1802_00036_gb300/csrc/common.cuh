@@ -101,7 +101,7 @@ struct Tuning {
     int b_ctas_per_sm;    // stage B: persistent CTAs per SM (1..5)
     int b_sparse_fill;    // stage B: most empty pixels a tile fills itself (0..160)
 };
-constexpr Tuning kDefaultTuning{12, 5, 160};
+constexpr Tuning kDefaultTuning{8, 5, 160};
 
 // Launchers (stage_a.cu, stage_b.cu).  Return cudaGetLastError().
 // `work` holds 3 + (stage B tiles) ints: the number of stage-B tiles that

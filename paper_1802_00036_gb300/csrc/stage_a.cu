@@ -393,34 +393,42 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
             const float d = raw[PHI][v];
-            const float inv = (d >= kEmptyBelow) ? __fsub_rn(kInvertFrom, d) : 0.0f;
-            x.v[v] = (row_in && (!edge || col_in[v])) ? inv : ninf();
+            x.v[v] = (d >= kEmptyBelow) ? __fsub_rn(kInvertFrom, d) : 0.0f;
         }
+        // out-of-frame pixels take the neutral value; the tests are
+        // warp-uniform and false for inner strips away from the frame's ends
+        if (!row_in || edge)
+#pragma unroll
+            for (int v = 0; v < kV; ++v)
+                if (!row_in || !col_in[v]) x.v[v] = ninf();
         load_row(t + 4, raw[PHI]);
         // step 2: row t -> A(t - R1)
         Row a;
         s2.template push<PHI>(x, a.v);
         const int ra = t - R1;
         const bool a_in = ra >= 0 && ra < H;
+        if (!a_in || edge)
 #pragma unroll
-        for (int v = 0; v < kV; ++v)
-            if (!a_in || (edge && !col_in[v])) a.v[v] = ninf();
+            for (int v = 0; v < kV; ++v)
+                if (!a_in || !col_in[v]) a.v[v] = ninf();
         // step 3, dilation: A(ra) -> D(ra - 2)
         Row dd;
         s3d.template push<PHI>(a, dd.v);
         const int rd = ra - 2;
         const bool d_in = rd >= 0 && rd < H;
+        if (!d_in || edge)
 #pragma unroll
-        for (int v = 0; v < kV; ++v)
-            if (!d_in || (edge && !col_in[v])) dd.v[v] = pinf();
+            for (int v = 0; v < kV; ++v)
+                if (!d_in || !col_in[v]) dd.v[v] = pinf();
         // step 3, erosion: D(rd) -> B(rd - 2)
         Row b;
         s3e.template push<PHI>(dd, b.v);
         const int rb = rd - 2;
         const bool b_in = rb >= 0 && rb < H;
+        if (!b_in || edge)
 #pragma unroll
-        for (int v = 0; v < kV; ++v)
-            if (!b_in || (edge && !col_in[v])) b.v[v] = ninf();
+            for (int v = 0; v < kV; ++v)
+                if (!b_in || !col_in[v]) b.v[v] = ninf();
         // step 4: B(rb) -> C(rb - 3)
         float c[kV];
         s4.template push<PHI>(b, c);
