@@ -85,6 +85,9 @@ __device__ __forceinline__ unsigned key_of(float v, bool& ok)
     return kb & 0xFFFFu;
 }
 
+// A key k is empty (k / 256 < 0.1) exactly when k <= 25.
+constexpr unsigned kEmptyKeyMax = 25;
+
 // The float value of a 16-bit key: exactly k / 256.
 __device__ __forceinline__ float value_of(unsigned k)
 {
@@ -289,7 +292,69 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
         }
         __syncthreads();
     }
-    // column pass / bilateral, masked by the median, inverted, stored: each
+    if (p.blur == kBlurGauss) {
+        // column pass, masked by the median, inverted, stored: each thread
+        // takes kGRows rows of two adjacent columns
+        constexpr int kPairs = kTBW / 2, kGRows = kTBH / 4;
+        static_assert(kTBW % 2 == 0 && kTBH % 4 == 0 && kThreadsB >= 4 * kPairs && kRS % 2 == 0 && kMS % 2 == 0,
+                      "column-pass mapping");
+        if (tid < 4 * kPairs) {
+            const int cp = tid % kPairs, a0 = (tid / kPairs) * kGRows;
+            const int b = 2 * cp, x = T.x0 + b;
+            const int rows = min(kGRows, H - (T.y0 + a0));
+            if (x < W && rows > 0) {
+                float2 r[kGRows + 4];
+#pragma unroll
+                for (int k = 0; k < kGRows + 4; ++k) r[k] = *reinterpret_cast<const float2*>(R + (a0 + k) * kRS + b);
+                const bool two = x + 1 < W;
+                // both outputs in one 8-byte store when every row keeps them aligned
+                const bool vec = two && (T.fd.out_pitch % 2) == 0 &&
+                                 (reinterpret_cast<uintptr_t>(T.fd.out + x) % sizeof(float2)) == 0;
+                float* dst = T.fd.out + (size_t)(T.y0 + a0) * T.fd.out_pitch + x;
+#pragma unroll
+                for (int k = 0; k < kGRows; ++k) {
+                    if (k >= rows) break;
+                    const int mi = (a0 + k + 2) * kMS + b + 2;
+                    bool e0, e1;
+                    if constexpr (KEYS) {
+                        const unsigned w = *reinterpret_cast<const unsigned*>(Mk + mi);
+                        e0 = (w & 0xFFFFu) <= kEmptyKeyMax;
+                        e1 = (w >> 16) <= kEmptyKeyMax;
+                    } else {
+                        const float2 m2 = *reinterpret_cast<const float2*>(Mf + mi);
+                        e0 = is_empty(m2.x);
+                        e1 = is_empty(m2.y);
+                    }
+                    float acc0 = w0 * r[k].x, acc1 = w0 * r[k].y;
+                    acc0 = fmaf(w1, r[k + 1].x, acc0);
+                    acc1 = fmaf(w1, r[k + 1].y, acc1);
+                    acc0 = fmaf(w2, r[k + 2].x, acc0);
+                    acc1 = fmaf(w2, r[k + 2].y, acc1);
+                    acc0 = fmaf(w1, r[k + 3].x, acc0);
+                    acc1 = fmaf(w1, r[k + 3].y, acc1);
+                    acc0 = fmaf(w0, r[k + 4].x, acc0);
+                    acc1 = fmaf(w0, r[k + 4].y, acc1);
+                    float o0, o1;
+                    if (p.stop == kStopBlur) {  // the blurred map itself (inverted domain)
+                        o0 = e0 ? m_at<KEYS>(Mf, Mk, mi) : acc0;
+                        o1 = e1 ? m_at<KEYS>(Mf, Mk, mi + 1) : acc1;
+                    } else {
+                        o0 = e0 ? 0.0f : __fsub_rn(kInvertFrom, acc0);
+                        o1 = e1 ? 0.0f : __fsub_rn(kInvertFrom, acc1);
+                    }
+                    if (vec) {
+                        *reinterpret_cast<float2*>(dst) = make_float2(o0, o1);
+                    } else {
+                        dst[0] = o0;
+                        if (two) dst[1] = o1;
+                    }
+                    dst += T.fd.out_pitch;
+                }
+            }
+        }
+        return;
+    }
+    // bilateral or no blur, masked by the median, inverted, stored: each
     // thread takes kStripRows rows of one column
     constexpr int kStrips = kThreadsB / 64;
     constexpr int kStripRows = kTBH / kStrips;
@@ -297,49 +362,29 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
     const int b = tid & 63, a0 = (tid >> 6) * kStripRows;
     const int x = T.x0 + b;
     if (b < kTBW && x < W) {
-        if (p.blur == kBlurGauss) {
-            float r[kStripRows + 4];
+        for (int k = 0; k < kStripRows; ++k) {
+            const int a = a0 + k, y = T.y0 + a;
+            if (y >= H) break;
+            const float m = m_at<KEYS>(Mf, Mk, (a + 2) * kMS + b + 2);
+            float g = m;
+            if (!is_empty(m) && p.blur == kBlurBilateral) {
+                float num = 0.0f, den = 0.0f;
 #pragma unroll
-            for (int k = 0; k < kStripRows + 4; ++k) r[k] = R[(a0 + k) * kRS + b];
+                for (int dy = -2; dy <= 2; ++dy)
 #pragma unroll
-            for (int k = 0; k < kStripRows; ++k) {
-                const int y = T.y0 + a0 + k;
-                if (y >= H) break;
-                const float m = m_at<KEYS>(Mf, Mk, (a0 + k + 2) * kMS + b + 2);
-                float acc = w0 * r[k];
-                acc = fmaf(w1, r[k + 1], acc);
-                acc = fmaf(w2, r[k + 2], acc);
-                acc = fmaf(w1, r[k + 3], acc);
-                acc = fmaf(w0, r[k + 4], acc);
-                const float g = is_empty(m) ? m : acc;
-                const float o = (p.stop == kStopBlur) ? g : (is_empty(m) ? 0.0f : __fsub_rn(kInvertFrom, g));
-                T.fd.out[(size_t)y * T.fd.out_pitch + x] = o;
+                    for (int dx = -2; dx <= 2; ++dx) {
+                        const int r2 = dy * dy + dx * dx;
+                        if (r2 > 4) continue;
+                        const float v = m_at<KEYS>(Mf, Mk, (a + 2 + dy) * kMS + b + 2 + dx);
+                        const float d = v - m;
+                        const float wgt = p.ws[r2] * expf(-(d * d) * p.inv_2sc2);
+                        num = fmaf(v, wgt, num);
+                        den += wgt;
+                    }
+                g = num / den;
             }
-        } else {
-            for (int k = 0; k < kStripRows; ++k) {
-                const int a = a0 + k, y = T.y0 + a;
-                if (y >= H) break;
-                const float m = m_at<KEYS>(Mf, Mk, (a + 2) * kMS + b + 2);
-                float g = m;
-                if (!is_empty(m) && p.blur == kBlurBilateral) {
-                    float num = 0.0f, den = 0.0f;
-#pragma unroll
-                    for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-                        for (int dx = -2; dx <= 2; ++dx) {
-                            const int r2 = dy * dy + dx * dx;
-                            if (r2 > 4) continue;
-                            const float v = m_at<KEYS>(Mf, Mk, (a + 2 + dy) * kMS + b + 2 + dx);
-                            const float d = v - m;
-                            const float wgt = p.ws[r2] * expf(-(d * d) * p.inv_2sc2);
-                            num = fmaf(v, wgt, num);
-                            den += wgt;
-                        }
-                    g = num / den;
-                }
-                const float o = (p.stop == kStopBlur) ? g : (is_empty(m) ? 0.0f : __fsub_rn(kInvertFrom, g));
-                T.fd.out[(size_t)y * T.fd.out_pitch + x] = o;
-            }
+            const float o = (p.stop == kStopBlur) ? g : (is_empty(m) ? 0.0f : __fsub_rn(kInvertFrom, g));
+            T.fd.out[(size_t)y * T.fd.out_pitch + x] = o;
         }
     }
 }
