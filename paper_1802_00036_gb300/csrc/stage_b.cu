@@ -240,7 +240,11 @@ __device__ __forceinline__ void m_row8(const float* __restrict__ Mf, const unsig
 }
 
 // After the median: mirrored ring, blur, inversion, store.  R (kMR x kRS
-// floats) is the Gaussian row-pass buffer; it must not overlap M.
+// floats) is the Gaussian row-pass buffer; it must not overlap M.  On keys
+// the Gaussian is exact: every median value is k / 256 with an integer k <=
+// 25600 (inverted depths are below 100), so its binomial 5 x 5 sum is n /
+// 2^16 with an integer n < 2^23, a float; step 8 then rounds 100 - n / 2^16
+// once, as the exact definition does.
 template <bool KEYS>
 __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restrict__ Mf,
                            unsigned short* __restrict__ Mk, float* __restrict__ R)
@@ -276,19 +280,31 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
         // row pass over all kMR rows of M, the tile's kTBW columns -> R
         for (int i = tid; i < kMR * (kTBW / 4); i += kThreadsB) {
             const int a = i / (kTBW / 4), b0 = 4 * (i - a * (kTBW / 4));
-            float v[8];
-            m_row8<KEYS>(Mf, Mk, a * kMS + b0, v);
-            float o[4];
+            if constexpr (KEYS) {
+                // exact: the integer sums k(-2) + 4 k(-1) + 6 k + 4 k(1) + k(2) of the keys
+                const uint2 lo = *reinterpret_cast<const uint2*>(Mk + a * kMS + b0);
+                const uint2 hi = *reinterpret_cast<const uint2*>(Mk + a * kMS + b0 + 4);
+                const unsigned k[8] = {lo.x & 0xFFFFu, lo.x >> 16, lo.y & 0xFFFFu, lo.y >> 16,
+                                       hi.x & 0xFFFFu, hi.x >> 16, hi.y & 0xFFFFu, hi.y >> 16};
+                unsigned o[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float acc = w0 * v[k];
-                acc = fmaf(w1, v[k + 1], acc);
-                acc = fmaf(w2, v[k + 2], acc);
-                acc = fmaf(w1, v[k + 3], acc);
-                acc = fmaf(w0, v[k + 4], acc);
-                o[k] = acc;
+                for (int j = 0; j < 4; ++j) o[j] = k[j] + k[j + 4] + 4u * (k[j + 1] + k[j + 3]) + 6u * k[j + 2];
+                *reinterpret_cast<uint4*>(R + a * kRS + b0) = make_uint4(o[0], o[1], o[2], o[3]);
+            } else {
+                float v[8];
+                m_row8<KEYS>(Mf, Mk, a * kMS + b0, v);
+                float o[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float acc = w0 * v[k];
+                    acc = fmaf(w1, v[k + 1], acc);
+                    acc = fmaf(w2, v[k + 2], acc);
+                    acc = fmaf(w1, v[k + 3], acc);
+                    acc = fmaf(w0, v[k + 4], acc);
+                    o[k] = acc;
+                }
+                *reinterpret_cast<float4*>(R + a * kRS + b0) = make_float4(o[0], o[1], o[2], o[3]);
             }
-            *reinterpret_cast<float4*>(R + a * kRS + b0) = make_float4(o[0], o[1], o[2], o[3]);
         }
         __syncthreads();
     }
@@ -325,15 +341,30 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
                         e0 = is_empty(m2.x);
                         e1 = is_empty(m2.y);
                     }
-                    float acc0 = w0 * r[k].x, acc1 = w0 * r[k].y;
-                    acc0 = fmaf(w1, r[k + 1].x, acc0);
-                    acc1 = fmaf(w1, r[k + 1].y, acc1);
-                    acc0 = fmaf(w2, r[k + 2].x, acc0);
-                    acc1 = fmaf(w2, r[k + 2].y, acc1);
-                    acc0 = fmaf(w1, r[k + 3].x, acc0);
-                    acc1 = fmaf(w1, r[k + 3].y, acc1);
-                    acc0 = fmaf(w0, r[k + 4].x, acc0);
-                    acc1 = fmaf(w0, r[k + 4].y, acc1);
+                    float acc0, acc1;
+                    if constexpr (KEYS) {
+                        // the integer 5 x 5 sum n over keys; the blur is n / 2^16 exactly
+                        // (n < 256 * 25600 < 2^23, so 2^7 + n / 2^16 is a float)
+                        const unsigned n0 = __float_as_uint(r[k].x) + __float_as_uint(r[k + 4].x) +
+                                            4u * (__float_as_uint(r[k + 1].x) + __float_as_uint(r[k + 3].x)) +
+                                            6u * __float_as_uint(r[k + 2].x);
+                        const unsigned n1 = __float_as_uint(r[k].y) + __float_as_uint(r[k + 4].y) +
+                                            4u * (__float_as_uint(r[k + 1].y) + __float_as_uint(r[k + 3].y)) +
+                                            6u * __float_as_uint(r[k + 2].y);
+                        acc0 = __uint_as_float(0x43000000u | n0) - 128.0f;
+                        acc1 = __uint_as_float(0x43000000u | n1) - 128.0f;
+                    } else {
+                        acc0 = w0 * r[k].x;
+                        acc1 = w0 * r[k].y;
+                        acc0 = fmaf(w1, r[k + 1].x, acc0);
+                        acc1 = fmaf(w1, r[k + 1].y, acc1);
+                        acc0 = fmaf(w2, r[k + 2].x, acc0);
+                        acc1 = fmaf(w2, r[k + 2].y, acc1);
+                        acc0 = fmaf(w1, r[k + 3].x, acc0);
+                        acc1 = fmaf(w1, r[k + 3].y, acc1);
+                        acc0 = fmaf(w0, r[k + 4].x, acc0);
+                        acc1 = fmaf(w0, r[k + 4].y, acc1);
+                    }
                     float o0, o1;
                     if (p.stop == kStopBlur) {  // the blurred map itself (inverted domain)
                         o0 = e0 ? m_at<KEYS>(Mf, Mk, mi) : acc0;
@@ -619,7 +650,10 @@ __device__ void constant_tile_store(const Tile& T, const StageBParams& p, const 
     }
     __syncthreads();
     if (tid < kMC) Mrow[tid] = m;
-    __syncthreads();
+    // all of them 16-bit keys: the blur below is exact, as in the general path
+    bool ok = true;
+    if (tid < kMC) key_of(m, ok);
+    const bool keys = __syncthreads_and(ok);
     constexpr float w0 = 0.0625f, w1 = 0.25f, w2 = 0.375f;
     if (tid < kTBW) {
         const int b = tid;
@@ -630,7 +664,16 @@ __device__ void constant_tile_store(const Tile& T, const StageBParams& p, const 
         } else if (p.stop != kStopMedian) {
             float g = mc;
             if (!is_empty(mc)) {
-                if (p.blur == kBlurGauss) {
+                if (p.blur == kBlurGauss && keys) {
+                    // the 5 x 5 sum over keys is 16 times the row sum n over keys:
+                    // the blur is n / 2^12 (n < 16 * 25600 < 2^23)
+                    bool unused = true;
+                    unsigned kk[5];
+#pragma unroll
+                    for (int j = 0; j < 5; ++j) kk[j] = key_of(Mrow[b + j], unused);
+                    const unsigned n = kk[0] + kk[4] + 4u * (kk[1] + kk[3]) + 6u * kk[2];
+                    g = __uint_as_float(0x45000000u | n) - 2048.0f;
+                } else if (p.blur == kBlurGauss) {
                     float r = w0 * Mrow[b];
                     r = fmaf(w1, Mrow[b + 1], r);
                     r = fmaf(w2, Mrow[b + 2], r);

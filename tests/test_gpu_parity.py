@@ -194,6 +194,21 @@ def test_full_size_frame_352x1216(ctx):
                 stop, "352x1216")
 
 
+@pytest.mark.parametrize("stop", ["blur", "full"])
+def test_quantised_frames_bit_exact_through_the_blur(ctx, stop):
+    # depths in steps of 1/256 m (KITTI's fixed point): every tile runs on
+    # 16-bit keys and the Gaussian is summed exactly, so the whole chain --
+    # blur and final inversion included -- equals the oracle bit for bit
+    frames = [synth.make_frame(synth.ONE_FRAME, synth.frame_seed(0, 1)),
+              synth.make_frame(SMALL, 777)]
+    for f in frames:
+        assert np.array_equal(np.rint(f * 256.0) / 256.0, f)
+        got = gpu_run(ctx, f[None], stop_after=stop)[0]
+        want = oracle.complete(f, stop_after=stop)
+        bad = np.argwhere(got.view(np.uint32) != want.view(np.uint32))
+        assert len(bad) == 0, f"{len(bad)} mismatches, first {bad[:5].tolist()}"
+
+
 def test_batched_375x1242_sampled_and_batch_independent(ctx):
     # the 64-frame batched workload; three frames checked against the oracle,
     # every frame checked against its own single-frame run
