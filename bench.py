@@ -456,7 +456,7 @@ def run_serving(seconds):
     import torch
 
     from paper_1802_00036_gb300 import synth
-    from paper_1802_00036_gb300.serve import Server, drive
+    from paper_1802_00036_gb300.serve import NativeServer, drive_native
     sensors = 8
     pools = []
     for s in range(sensors):
@@ -468,15 +468,16 @@ def run_serving(seconds):
             pool.append(torch.from_numpy(f).pin_memory())
         pools.append(pool)
     out = {"sensors": sensors, "mix": "50/50 352x1216 / 512x2048, 3-10 % valid", "budget_bytes": 2 << 30,
-           "deadline_ms": 2.0, "seconds_per_rate": seconds, "rates": []}
-    for rate in (125.0, 1000.0, 4000.0):
+           "deadline_ms": 2.0, "seconds_per_rate": seconds, "server": "dc_server (native worker), 3 lanes",
+           "latency": "scheduled arrival to result in pinned host memory", "rates": []}
+    for rate in (125.0, 1000.0, 4000.0, 8000.0):
         row = {"per_sensor_hz": rate}
         for name, kw in (("batched", dict(deadline_ms=2.0, max_batch=64, lanes=3)),
                          ("per_frame", dict(deadline_ms=0.0, max_batch=1, lanes=3))):
-            srv = Server(max_hw=(512, 2048), budget_bytes=2 << 30, copy_results=False, **kw)
+            srv = NativeServer(max_hw=(512, 2048), budget_bytes=2 << 30, **kw)
             try:
-                drive(srv, pools, 50.0, 0.2, seed=1)          # warm-up
-                res = drive(srv, pools, rate, seconds, seed=2)
+                drive_native(srv, pools, 50.0, 0.2, seed=1)          # warm-up
+                res = drive_native(srv, pools, rate, seconds, seed=2)
             finally:
                 srv.close()
             row[name] = {k: round(v, 3) if isinstance(v, float) else v for k, v in res.items()}

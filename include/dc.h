@@ -265,6 +265,62 @@ void dc_destroy(dc_ctx* ctx);
 dc_status dc_complete_noalloc(const float* in, float* out, int n, int H, int W,
                               const dc_params* params, void* stream);
 
+/* ---- Serving: continuous batching on one GPU ----------------------------
+ *
+ * The paper has no counterpart: the chain served to several sensors whose
+ * frames arrive one at a time (the serving workload: frames of mixed sizes
+ * from several sensors, p50 / p99 latency beside throughput).  A worker
+ * thread of the server owns all device work:
+ *   - a submitted frame takes a free device slot (input and output frames of
+ *     max_H x max_W; the slots share budget_bytes with the lanes' scratch)
+ *     and is copied in; with no free slot it waits (back-pressure);
+ *   - the copied frames form a batch when max_batch of them are ready or the
+ *     oldest has waited deadline_us since it was submitted, and the batch
+ *     runs as one dc_complete on a free lane (one of `lanes`, each with its
+ *     own context, scratch reserved for a full batch, and stream), followed
+ *     on that stream by the copies of the results into the callers' buffers;
+ *   - once a lane's work has passed, its frames are reported done with their
+ *     latency: from submission to the result in host memory.
+ * Results are those of dc_complete for the frame alone.  Errors of the
+ * worker's CUDA calls are sticky: returned by the next submit, poll or
+ * stats call. */
+typedef struct dc_server dc_server;
+
+typedef struct {
+    unsigned long long submitted; /* frames accepted by dc_server_submit */
+    unsigned long long done;      /* frames whose result is in host memory */
+    unsigned long long batches;   /* batches run */
+    int slots;                    /* device slots (frames in flight at most) */
+    int lanes;
+} dc_server_stats;
+
+/* Create a server on `device` for frames of at most max_H x max_W.
+ * DC_ERR_OOM when budget_bytes cannot hold the lanes' scratch and one slot
+ * (or device memory runs out); DC_ERR_INVALID_ARG for bad sizes, a negative
+ * deadline, max_batch < 1 or lanes outside 1..16. */
+dc_status dc_server_create(dc_server** srv, int device, int max_H, int max_W, size_t budget_bytes,
+                           int deadline_us, int max_batch, int lanes, const dc_params* params);
+
+/* Queue one H x W frame (host_in, float32 depths, row pitch W).  host_out
+ * (H x W) receives the dense map; neither buffer may be touched until the
+ * frame's tag comes back from dc_server_poll.  Pinned host memory keeps the
+ * copies asynchronous.  Thread-safe.  DC_ERR_INVALID_ARG for null buffers or
+ * a size beyond the server's maximum. */
+dc_status dc_server_submit(dc_server* srv, const float* host_in, float* host_out, int H, int W,
+                           unsigned long long tag);
+
+/* The frames done since the last call, oldest first: up to `max` tags and
+ * (when latency_ms is not null) their latencies in ms; *n_done receives the
+ * count.  Thread-safe. */
+dc_status dc_server_poll(dc_server* srv, unsigned long long* tags, double* latency_ms, int max,
+                         int* n_done);
+
+/* Counters of the server. */
+dc_status dc_server_get_stats(dc_server* srv, dc_server_stats* stats);
+
+/* Stop accepting frames, finish every queued one, free everything. */
+void dc_server_destroy(dc_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

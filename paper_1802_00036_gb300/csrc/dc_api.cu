@@ -409,7 +409,7 @@ dc_status dc_reserve(dc_ctx* ctx, int n_frames, int H, int W)
     DeviceGuard g(ctx->device);
     const size_t tiles = (size_t)ceil_div(W, kTileBW) * (size_t)ceil_div(H, kTileBH) * (size_t)n_frames;
     return note(ctx, grow(ctx, frame_c_floats(H, W) * (size_t)n_frames,
-                          frame_top_ints(W) * (size_t)n_frames, n_frames, 0, tiles + 2));
+                          frame_top_ints(W) * (size_t)n_frames, n_frames, 0, tiles + 3));
 }
 
 dc_status dc_complete(dc_ctx* ctx, const dc_frame* frames, int n_frames, const dc_params* params,

@@ -51,6 +51,11 @@ class dc_tuning(ctypes.Structure):
                 ("b_sparse_fill", ctypes.c_int)]
 
 
+class dc_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_ulonglong), ("done", ctypes.c_ulonglong),
+                ("batches", ctypes.c_ulonglong), ("slots", ctypes.c_int), ("lanes", ctypes.c_int)]
+
+
 class dc_frame(ctypes.Structure):
     _fields_ = [
         ("in_", ctypes.c_void_p),
@@ -100,6 +105,15 @@ SIGNATURES = [
     ("dc_destroy", None, [ctypes.c_void_p]),
     ("dc_complete_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, ctypes.POINTER(dc_params), ctypes.c_void_p]),
+    ("dc_server_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(dc_params)]),
+    ("dc_server_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_ulonglong]),
+    ("dc_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("dc_server_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dc_server_stats)]),
+    ("dc_server_destroy", None, [ctypes.c_void_p]),
 ]
 
 
@@ -188,6 +202,40 @@ def dc_complete_host_async(ctx, host_in: int, host_out: int, n: int, H: int, W: 
 
 def dc_host_wait(ctx) -> None:
     _check(load().dc_host_wait(ctx), "dc_host_wait")
+
+
+def dc_server_create(device: int, max_H: int, max_W: int, budget_bytes: int, deadline_us: int, max_batch: int,
+                     lanes: int, p: dc_params) -> int:
+    h = ctypes.c_void_p()
+    _check(load().dc_server_create(ctypes.byref(h), device, max_H, max_W, budget_bytes, deadline_us, max_batch,
+                                   lanes, ctypes.byref(p)), "dc_server_create")
+    return h.value
+
+
+def dc_server_submit(srv, host_in: int, host_out: int, H: int, W: int, tag: int) -> None:
+    _check(load().dc_server_submit(srv, ctypes.c_void_p(host_in), ctypes.c_void_p(host_out), H, W, tag),
+           "dc_server_submit")
+
+
+def dc_server_poll(srv, max_n: int = 4096):
+    """[(tag, latency_ms), ...] of the frames done since the last poll."""
+    tags = (ctypes.c_ulonglong * max_n)()
+    lat = (ctypes.c_double * max_n)()
+    n = ctypes.c_int()
+    _check(load().dc_server_poll(srv, tags, lat, max_n, ctypes.byref(n)), "dc_server_poll")
+    return [(tags[i], lat[i]) for i in range(n.value)]
+
+
+def dc_server_get_stats(srv) -> dict:
+    st = dc_server_stats()
+    _check(load().dc_server_get_stats(srv, ctypes.byref(st)), "dc_server_get_stats")
+    return {"submitted": st.submitted, "done": st.done, "batches": st.batches, "slots": st.slots,
+            "lanes": st.lanes}
+
+
+def dc_server_destroy(srv) -> None:
+    if srv:
+        load().dc_server_destroy(srv)
 
 
 def dc_complete_noalloc(in_ptr: int, out_ptr: int, n: int, H: int, W: int, p: dc_params,
