@@ -51,6 +51,9 @@ def parse():
                     help="seconds of Poisson arrivals per rate in the serving leg (0: skip)")
     ap.add_argument("--quick", action="store_true",
                     help="timed batched steps only (no per-frame, e2e or CPU legs): for profiling")
+    ap.add_argument("--configs", action="store_true",
+                    help="instead of the bench line: one JSON line per further workload (the 375x1242 "
+                         "batch with both blurs, the four-resolution mix, the element x fill-size sweep)")
     return ap.parse_args()
 
 
@@ -485,8 +488,100 @@ def run_serving(seconds):
     return out
 
 
+def run_configs(args):
+    """Throughput of the further workloads, one JSON line each.  Every
+    timing: CUDA events around `steps` calls after `warmup` on rotating input
+    sets whose total exceeds the L2; frames/s and algorithmic GB/s (8 B/px)."""
+    import torch
+
+    from paper_1802_00036_gb300 import dc, synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = dc.Context(0)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    steps, warm = max(args.steps // 10, 20), max(args.warmup, 3)
+
+    def timed(call, sets):
+        for i in range(warm):
+            call(i % sets)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            call(i % sets)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps  # ms per call
+
+    def batch_sets(host, sets):
+        return [torch.from_numpy(host).to(dev) for _ in range(sets)], [torch.empty(host.shape, device=dev)
+                                                                        for _ in range(sets)]
+
+    # the 64-frame 375x1242 batch, 4-6 % per frame: one call vs 64 calls, both blurs
+    host = synth.make_batch(64, synth.UNIFORM_375, config=2, density_range=(0.04, 0.06))
+    ins, outs = batch_sets(host, 4)
+    n, H, W = host.shape
+    for blur in ("gauss", "bilateral"):
+        p = dc.params(blur=blur)
+        ms = timed(lambda i: dc.dc_complete_uniform(ctx.h, ins[i].data_ptr(), outs[i].data_ptr(), n, H, W, p, sp), 4)
+        ms1 = timed(lambda i: [dc.dc_complete_uniform(ctx.h, ins[i][k].data_ptr(), outs[i][k].data_ptr(), 1, H, W,
+                                                      p, sp) for k in range(n)], 4)
+        print(json.dumps({"workload": f"64 x 375x1242, 4-6 % valid, 1-90 m, median + {blur}",
+                          "batched_frames_per_s": round(n / ms * 1e3, 1),
+                          "per_frame_frames_per_s": round(n / ms1 * 1e3, 1),
+                          "batched_GBps": round(n * H * W * 8 / ms / 1e6, 1)}), flush=True)
+
+    # the four-resolution mix: 32 frames of each, one call (dc_complete) and per resolution
+    mix = []
+    for k, spec in enumerate(synth.MIX):
+        mix.append(synth.make_batch(32, spec, config=3, first=100 * k))
+    dev_in = [[torch.from_numpy(b).to(dev) for b in mix] for _ in range(2)]
+    dev_out = [[torch.empty(b.shape, device=dev) for b in mix] for _ in range(2)]
+    p = dc.params()
+
+    def frames_of(i):
+        fr = []
+        for b_in, b_out in zip(dev_in[i], dev_out[i]):
+            _, h, w = b_in.shape
+            fr += [(b_in[j].data_ptr(), b_out[j].data_ptr(), h, w, w, w) for j in range(b_in.shape[0])]
+        return fr
+    tables = [frames_of(0), frames_of(1)]
+    ms = timed(lambda i: dc.dc_complete(ctx.h, tables[i], p, sp), 2)
+    px = sum(b.size for b in mix)
+    per_res = {}
+    for k, b in enumerate(mix):
+        _, h, w = b.shape
+        msr = timed(lambda i: dc.dc_complete_uniform(ctx.h, dev_in[i][k].data_ptr(), dev_out[i][k].data_ptr(), 32, h,
+                                                     w, p, sp), 2)
+        per_res[f"{h}x{w}"] = round(32 / msr * 1e3, 1)
+    print(json.dumps({"workload": "128 frames, 32 each of 256x512@3%, 352x1216@5%, 375x1242@5%, 512x2048@10%",
+                      "one_call_frames_per_s": round(128 / ms * 1e3, 1),
+                      "one_call_GBps": round(px * 8 / ms / 1e6, 1),
+                      "per_resolution_batch_of_32_frames_per_s": per_res}), flush=True)
+
+    # first element x large-fill size on 32 x 352x1216
+    host = synth.make_batch(32, synth.ONE_FRAME, config=4)
+    ins, outs = batch_sets(host, 4)
+    n, H, W = host.shape
+    rows = []
+    for shape in ("diamond5", "full5", "cross5", "full3", "circle5", "full7"):
+        for fill in (15, 31, 51):
+            p = dc.params(first_kernel=shape, large_fill=fill)
+            ms = timed(lambda i: dc.dc_complete_uniform(ctx.h, ins[i].data_ptr(), outs[i].data_ptr(), n, H, W, p,
+                                                        sp), 4)
+            rows.append({"first": shape, "fill": fill, "frames_per_s": round(n / ms * 1e3, 1),
+                         "GBps": round(n * H * W * 8 / ms / 1e6, 1)})
+    print(json.dumps({"workload": "32 x 352x1216, 5 % valid: first element x large fill", "rows": rows}),
+          flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.configs:
+        run_configs(args)
+        return
     if args.impl == "reference":
         # the CPU oracle needs no process group: rank 0 runs it, others exit
         run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))

@@ -90,6 +90,7 @@ __device__ __forceinline__ int find_frame(const FrameDesc* __restrict__ d, int n
 // Stage A geometry (stage_a.cu): output columns per strip and the halo
 // (= vertical delay) for a first element.
 int stage_a_strip_width(int shape);
+int stage_a_strips(int W, int shape);  // strips covering W columns (the first writes its left halo)
 int stage_a_halo(int shape);
 // Rows per stage-A band so that a batch with `total_strips` strips gives
 // about `target_warps` warps; at least 32 rows.

@@ -236,9 +236,8 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
 
     // layout of scratch, stage-A units (strip x band) and stage-B tiles
     std::vector<FrameDesc> desc((size_t)n);
-    const int strip_w = stage_a_strip_width(p->first_kernel);
     long long total_strips = 0;
-    for (int i = 0; i < n; ++i) total_strips += ceil_div(frames[i].W, strip_w);
+    for (int i = 0; i < n; ++i) total_strips += stage_a_strips(frames[i].W, p->first_kernel);
     size_t c_off = 0, top_off = 0;
     long long tiles_a = 0, tiles_b = 0;
     for (int i = 0; i < n; ++i) {
@@ -251,7 +250,7 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         d.in_pitch = f.in_pitch;
         d.out_pitch = f.out_pitch;
         d.c_pitch = (int)round_up((size_t)f.W, 32);
-        d.tiles_x_a = ceil_div(f.W, strip_w);
+        d.tiles_x_a = stage_a_strips(f.W, p->first_kernel);
         d.band_a = stage_a_band_rows(f.H, total_strips, (long long)ctx->tune.a_warps_per_sm * ctx->sm_count);
         d.tiles_x_b = ceil_div(f.W, kTileBW);
         d.base_a = (int)tiles_a;

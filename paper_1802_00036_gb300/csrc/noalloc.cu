@@ -131,8 +131,7 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     int* work = reinterpret_cast<int*>(base + kTableBytes + kTopBytes);
     float* cmap = reinterpret_cast<float*>(base + kTableBytes + kTopBytes + kWorkBytes);
     const bool need_b = (params->stop_after == DC_STOP_FULL || params->stop_after >= DC_STOP_EXTEND);
-    const int strip_w = stage_a_strip_width(params->first_kernel);
-    const int tiles_x_a = (W + strip_w - 1) / strip_w;
+    const int tiles_x_a = stage_a_strips(W, params->first_kernel);
     const int band_a = stage_a_band_rows(H, (long long)tiles_x_a * n,
                                          (long long)kDefaultTuning.a_warps_per_sm * sms);
     const int tiles_a = tiles_x_a * ((H + band_a - 1) / band_a);

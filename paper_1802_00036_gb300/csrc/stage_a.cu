@@ -57,15 +57,20 @@ struct Row {
     }
 };
 
-// Fetch `rad` neighbour columns on each side from the adjacent lanes.
+// Fetch `rad` neighbour columns on each side from the adjacent lanes.  In a
+// strip that starts at the frame's first column (at_left, warp-uniform) the
+// columns left of lane 0 are outside the frame: the operation's neutral value.
 template <int rad>
-__device__ __forceinline__ void neighbours(Row& x)
+__device__ __forceinline__ void neighbours(Row& x, bool at_left, float neutral)
 {
 #pragma unroll
     for (int i = 1; i <= rad; ++i) {
         x.l[i] = __shfl_up_sync(0xffffffffu, x.v[kV - i], 1);
         x.r[i] = __shfl_down_sync(0xffffffffu, x.v[i - 1], 1);
     }
+    if (at_left && (threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int i = 1; i <= rad; ++i) x.l[i] = neutral;
 }
 
 template <bool kMax>
@@ -118,9 +123,9 @@ template <> struct FirstDilation<kDiamond5> {
         for (int v = 0; v < kV; ++v) x[0][v] = x[1][v] = p[0][v] = p[1][v] = h1[v] = ninf();
     }
     template <int PHI>
-    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV], bool at_left)
     {
-        neighbours<2>(in);
+        neighbours<2>(in, at_left, ninf());
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
             const float a1 = max3f(in.at(v - 1), in.v[v], in.at(v + 1));
@@ -142,9 +147,9 @@ template <> struct FirstDilation<kFull5> {
         for (int v = 0; v < kV; ++v) h[0][v] = h[1][v] = s[0][v] = s[1][v] = ninf();
     }
     template <int PHI>
-    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV], bool at_left)
     {
-        neighbours<2>(in);
+        neighbours<2>(in, at_left, ninf());
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
             const float a2 = max3f(max3f(in.at(v - 2), in.at(v - 1), in.v[v]), in.at(v + 1), in.at(v + 2));
@@ -164,9 +169,9 @@ template <> struct FirstDilation<kCross5> {
         for (int v = 0; v < kV; ++v) x[0][v] = x[1][v] = p[0][v] = p[1][v] = ninf();
     }
     template <int PHI>
-    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV], bool at_left)
     {
-        neighbours<2>(in);
+        neighbours<2>(in, at_left, ninf());
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
             const float a2 = max3f(max3f(in.at(v - 2), in.at(v - 1), in.v[v]), in.at(v + 1), in.at(v + 2));
@@ -187,9 +192,9 @@ template <> struct FirstDilation<kFull3> {
         for (int v = 0; v < kV; ++v) h[0][v] = h[1][v] = ninf();
     }
     template <int PHI>
-    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV], bool at_left)
     {
-        neighbours<1>(in);
+        neighbours<1>(in, at_left, ninf());
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
             const float a1 = max3f(in.at(v - 1), in.v[v], in.at(v + 1));
@@ -208,9 +213,9 @@ template <> struct FirstDilation<kCircle5> {
         for (int v = 0; v < kV; ++v) h1[0][v] = h1[1][v] = h2[v] = p[0][v] = p[1][v] = ninf();
     }
     template <int PHI>
-    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV], bool at_left)
     {
-        neighbours<2>(in);
+        neighbours<2>(in, at_left, ninf());
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
             const float a1 = max3f(in.at(v - 1), in.v[v], in.at(v + 1));
@@ -228,9 +233,9 @@ template <> struct FirstDilation<kFull7> {
     Window7<true> w;
     __device__ void init() { w.init(ninf()); }
     template <int PHI>
-    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV], bool at_left)
     {
-        neighbours<3>(in);
+        neighbours<3>(in, at_left, ninf());
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
             const float a3 = max3f(max3f(in.at(v - 3), in.at(v - 2), in.at(v - 1)), in.v[v],
@@ -250,9 +255,9 @@ struct Square5 {
         for (int v = 0; v < kV; ++v) h[0][v] = h[1][v] = s[0][v] = s[1][v] = fill;
     }
     template <int PHI>
-    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV], bool at_left)
     {
-        neighbours<2>(in);
+        neighbours<2>(in, at_left, kMax ? ninf() : pinf());
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
             const float hn =
@@ -275,9 +280,9 @@ struct Fill7 {
         for (int v = 0; v < kV; ++v) b[0][v] = b[1][v] = b[2][v] = b[3][v] = ninf();
     }
     template <int PHI>
-    __device__ __forceinline__ void push(Row& in, float (&out)[kV])
+    __device__ __forceinline__ void push(Row& in, float (&out)[kV], bool at_left)
     {
-        neighbours<3>(in);
+        neighbours<3>(in, at_left, ninf());
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
             const float hn = max3f(max3f(in.at(v - 3), in.at(v - 2), in.at(v - 1)), in.v[v],
@@ -318,15 +323,19 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
     const int H = fd.H, W = fd.W, in_pitch = fd.in_pitch;
     const float* __restrict__ src = fd.in;
     const int r0 = band * fd.band_a, r1 = min(r0 + fd.band_a, H);
-    const int sx = strip * OW - Rh;            // frame column of strip column 0
+    // Strip s reads frame columns [s OW, s OW + kSW) and writes [s OW + Rh,
+    // (s + 1) OW + Rh); the first strip also writes its left halo columns,
+    // which have nothing left of them but the frame's edge.
+    const int sx = strip * OW;                 // frame column of strip column 0
     const int cx = sx + lane * kV;             // frame column of this lane's first column
-    const bool edge = sx < 0 || sx + kSW > W;  // strip crosses a frame edge
+    const bool edge = sx + kSW > W;            // strip crosses the frame's right edge
+    const bool at_left = sx == 0;
     bool col_in[kV], col_out[kV];
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
         const int c = cx + v, j = lane * kV + v;
-        col_in[v] = c >= 0 && c < W;
-        col_out[v] = col_in[v] && j >= Rh && j < Rh + OW;
+        col_in[v] = c < W;
+        col_out[v] = col_in[v] && (j >= Rh || at_left) && j < Rh + OW;
     }
 
     FirstDilation<S> s2;
@@ -404,7 +413,7 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
         load_row(t + 4, raw[PHI]);
         // step 2: row t -> A(t - R1)
         Row a;
-        s2.template push<PHI>(x, a.v);
+        s2.template push<PHI>(x, a.v, at_left);
         const int ra = t - R1;
         const bool a_in = ra >= 0 && ra < H;
         if (!a_in || edge)
@@ -413,7 +422,7 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
                 if (!a_in || !col_in[v]) a.v[v] = ninf();
         // step 3, dilation: A(ra) -> D(ra - 2)
         Row dd;
-        s3d.template push<PHI>(a, dd.v);
+        s3d.template push<PHI>(a, dd.v, at_left);
         const int rd = ra - 2;
         const bool d_in = rd >= 0 && rd < H;
         if (!d_in || edge)
@@ -422,7 +431,7 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
                 if (!d_in || !col_in[v]) dd.v[v] = pinf();
         // step 3, erosion: D(rd) -> B(rd - 2)
         Row b;
-        s3e.template push<PHI>(dd, b.v);
+        s3e.template push<PHI>(dd, b.v, at_left);
         const int rb = rd - 2;
         const bool b_in = rb >= 0 && rb < H;
         if (!b_in || edge)
@@ -431,7 +440,7 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
                 if (!b_in || !col_in[v]) b.v[v] = ninf();
         // step 4: B(rb) -> C(rb - 3)
         float c[kV];
-        s4.template push<PHI>(b, c);
+        s4.template push<PHI>(b, c, at_left);
         const int rc = rb - 3;  // == t - Rh
         if (stop == kStopFull) {
             if (rc >= r0 && rc < r1) {
@@ -526,6 +535,13 @@ int stage_a_halo(int shape)
 }
 
 int stage_a_strip_width(int shape) { return kSW - 2 * stage_a_halo(shape); }
+
+int stage_a_strips(int W, int shape)
+{
+    const int ow = stage_a_strip_width(shape), h = stage_a_halo(shape);
+    const int n = (W - h + ow - 1) / ow;
+    return n < 1 ? 1 : n;
+}
 
 int stage_a_band_rows(int H, long long total_strips, long long target_warps)
 {
