@@ -79,10 +79,12 @@ struct PackedKeyOps {
 // v * 256 is an integer in [0, 2^23).
 __device__ __forceinline__ unsigned key_of(float v, bool& ok)
 {
-    const float scaled = v * 256.0f;
-    const unsigned kb = __float_as_uint(fmaf(v, 256.0f, 8388608.0f));
-    ok = ok && (kb >> 16) == 0x4B00u && (__uint_as_float(kb) - 8388608.0f) == scaled;
-    return kb & 0xFFFFu;
+    // the nearest k / 256 (2^23 + 256 v rounded: k in the low mantissa bits),
+    // then the check that it is v itself, which fails for v outside [0, 256)
+    // and for v between two keys
+    const unsigned k = __float_as_uint(fmaf(v, 256.0f, 8388608.0f)) & 0xFFFFu;
+    ok = ok && (__uint_as_float(0x47000000u | k) - 32768.0f) == v;
+    return k;
 }
 
 // A key k is empty (k / 256 < 0.1) exactly when k <= 25.
@@ -829,10 +831,14 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
                     unsigned em = 0u;  // empty in-frame columns of this chunk row
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
-                        if (e < ncol) {
-                            key[h][e] = key_of(v[e], keys_ok);
-                            em |= (is_empty(v[e]) ? 1u : 0u) << e;
-                        }
+                        if (e < ncol) key[h][e] = key_of(v[e], keys_ok);
+                    // most chunks hold no empty pixel: test their smallest value first
+                    // (out-of-frame columns of a chunk at the right edge hold pixels
+                    // of the next row's start or padding, and are masked below)
+                    if (is_empty(fminf(fminf(v[0], v[1]), fminf(v[2], v[3]))))
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (e < ncol) em |= (is_empty(v[e]) ? 1u : 0u) << e;
                     // rows kHalf .. kPR - 1 appear in both halves: count them once
                     const bool counted = (h == 0) || (kp >= kPR - kHalf);
                     if (em && counted && p.large_fill_on) {
