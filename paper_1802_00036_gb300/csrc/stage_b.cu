@@ -930,10 +930,14 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
                     __syncthreads();
                     for (int r0 = 0; r0 < BR; r0 += RB) {
                         const int nb = min(RB, BR - r0);
-                        // the band of E (step 5 applied) ...
+                        // the band of E (step 5 applied): inside the tile's region from
+                        // shared memory, elsewhere from C ...
                         for (int i = tid; i < nb * BC; i += kThreadsB) {
                             const int r = i / BC, c = i - r * BC;
-                            band[i] = extended(T, p, by0 + r0 + r, bx0 + c, btop[c], btv[c]);
+                            const int k = by0 + r0 + r - (T.y0 - 4), l = bx0 + c - (T.x0 - 4);
+                            band[i] = ((unsigned)k < (unsigned)kER && (unsigned)l < (unsigned)kEC)
+                                          ? E[k * kES + l]
+                                          : extended(T, p, by0 + r0 + r, bx0 + c, btop[c], btv[c]);
                         }
                         __syncthreads();
                         // ... its row maxima over the window width at the empty columns
