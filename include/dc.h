@@ -221,7 +221,9 @@ dc_status dc_set_profiling(dc_ctx* ctx, int on);
 dc_status dc_kernel_times(dc_ctx* ctx, float* ms, int max_calls, int* n_out);
 
 /* First asynchronous error seen on the context's work so far (clears it).
- * Synchronises the context's last stream. */
+ * Synchronises the context's last stream.  DC_ERR_TIMEOUT: a kernel's
+ * bounded wait for its tensor copy of a region gave up (that kernel stopped;
+ * its outputs are incomplete). */
 dc_status dc_last_async_error(dc_ctx* ctx);
 
 /* Human-readable name of a status code (static storage). */

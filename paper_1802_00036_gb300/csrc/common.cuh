@@ -8,6 +8,7 @@
 //   stage B: steps 5-8 on halo'd tiles of C, writes the output.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -65,6 +66,7 @@ struct StageBParams {
     int stop;
     int sparse_fill_max;  // a tile with more empty pixels goes to the step-6 worklist
     int row_stride;       // frames of one shape: the batch's tiles per tile row (tile order), else 0
+    int tma;              // 1: regions come by one tensor copy through the CUtensorMap of C (frames of one shape)
     float ws[5];        // bilateral spatial weight for dy^2+dx^2 = 0,1,2,(3),4
     float inv_2sc2;     // 1 / (2 sigma_color^2)
 };
@@ -114,9 +116,12 @@ constexpr Tuning kDefaultTuning{8, 5, 160};
 cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_units,
                            int shape, int stop, int* work, int band_stride, int sm_count,
                            cudaStream_t stream);
+// cmap: with p.tma, the tensor map of the batch's step-4 maps C as a
+// W x H x n_frames array (rows c_pitch floats apart, frames H c_pitch);
+// err: set to 1 when a bounded device-side wait gives up.
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,
                            const StageBParams& p, int* worklist, int sm_count, int ctas_per_sm,
-                           cudaStream_t stream);
+                           const CUtensorMap* cmap, int* err, cudaStream_t stream);
 
 // Accuracy measures (metrics.cu): acc holds 5 n doubles of scratch, out
 // (device) receives 5 n doubles.

@@ -3,6 +3,8 @@
 #include "../../include/dc.h"
 #include "common.cuh"
 
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -31,6 +33,11 @@ struct dc_ctx {
     size_t work_cap = 0;      // ints
     double* acc = nullptr;    // accuracy sums and results, 10 doubles per frame
     int acc_cap = 0;          // frames
+    int* err = nullptr;          // set by a device-side wait that gave up (device int)
+    // the tensor map of C for batches of one shape, kept while the layout holds
+    CUtensorMap cmap{};
+    const void* cmap_base = nullptr;
+    int cmap_W = 0, cmap_H = 0, cmap_n = 0, cmap_pitch = 0;
     FrameDesc* table = nullptr;  // frame descriptors of the current call (device)
     int frames_cap = 0;          // descriptors
     cudaEvent_t done = nullptr;  // recorded after each call's last kernel
@@ -229,6 +236,52 @@ cudaError_t put_table(const FrameDesc* desc, int n, FrameDesc* dst, int* top, si
 size_t frame_c_floats(int H, int W) { return round_up((size_t)W, 32) * (size_t)H; }
 size_t frame_top_ints(int W) { return round_up((size_t)W, 32); }
 
+// cuTensorMapEncodeTiled from the driver, looked up once (no link-time
+// dependency on the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// The tensor map of n step-4 maps of H x W (rows `pitch` floats apart,
+// frames H pitch floats apart) at `base`, with a box of the stage-B region;
+// false if it cannot be made (then the regions come by cp.async).
+bool c_tensor_map(dc_ctx* ctx, const float* base, int n, int H, int W, int pitch)
+{
+    if (ctx->cmap_base == base && ctx->cmap_n == n && ctx->cmap_H == H && ctx->cmap_W == W &&
+        ctx->cmap_pitch == pitch)
+        return true;
+    ctx->cmap_base = nullptr;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || (reinterpret_cast<uintptr_t>(base) % 16) != 0 || (pitch * sizeof(float)) % 16 != 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * sizeof(float), (cuuint64_t)pitch * sizeof(float) * H};
+    const cuuint32_t box[3] = {(cuuint32_t)(kTileBW + 8), (cuuint32_t)(kTileBH + 8), 1};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    if (enc(&ctx->cmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    ctx->cmap_base = base;
+    ctx->cmap_n = n;
+    ctx->cmap_H = H;
+    ctx->cmap_W = W;
+    ctx->cmap_pitch = pitch;
+    return true;
+}
+
 dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cudaStream_t stream)
 {
     ctx->last_launches = 0;
@@ -315,7 +368,11 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         const double sc = p->blur == DC_BLUR_BILATERAL ? p->sigma_color : 1.0;
         for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));
         bp.inv_2sc2 = (float)(1.0 / (2.0 * sc * sc));
-        e = launch_stage_b(ctx->table, n, (int)tiles_b, bp, ctx->work, ctx->sm_count, ctx->tune.b_ctas_per_sm, stream);
+        // frames of one shape: C is one W x H x n array, one tensor map
+        const bool tma = one_shape && c_tensor_map(ctx, desc[0].c, n, frames[0].H, frames[0].W, desc[0].c_pitch);
+        bp.tma = tma ? 1 : 0;
+        e = launch_stage_b(ctx->table, n, (int)tiles_b, bp, ctx->work, ctx->sm_count, ctx->tune.b_ctas_per_sm,
+                           tma ? &ctx->cmap : nullptr, ctx->err, stream);
         if (e != cudaSuccess) return DC_ERR_CUDA;
         // stage B is one kernel, plus the step-6 pass when step 6 can run
         ctx->last_launches = table_launches + ((bp.large_fill_on && bp.stop != kStopExtend) ? 3 : 2);
@@ -393,6 +450,7 @@ dc_status dc_create(dc_ctx** out, int device, size_t scratch_budget_bytes)
     DeviceGuard g(device);
     bool ok = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&ctx->done, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaMalloc(&ctx->err, sizeof(int)) == cudaSuccess && cudaMemset(ctx->err, 0, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         dc_destroy(ctx);
@@ -720,6 +778,12 @@ dc_status dc_last_async_error(dc_ctx* ctx)
     dc_status s = ctx->sticky;
     ctx->sticky = DC_OK;
     if (cudaStreamSynchronize(ctx->last_stream) != cudaSuccess) s = DC_ERR_CUDA;
+    int waited_out = 0;
+    if (ctx->err && cudaMemcpy(&waited_out, ctx->err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess &&
+        waited_out != 0) {
+        cudaMemset(ctx->err, 0, sizeof(int));
+        if (s == DC_OK) s = DC_ERR_TIMEOUT;
+    }
     if (cudaGetLastError() != cudaSuccess) s = DC_ERR_CUDA;
     return s;
 }
@@ -748,6 +812,7 @@ void dc_destroy(dc_ctx* ctx)
         cudaFree(ctx->work);
         cudaFree(ctx->acc);
         cudaFree(ctx->table);
+        cudaFree(ctx->err);
         if (ctx->done) cudaEventDestroy(ctx->done);
         for (int k = 0; k < 2; ++k) {
             cudaFree(ctx->io_in[k]);

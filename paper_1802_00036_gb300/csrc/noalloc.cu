@@ -137,7 +137,7 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     const int tiles_a = tiles_x_a * ((H + band_a - 1) / band_a);
     const int tiles_x_b = (W + kTileBW - 1) / kTileBW;
     const int tiles_b = tiles_x_b * ((H + kTileBH - 1) / kTileBH);
-    if ((long long)tiles_a * n > INT32_MAX / 2 || (long long)tiles_b * n + 3 > DC_NOALLOC_WORK_INTS)
+    if ((long long)tiles_a * n > INT32_MAX / 2 || (long long)tiles_b * n + 4 > DC_NOALLOC_WORK_INTS)
         return DC_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
 
@@ -169,7 +169,8 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
         const double sc = params->blur == DC_BLUR_BILATERAL ? params->sigma_color : 1.0;
         for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));
         bp.inv_2sc2 = (float)(1.0 / (2.0 * sc * sc));
-        if (launch_stage_b(table, n, tiles_b * n, bp, work, sms, kDefaultTuning.b_ctas_per_sm, st) != cudaSuccess)
+        if (launch_stage_b(table, n, tiles_b * n, bp, work, sms, kDefaultTuning.b_ctas_per_sm, nullptr,
+                           work + DC_NOALLOC_WORK_INTS - 1, st) != cudaSuccess)
             return DC_ERR_CUDA;
     }
     return DC_OK;

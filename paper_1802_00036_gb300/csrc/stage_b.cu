@@ -109,6 +109,7 @@ __device__ __forceinline__ int reflect101(int p, int n)
 struct Tile {
     FrameDesc fd;
     int y0, x0;  // first output pixel
+    int f;       // frame index in the batch
 };
 
 // Positions of a rows x cols region (origin at tile pixel - w) that lie
@@ -166,10 +167,12 @@ __device__ __forceinline__ Tile tile_of(const FrameDesc* __restrict__ frames, in
         T.fd = frames[f];
         T.y0 = ((T.fd.H + kTBH - 1) / kTBH - 1 - r) * kTBH;
         T.x0 = (g - f * T.fd.tiles_x_b) * kTBW;
+        T.f = f;
         return T;
     }
     const int f = find_frame<false>(frames, n_frames, t);
     T.fd = frames[f];
+    T.f = f;
     const int local = t - T.fd.base_b;
     const int ty = local / T.fd.tiles_x_b;
     T.y0 = ty * kTBH;
@@ -550,6 +553,56 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// The region by one tensor copy (TMA): thread 0 arms the CTA's mbarrier with
+// the byte count and starts the copy of the kER x kEC box at (x, y, frame) of
+// C; parts outside the frame arrive as zeros (they are never read as pixels).
+// Every thread then waits for the barrier's phase, a bounded number of times.
+constexpr unsigned kRegionBytes = kER * kEC * sizeof(float);
+static_assert(kEC == kES && (kEC * sizeof(float)) % 16 == 0, "dense 16-byte rows in the tensor box");
+
+__device__ __forceinline__ unsigned smem_addr(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* mbar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_region(float* dst, const CUtensorMap* map, int x, int y, int f,
+                                           unsigned long long* mbar)
+{
+    // earlier reads and writes of dst (the previous tile) before the copy writes it
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(mbar)),
+                 "r"(kRegionBytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+            smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(f), "r"(smem_addr(mbar))
+        : "memory");
+}
+
+// Wait until the barrier's current phase (parity) completes; false if it
+// has not after ~4M polls (each poll may suspend the thread for a while).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* mbar, unsigned parity)
+{
+    const unsigned a = smem_addr(mbar);
+    for (int i = 0; i < (1 << 22); ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // Region work is split by column chunk: thread t < kRowGroups x kChunksPerRow
 // takes chunk t % kChunksPerRow of every kRowGroups-th row from t /
 // kChunksPerRow, so its column bounds and column tops are computed once.
@@ -729,12 +782,12 @@ __device__ void constant_tile_store(const Tile& T, const StageBParams& p, const 
 // tile that needs more also takes K and rebuilds its keys afterwards
 // (kBigScratch floats).  The total leaves room for five CTAs per SM
 // (233,472 bytes; allocations in 128-byte units, 1 KB reserved per CTA).
-constexpr int kScratchExtra = 1824;
+constexpr int kScratchExtra = 1792;
 constexpr int kSmallScratch = kMR * kMS / 2 + kScratchExtra;
 constexpr int kBigScratch = kPR * kES + kSmallScratch;
 constexpr size_t kMainSmemFloats =
     kER * kES + kPR * kES + kMR * kMS / 2 + kScratchExtra + 2 * kEC + kMaxSparseFill + 4 + 4 + 2 * kEC;
-constexpr size_t kMainStaticSmem = 32;  // s_next, ebox
+constexpr size_t kMainStaticSmem = 128;  // s_next, ebox, the mbarrier: padded to the dynamic part's alignment
 static_assert(kPR * kES + kMR * kMS / 2 >= kMR * kMS, "the float median output fits over K and Mk");
 static_assert((kER * kES) % 4 == 0 && (kPR * kES) % 4 == 0 && kMS % 8 == 0, "16-byte aligned buffers and rows");
 static_assert(5 * ((kMainSmemFloats * 4 + kMainStaticSmem + 127) / 128 * 128 + 1024) <= 233472,
@@ -747,9 +800,9 @@ static_assert(5 * ((kMainSmemFloats * 4 + kMainStaticSmem + 127) / 128 * 128 + 1
 // than a second buffer would (that costs CTAs per SM).
 __global__ void __launch_bounds__(kThreadsB, 5)
 stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles, StageBParams p,
-             int* __restrict__ worklist)
+             int* __restrict__ worklist, const __grid_constant__ CUtensorMap cmap, int* __restrict__ err)
 {
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];  // the tensor copy wants 128-byte alignment
     float* Ebuf = smem;                                                      // the region
     unsigned* K = reinterpret_cast<unsigned*>(smem + kER * kES);             // packed keys
     unsigned short* Mk = reinterpret_cast<unsigned short*>(K + kPR * kES);   // median output, keys
@@ -769,10 +822,18 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
     if (t >= total_tiles) return;
     Tile T = tile_of(frames, n_frames, t, p.row_stride);
     __shared__ int s_next;
+    __shared__ __align__(8) unsigned long long s_mbar;  // completion of the region's tensor copy
+    unsigned mbar_parity = 0;
+    if (p.tma && tid == 0) mbar_init(&s_mbar);
+    __syncthreads();
     for (int it = 0;; ++it) {
         float* E = Ebuf;
         const int H = T.fd.H, W = T.fd.W;
-        issue_region(T, E);
+        if (p.tma) {
+            if (tid == 0) tma_region(E, &cmap, T.x0 - 4, T.y0 - 4, T.f, &s_mbar);
+        } else {
+            issue_region(T, E);
+        }
         load_tops(T, p, T.x0 - 4, kEC, ctop, cval);
         if (tid == 0) {
             *ecount = 0;
@@ -781,8 +842,17 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
             ecols[0] = ecols[1] = ecols[2] = 0u;
             s_next = (int)gridDim.x + atomicAdd(worklist + 1, 1);
         }
-        cp_async_wait_all();
-        __syncthreads();
+        if (p.tma) {
+            const bool arrived = mbar_wait(&s_mbar, mbar_parity);
+            mbar_parity ^= 1u;
+            if (!__syncthreads_and(arrived)) {  // the copy never completed: report, stop
+                if (tid == 0) atomicOr(err, 1);
+                return;
+            }
+        } else {
+            cp_async_wait_all();
+            __syncthreads();
+        }
         const bool ext_tile = __syncthreads_or(tid < kEC && ctop[tid] != kNoTop && ctop[tid] > T.y0 - 4);
         const int tn = s_next;
         const bool more = tn < total_tiles;
@@ -1087,7 +1157,7 @@ size_t stage_b_fill_smem_bytes(int large_radius)
 
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,
                            const StageBParams& p, int* worklist, int sm_count, int ctas_per_sm,
-                           cudaStream_t stream)
+                           const CUtensorMap* cmap, int* err, cudaStream_t stream)
 {
     static int configured_dev = -1;
     int dev = 0;
@@ -1105,7 +1175,11 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
     if (ctas_per_sm < 1) ctas_per_sm = 1;
     if (ctas_per_sm > 5) ctas_per_sm = 5;  // shared memory and registers hold five per SM
     const int main_grid = total_tiles < ctas_per_sm * sm_count ? total_tiles : ctas_per_sm * sm_count;
-    stage_b_main<<<main_grid, kThreadsB, main_smem, stream>>>(d_frames, n_frames, total_tiles, p, worklist);
+    CUtensorMap map{};
+    if (p.tma && cmap) map = *cmap;
+    StageBParams q = p;
+    q.tma = (p.tma && cmap) ? 1 : 0;
+    stage_b_main<<<main_grid, kThreadsB, main_smem, stream>>>(d_frames, n_frames, total_tiles, q, worklist, map, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !p.large_fill_on || p.stop == kStopExtend) return e;
     int grid = 2 * sm_count;

@@ -106,7 +106,7 @@ def _step6_box(f, ty, tx, radius=15):
 
 # Step-6 scratch of a stage-B CTA (floats): without and with the key buffer;
 # a tile uses it when rows x distinct columns + 3 x box width fits.
-SMALL_SCRATCH, BIG_SCRATCH = 3872, 6320
+SMALL_SCRATCH, BIG_SCRATCH = 3840, 6288
 
 
 @pytest.mark.parametrize("layout", ["banded", "keys_rebuilt", "per_pixel"])
