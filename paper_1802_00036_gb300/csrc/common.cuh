@@ -20,8 +20,17 @@ constexpr float kEmptyBelow = 0.1f;
 // D_inv = 100 - D (Section IV-1 and IV-8).
 constexpr float kInvertFrom = 100.0f;
 
-// top[] entries start at this value; any real row is smaller.
+// A column's top row as stage B keeps it (any real row is smaller).
 constexpr int kNoTop = 0x7F7F7F7F;
+
+// A column's top in scratch: the row in the high half, the bits of the
+// (positive) C value there in the low half, so that one 64-bit atomicMin
+// keeps the smallest row with its value and one load brings both.
+constexpr unsigned long long kNoTopPacked = ~0ull;
+__device__ __forceinline__ unsigned long long top_pack(int row, float v)
+{
+    return ((unsigned long long)(unsigned)row << 32) | (unsigned long long)__float_as_uint(v);
+}
 
 // Stage A: one warp streams one (strip, band) unit; 4 units per block.
 constexpr int kStageAColsPerLane = 4;
@@ -47,7 +56,7 @@ struct FrameDesc {
     const float* in;   // sparse depth, in_pitch floats per row
     float* out;        // result, out_pitch floats per row
     float* c;          // step-4 map, c_pitch floats per row (scratch)
-    int* top;          // W entries: topmost non-empty row of C (scratch)
+    unsigned long long* top;  // W entries: top_pack(topmost non-empty row of C, C there); kNoTopPacked: none
     int H, W;
     int in_pitch, out_pitch, c_pitch;
     int tiles_x_a, base_a;  // stage A: strips per frame, first flat unit

@@ -27,8 +27,8 @@ struct dc_ctx {
     // scratch
     float* c = nullptr;       // step-4 maps, all frames
     size_t c_cap = 0;         // floats
-    int* top = nullptr;       // per-column tops, all frames
-    size_t top_cap = 0;       // ints
+    unsigned long long* top = nullptr;  // per-column tops (top_pack), all frames
+    size_t top_cap = 0;                 // entries
     int* work = nullptr;      // counters of both stages, then the step-6 tile list
     size_t work_cap = 0;      // ints
     double* acc = nullptr;    // accuracy sums and results, 10 doubles per frame
@@ -88,7 +88,7 @@ size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
 size_t scratch_bytes(size_t c_floats, size_t top_ints, int frames, size_t io_floats, size_t work_ints)
 {
-    return c_floats * sizeof(float) + top_ints * sizeof(int) + work_ints * sizeof(int) +
+    return c_floats * sizeof(float) + top_ints * sizeof(unsigned long long) + work_ints * sizeof(int) +
            (size_t)frames * sizeof(FrameDesc) + 4 * io_floats * sizeof(float);
 }
 
@@ -137,7 +137,10 @@ dc_status grow(dc_ctx* ctx, size_t c_floats, size_t top_ints, int frames, size_t
         cudaFree(ctx->top);
         ctx->top = nullptr;
         ctx->top_cap = 0;
-        if (cudaMalloc(&ctx->top, nt * sizeof(int)) != cudaSuccess) { cudaGetLastError(); return DC_ERR_OOM; }
+        if (cudaMalloc(&ctx->top, nt * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return DC_ERR_OOM;
+        }
         ctx->top_cap = nt;
     }
     if (nw > ctx->work_cap) {
@@ -188,18 +191,19 @@ static_assert(sizeof(TableChunk<384>) + 64 <= 32764, "kernel parameter space");
 
 template <int K>
 __global__ void table_put(const __grid_constant__ TableChunk<K> src, FrameDesc* __restrict__ dst, int n,
-                          int* __restrict__ top, size_t top_ints, int* __restrict__ counter)
+                          unsigned long long* __restrict__ top, size_t top_ints, int* __restrict__ counter)
 {
     const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     if (counter && tid == 0) *counter = 0;
     for (size_t i = tid; i < (size_t)n; i += stride) dst[i] = src.d[i];
     if (top)
-        for (size_t i = tid; i < top_ints; i += stride) top[i] = kNoTop;
+        for (size_t i = tid; i < top_ints; i += stride) top[i] = kNoTopPacked;
 }
 
 template <int K>
-cudaError_t table_put_chunk(const FrameDesc* desc, int n, FrameDesc* dst, int* top, size_t top_ints, int* counter,
+cudaError_t table_put_chunk(const FrameDesc* desc, int n, FrameDesc* dst, unsigned long long* top, size_t top_ints,
+                            int* counter,
                             int sms, cudaStream_t stream)
 {
     TableChunk<K> c;
@@ -214,13 +218,14 @@ cudaError_t table_put_chunk(const FrameDesc* desc, int n, FrameDesc* dst, int* t
 // Store n descriptors at dst (chunks of up to 384 per launch), reset
 // top_ints column tops and zero *counter; returns the number of launches
 // through *launches.
-cudaError_t put_table(const FrameDesc* desc, int n, FrameDesc* dst, int* top, size_t top_ints, int* counter,
+cudaError_t put_table(const FrameDesc* desc, int n, FrameDesc* dst, unsigned long long* top, size_t top_ints,
+                      int* counter,
                       int sms, cudaStream_t stream, int* launches)
 {
     *launches = 0;
     for (int i = 0; i < n; i += 384) {
         const int m = n - i < 384 ? n - i : 384;
-        int* t = i == 0 ? top : nullptr;
+        unsigned long long* t = i == 0 ? top : nullptr;
         const size_t ti = i == 0 ? top_ints : 0;
         int* z = i == 0 ? counter : nullptr;
         cudaError_t e = m <= 8    ? table_put_chunk<8>(desc + i, m, dst + i, t, ti, z, sms, stream)
@@ -311,7 +316,7 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         tiles_a += (long long)d.tiles_x_a * ceil_div(f.H, d.band_a);
         tiles_b += (long long)d.tiles_x_b * ceil_div(f.H, kTileBH);
         d.c = reinterpret_cast<float*>(c_off);  // offsets until scratch is known
-        d.top = reinterpret_cast<int*>(top_off);
+        d.top = reinterpret_cast<unsigned long long*>(top_off);
         c_off += frame_c_floats(f.H, f.W);
         top_off += frame_top_ints(f.W);
     }

@@ -18,7 +18,7 @@ using namespace dcgb;
 namespace {
 
 constexpr size_t kTableBytes = 65536;
-constexpr size_t kTopBytes = 4u * DC_NOALLOC_MAX_COLUMNS;
+constexpr size_t kTopBytes = 8u * DC_NOALLOC_MAX_COLUMNS;
 constexpr size_t kWorkBytes = 4u * DC_NOALLOC_WORK_INTS;
 constexpr size_t kMapBytes = 4u * DC_NOALLOC_MAX_PIXELS;
 static_assert(kTableBytes + kTopBytes + kWorkBytes + kMapBytes == DC_NOALLOC_SCRATCH_BYTES, "layout");
@@ -59,7 +59,7 @@ dc_status setup(int dev, unsigned char** ptr, int* sms)
 // Writes the frame table for n packed frames, resets the tops and stage A's
 // unit counter: the only preparation the two stage kernels need, done on
 // the device so that the call copies nothing from the host.
-__global__ void noalloc_prepare(FrameDesc* table, int* top, float* cmap, const float* in, float* out,
+__global__ void noalloc_prepare(FrameDesc* table, unsigned long long* top, float* cmap, const float* in, float* out,
                                 int n, int H, int W, int c_pitch, int tiles_x_a, int tiles_a, int band_a,
                                 int tiles_x_b, int tiles_b, int top_ints, int* counter)
 {
@@ -85,7 +85,7 @@ __global__ void noalloc_prepare(FrameDesc* table, int* top, float* cmap, const f
         table[i] = d;
     }
     if (top)
-        for (int i = tid; i < top_ints; i += stride) top[i] = kNoTop;
+        for (int i = tid; i < top_ints; i += stride) top[i] = kNoTopPacked;
 }
 
 bool params_valid(const dc_params* p)
@@ -127,7 +127,7 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     if (s != DC_OK) return s;
 
     FrameDesc* table = reinterpret_cast<FrameDesc*>(base);
-    int* top = reinterpret_cast<int*>(base + kTableBytes);
+    unsigned long long* top = reinterpret_cast<unsigned long long*>(base + kTableBytes);
     int* work = reinterpret_cast<int*>(base + kTableBytes + kTopBytes);
     float* cmap = reinterpret_cast<float*>(base + kTableBytes + kTopBytes + kWorkBytes);
     const bool need_b = (params->stop_after == DC_STOP_FULL || params->stop_after >= DC_STOP_EXTEND);

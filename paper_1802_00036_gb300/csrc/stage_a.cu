@@ -20,7 +20,8 @@
 // rows, and the rings start with values that only reach rows above the band.
 //
 // Output: C (the step-4 map) into scratch, and for each column the smallest
-// row with a non-empty C via atomicMin on top[] (step 5 needs it).  With a
+// row with a non-empty C and its value, by a 64-bit atomicMin on top[]
+// (step 5 needs them).  With a
 // stop before step 5 the requested map goes to the output instead.
 #include "common.cuh"
 
@@ -347,8 +348,12 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
     s3e.init(pinf());
     s4.init();
     int top_row[kV];
+    float top_val[kV];
 #pragma unroll
-    for (int v = 0; v < kV; ++v) top_row[v] = INT_MAX;
+    for (int v = 0; v < kV; ++v) {
+        top_row[v] = INT_MAX;
+        top_val[v] = 0.0f;
+    }
     bool tops_pending = (stop == kStopFull);
 
     const int t0 = r0 - Rh;
@@ -452,7 +457,10 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
                     bool left = false;
 #pragma unroll
                     for (int v = 0; v < kV; ++v) {
-                        if (col_out[v] && !is_empty(c[v]) && top_row[v] == INT_MAX) top_row[v] = rc;
+                        if (col_out[v] && !is_empty(c[v]) && top_row[v] == INT_MAX) {
+                            top_row[v] = rc;
+                            top_val[v] = c[v];
+                        }
                         left |= col_out[v] && top_row[v] == INT_MAX;
                     }
                     tops_pending = __any_sync(0xffffffffu, left);
@@ -490,7 +498,7 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
     if (stop == kStopFull) {
 #pragma unroll
         for (int v = 0; v < kV; ++v)
-            if (col_out[v] && top_row[v] != INT_MAX) atomicMin(&fd.top[cx + v], top_row[v]);
+            if (col_out[v] && top_row[v] != INT_MAX) atomicMin(&fd.top[cx + v], top_pack(top_row[v], top_val[v]));
     }
 }
 

@@ -190,10 +190,10 @@ __device__ __forceinline__ void load_tops(const Tile& T, const StageBParams& p, 
         int top = kNoTop;
         float v = 0.0f;
         if (p.extend_top) {
-            const int t = T.fd.top[x];
-            if (t < T.fd.H) {
-                top = t;
-                v = T.fd.c[(size_t)t * T.fd.c_pitch + x];
+            const unsigned long long t = T.fd.top[x];  // row and value in one load
+            if (t != kNoTopPacked) {
+                top = (int)(t >> 32);
+                v = __uint_as_float((unsigned)t);
             }
         }
         ctop[i] = top;
@@ -521,10 +521,10 @@ __device__ float large_fill_at(const Tile& T, const StageBParams& p, int y, int 
             int top = kNoTop;
             float tv = 0.0f;
             if (p.extend_top) {
-                const int t = T.fd.top[xx];
-                if (t < H) {
-                    top = t;
-                    tv = T.fd.c[(size_t)t * T.fd.c_pitch + xx];
+                const unsigned long long t = T.fd.top[xx];
+                if (t != kNoTopPacked) {
+                    top = (int)(t >> 32);
+                    tv = __uint_as_float((unsigned)t);
                 }
             }
 #pragma unroll 4
@@ -988,10 +988,10 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
                         int top = kNoTop;
                         float tv = 0.0f;
                         if (p.extend_top) {
-                            const int t2 = __ldg(T.fd.top + x);
-                            if (t2 < H) {
-                                top = t2;
-                                tv = __ldg(T.fd.c + (size_t)t2 * T.fd.c_pitch + x);
+                            const unsigned long long t2 = __ldg(T.fd.top + x);
+                            if (t2 != kNoTopPacked) {
+                                top = (int)(t2 >> 32);
+                                tv = __uint_as_float((unsigned)t2);
                             }
                         }
                         btop[c] = top;
