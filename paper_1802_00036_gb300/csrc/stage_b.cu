@@ -324,17 +324,20 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
             const int b = 2 * cp, x = T.x0 + b;
             const int rows = min(kGRows, H - (T.y0 + a0));
             if (x < W && rows > 0) {
-                float2 r[kGRows + 4];
+                // a window of five row-pass rows, slid down the strip (a rolled
+                // loop: the kernel's code is large and shares the instruction
+                // cache between five CTAs in different phases)
+                float2 r[5];
 #pragma unroll
-                for (int k = 0; k < kGRows + 4; ++k) r[k] = *reinterpret_cast<const float2*>(R + (a0 + k) * kRS + b);
+                for (int k = 0; k < 4; ++k) r[k] = *reinterpret_cast<const float2*>(R + (a0 + k) * kRS + b);
                 const bool two = x + 1 < W;
                 // both outputs in one 8-byte store when every row keeps them aligned
                 const bool vec = two && (T.fd.out_pitch % 2) == 0 &&
                                  (reinterpret_cast<uintptr_t>(T.fd.out + x) % sizeof(float2)) == 0;
                 float* dst = T.fd.out + (size_t)(T.y0 + a0) * T.fd.out_pitch + x;
-#pragma unroll
-                for (int k = 0; k < kGRows; ++k) {
-                    if (k >= rows) break;
+#pragma unroll 1
+                for (int k = 0; k < rows; ++k) {
+                    r[4] = *reinterpret_cast<const float2*>(R + (a0 + k + 4) * kRS + b);
                     const int mi = (a0 + k + 2) * kMS + b + 2;
                     bool e0, e1;
                     if constexpr (KEYS) {
@@ -350,25 +353,25 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
                     if constexpr (KEYS) {
                         // the integer 5 x 5 sum n over keys; the blur is n / 2^16 exactly
                         // (n < 256 * 25600 < 2^23, so 2^7 + n / 2^16 is a float)
-                        const unsigned n0 = __float_as_uint(r[k].x) + __float_as_uint(r[k + 4].x) +
-                                            4u * (__float_as_uint(r[k + 1].x) + __float_as_uint(r[k + 3].x)) +
-                                            6u * __float_as_uint(r[k + 2].x);
-                        const unsigned n1 = __float_as_uint(r[k].y) + __float_as_uint(r[k + 4].y) +
-                                            4u * (__float_as_uint(r[k + 1].y) + __float_as_uint(r[k + 3].y)) +
-                                            6u * __float_as_uint(r[k + 2].y);
+                        const unsigned n0 = __float_as_uint(r[0].x) + __float_as_uint(r[4].x) +
+                                            4u * (__float_as_uint(r[1].x) + __float_as_uint(r[3].x)) +
+                                            6u * __float_as_uint(r[2].x);
+                        const unsigned n1 = __float_as_uint(r[0].y) + __float_as_uint(r[4].y) +
+                                            4u * (__float_as_uint(r[1].y) + __float_as_uint(r[3].y)) +
+                                            6u * __float_as_uint(r[2].y);
                         acc0 = __uint_as_float(0x43000000u | n0) - 128.0f;
                         acc1 = __uint_as_float(0x43000000u | n1) - 128.0f;
                     } else {
-                        acc0 = w0 * r[k].x;
-                        acc1 = w0 * r[k].y;
-                        acc0 = fmaf(w1, r[k + 1].x, acc0);
-                        acc1 = fmaf(w1, r[k + 1].y, acc1);
-                        acc0 = fmaf(w2, r[k + 2].x, acc0);
-                        acc1 = fmaf(w2, r[k + 2].y, acc1);
-                        acc0 = fmaf(w1, r[k + 3].x, acc0);
-                        acc1 = fmaf(w1, r[k + 3].y, acc1);
-                        acc0 = fmaf(w0, r[k + 4].x, acc0);
-                        acc1 = fmaf(w0, r[k + 4].y, acc1);
+                        acc0 = w0 * r[0].x;
+                        acc1 = w0 * r[0].y;
+                        acc0 = fmaf(w1, r[1].x, acc0);
+                        acc1 = fmaf(w1, r[1].y, acc1);
+                        acc0 = fmaf(w2, r[2].x, acc0);
+                        acc1 = fmaf(w2, r[2].y, acc1);
+                        acc0 = fmaf(w1, r[3].x, acc0);
+                        acc1 = fmaf(w1, r[3].y, acc1);
+                        acc0 = fmaf(w0, r[4].x, acc0);
+                        acc1 = fmaf(w0, r[4].y, acc1);
                     }
                     float o0, o1;
                     if (p.stop == kStopBlur) {  // the blurred map itself (inverted domain)
@@ -385,6 +388,10 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
                         if (two) dst[1] = o1;
                     }
                     dst += T.fd.out_pitch;
+                    r[0] = r[1];
+                    r[1] = r[2];
+                    r[2] = r[3];
+                    r[3] = r[4];
                 }
             }
         }
