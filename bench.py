@@ -431,6 +431,23 @@ def run_next_rows(ctx, ins, outs, stream, B):
     res["metrics"] = {"frames_per_s": round(B / (ms / 1e3), 1), "ms_per_batch": round(ms, 4),
                       "achieved_GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
                       "note": "includes the synchronous copy of the results to the host"}
+    # the point-cloud mode of Section V-B (steps 5 and 6 off), on the batch, inputs rotating as in the
+    # main timed loop; and with the extension capped at 50 rows and the large fill kept
+    for name, kw in (("point_cloud_mode", dict(extend_top=False, large_fill_on=False)),
+                     ("extend_capped_50", dict(extend_rows=50))):
+        pm = dc.params(**kw)
+        for i in range(4):
+            dc.dc_complete_uniform(ctx.h, ins[i % len(ins)].data_ptr(), outs[i % len(outs)].data_ptr(), B, H, W, pm, sp)
+        reps = 50
+        ev0.record(stream)
+        for i in range(reps):
+            dc.dc_complete_uniform(ctx.h, ins[i % len(ins)].data_ptr(), outs[i % len(outs)].data_ptr(), B, H, W, pm, sp)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        gbs = BYTES_PER_PX * B * H * W / (ms / 1e3) / 1e9
+        res[name] = {"frames_per_s": round(B / (ms / 1e3), 1), "ms_per_batch": round(ms, 4),
+                     "achieved_GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
     # projection of one frame's point cloud (its returns lifted to 3D + 50k stray points)
     pts = synth.point_cloud(synth.ONE_FRAME, 4242, extra=50000)
     dpts = torch.from_numpy(pts).cuda()

@@ -132,8 +132,9 @@ dc_status dc_complete_uniform(dc_ctx* ctx, const float* in, float* out, int n,
 
 /* Same as dc_complete_uniform but `host_in` / `host_out` are HOST buffers
  * (pinned memory gives full copy bandwidth).  The batch is split into
- * chunks whose copy in, kernels (on `stream`) and copy out (on two copy
- * streams of the context) overlap; returns when the result is in host_out. */
+ * chunks whose copy in, kernels and copy out overlap, on three streams of
+ * the context (copy in, kernels, copy out); the copy in follows earlier
+ * work on `stream`.  Returns when the result is in host_out. */
 dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, int n,
                            int H, int W, const dc_params* params, void* stream);
 
@@ -141,9 +142,11 @@ dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, i
  * call only enqueues its copies and kernels and returns, so that this
  * call's copy in runs while the previous call's copy out does (the context
  * stages through two buffer sets, used by turns).  host_in must stay
- * unchanged and host_out untouched until dc_host_wait(ctx) returns; work
- * enqueued later on `stream` is ordered after the kernels, not after the
- * copy out.  Errors as dc_complete_host. */
+ * unchanged and host_out untouched until dc_host_wait(ctx) returns.  Work
+ * enqueued later on `stream` is not ordered after this call (its kernels
+ * run on a stream of the context, so that the next call's copy in need not
+ * wait for them); a later call on this context, on any stream, is.  Errors
+ * as dc_complete_host. */
 dc_status dc_complete_host_async(dc_ctx* ctx, const float* host_in, float* host_out, int n,
                                  int H, int W, const dc_params* params, void* stream);
 

@@ -46,11 +46,14 @@ struct dc_ctx {
     // two staging sets, used by turns, so that one call's copy in can run
     // while the previous call's copy out does; io_read[k] marks the end of
     // the last kernel reading io_in[k], io_drained[k] the end of the last
-    // copy out of io_out[k]
+    // copy out of io_out[k].  The kernels of host calls run on s_run, so
+    // that the caller's stream orders only the copy in: were they on it, the
+    // next call's copy in would wait for them.  Calls on other streams are
+    // ordered after them through `done` like any change of stream.
     float* io_in[2] = {};
     float* io_out[2] = {};
     size_t io_cap = 0;        // floats each
-    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaStream_t s_in = nullptr, s_out = nullptr, s_run = nullptr;
     cudaEvent_t io_ev[2 * kIoChunksMax] = {};
     cudaEvent_t io_read[2] = {}, io_drained[2] = {};
     bool io_used[2] = {};
@@ -513,17 +516,20 @@ dc_status dc_complete_uniform(dc_ctx* ctx, const float* in, float* out, int n, i
 
 namespace {
 
-// Enqueue a host-buffer call: copy in, kernels and copy out of up to four
-// chunks, through staging set ctx->io_next.  Nothing waits on the host.
+// Enqueue a host-buffer call: copy in, kernels and copy out of up to
+// `chunks` chunks, through staging set ctx->io_next.  Nothing waits on the host.  The
+// copies run on s_in and s_out, the kernels on s_run; `st` orders the copy in
+// only.
 dc_status host_enqueue(dc_ctx* ctx, const float* host_in, float* host_out, int n, int H, int W,
-                       const dc_params* params, cudaStream_t st)
+                       const dc_params* params, cudaStream_t st, int chunks)
 {
     const size_t frame = (size_t)H * W;
     dc_status s = grow(ctx, 0, 0, 0, (size_t)n * frame);
     if (s != DC_OK) return note(ctx, s);
     if (!ctx->s_in) {
         bool ok = cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking) == cudaSuccess &&
-                  cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking) == cudaSuccess;
+                  cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&ctx->s_run, cudaStreamNonBlocking) == cudaSuccess;
         for (int i = 0; ok && i < 2 * kIoChunksMax; ++i)
             ok = cudaEventCreateWithFlags(&ctx->io_ev[i], cudaEventDisableTiming) == cudaSuccess;
         for (int k = 0; ok && k < 2; ++k)
@@ -534,18 +540,22 @@ dc_status host_enqueue(dc_ctx* ctx, const float* host_in, float* host_out, int n
     const int set = ctx->io_next;
     float* io_in = ctx->io_in[set];
     float* io_out = ctx->io_out[set];
-    // up to 4 chunks of at least 8 frames: enough overlap of the copies with
-    // the kernels while each chunk still fills the GPU
-    int per = (n + 3) / 4;
+    // chunks of at least 8 frames, so that each still fills the GPU.  A
+    // single call overlaps its own copies and kernels through 4 chunks; a
+    // stream of calls overlaps one call's kernels with the copies of its
+    // neighbours, where 2 larger chunks do better (shorter kernels per frame,
+    // fewer copy starts)
+    int per = (n + chunks - 1) / chunks;
     if (per < 8) per = 8;
     if (per > n) per = n;
     // the copy in follows earlier work on `stream` (which may have produced
     // host_in) and the last kernel that read this staging set; the kernels
     // follow the last copy out of this set's output staging
+    cudaStream_t ks = ctx->s_run;
     cudaEvent_t start = ctx->io_ev[0];
     if (cudaEventRecord(start, st) != cudaSuccess || cudaStreamWaitEvent(ctx->s_in, start, 0) != cudaSuccess ||
         (ctx->io_used[set] && (cudaStreamWaitEvent(ctx->s_in, ctx->io_read[set], 0) != cudaSuccess ||
-                               cudaStreamWaitEvent(st, ctx->io_drained[set], 0) != cudaSuccess)))
+                               cudaStreamWaitEvent(ks, ctx->io_drained[set], 0) != cudaSuccess)))
         return note(ctx, DC_ERR_CUDA);
     int k = 0;
     for (int f0 = 0; f0 < n; f0 += per, ++k) {
@@ -553,15 +563,15 @@ dc_status host_enqueue(dc_ctx* ctx, const float* host_in, float* host_out, int n
         const size_t off = (size_t)f0 * frame, bytes = (size_t)m * frame * sizeof(float);
         cudaEvent_t in_done = ctx->io_ev[2 * k], run_done = ctx->io_ev[2 * k + 1];
         if (cudaMemcpyAsync(io_in + off, host_in + off, bytes, cudaMemcpyHostToDevice, ctx->s_in) != cudaSuccess ||
-            cudaEventRecord(in_done, ctx->s_in) != cudaSuccess || cudaStreamWaitEvent(st, in_done, 0) != cudaSuccess)
+            cudaEventRecord(in_done, ctx->s_in) != cudaSuccess || cudaStreamWaitEvent(ks, in_done, 0) != cudaSuccess)
             return note(ctx, DC_ERR_CUDA);
-        s = dc_complete_uniform(ctx, io_in + off, io_out + off, m, H, W, params, st);
+        s = dc_complete_uniform(ctx, io_in + off, io_out + off, m, H, W, params, ks);
         if (s != DC_OK) return s;
-        if (cudaEventRecord(run_done, st) != cudaSuccess || cudaStreamWaitEvent(ctx->s_out, run_done, 0) != cudaSuccess ||
+        if (cudaEventRecord(run_done, ks) != cudaSuccess || cudaStreamWaitEvent(ctx->s_out, run_done, 0) != cudaSuccess ||
             cudaMemcpyAsync(host_out + off, io_out + off, bytes, cudaMemcpyDeviceToHost, ctx->s_out) != cudaSuccess)
             return note(ctx, DC_ERR_CUDA);
     }
-    if (cudaEventRecord(ctx->io_read[set], st) != cudaSuccess ||
+    if (cudaEventRecord(ctx->io_read[set], ks) != cudaSuccess ||
         cudaEventRecord(ctx->io_drained[set], ctx->s_out) != cudaSuccess)
         return note(ctx, DC_ERR_CUDA);
     ctx->io_used[set] = true;
@@ -584,9 +594,9 @@ dc_status dc_complete_host(dc_ctx* ctx, const float* host_in, float* host_out, i
     if (n == 0) return DC_OK;
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
-    dc_status s = host_enqueue(ctx, host_in, host_out, n, H, W, params, st);
+    dc_status s = host_enqueue(ctx, host_in, host_out, n, H, W, params, st, 4);
     if (s != DC_OK) return s;
-    if (cudaStreamSynchronize(ctx->s_out) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+    if (cudaStreamSynchronize(ctx->s_out) != cudaSuccess || cudaStreamSynchronize(ctx->s_run) != cudaSuccess)
         return note(ctx, DC_ERR_CUDA);
     return DC_OK;
 }
@@ -597,7 +607,7 @@ dc_status dc_complete_host_async(dc_ctx* ctx, const float* host_in, float* host_
     if (!host_args_ok(ctx, host_in, host_out, n, H, W, params)) return DC_ERR_INVALID_ARG;
     if (n == 0) return DC_OK;
     DeviceGuard g(ctx->device);
-    return host_enqueue(ctx, host_in, host_out, n, H, W, params, (cudaStream_t)stream);
+    return host_enqueue(ctx, host_in, host_out, n, H, W, params, (cudaStream_t)stream, 2);
 }
 
 dc_status dc_host_wait(dc_ctx* ctx)
@@ -829,6 +839,7 @@ void dc_destroy(dc_ctx* ctx)
             if (e) cudaEventDestroy(e);
         if (ctx->s_in) cudaStreamDestroy(ctx->s_in);
         if (ctx->s_out) cudaStreamDestroy(ctx->s_out);
+        if (ctx->s_run) cudaStreamDestroy(ctx->s_run);
         if (ctx->prof_ev) {
             for (int i = 0; i < 3 * DC_PROFILE_CALLS; ++i)
                 if (ctx->prof_ev[i]) cudaEventDestroy(ctx->prof_ev[i]);

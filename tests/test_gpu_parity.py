@@ -286,6 +286,28 @@ def test_host_buffers_async_stream_of_batches(ctx):
         dc.dc_complete_host_async(ctx.h, 0, 0, 1, 352, 1216, dc.params())
 
 
+def test_host_calls_interleaved_with_device_calls(ctx):
+    # host-buffer calls run their kernels on a stream of the context; a
+    # device-buffer call on another stream in between shares the scratch and
+    # must be ordered after them, and the next host call after it
+    from paper_1802_00036_gb300 import dc
+    b0, b1, b2 = (synth.make_batch(8, synth.ONE_FRAME, config=9, first=10 * i) for i in range(3))
+    h0, h2 = torch.from_numpy(b0).pin_memory(), torch.from_numpy(b2).pin_memory()
+    o0, o2 = torch.full_like(h0, -1.0).pin_memory(), torch.full_like(h2, -1.0).pin_memory()
+    x1 = torch.from_numpy(b1).cuda()
+    y1 = torch.full_like(x1, -1.0)
+    other = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    dc.dc_complete_host_async(ctx.h, h0.data_ptr(), o0.data_ptr(), 8, 352, 1216, dc.params())
+    dc.dc_complete_uniform(ctx.h, x1.data_ptr(), y1.data_ptr(), 8, 352, 1216, dc.params(), other.cuda_stream)
+    dc.dc_complete_host_async(ctx.h, h2.data_ptr(), o2.data_ptr(), 8, 352, 1216, dc.params(),
+                              other.cuda_stream)
+    dc.dc_host_wait(ctx.h)
+    other.synchronize()
+    for b, got in ((b0, o0.numpy()), (b1, y1.cpu().numpy()), (b2, o2.numpy())):
+        assert np.array_equal(got.view(np.uint32), gpu_run(ctx, b).view(np.uint32))
+
+
 def test_results_do_not_depend_on_tuning(ctx):
     from paper_1802_00036_gb300 import dc
     frames = synth.make_batch(6, synth.UNIFORM_375, config=4)
