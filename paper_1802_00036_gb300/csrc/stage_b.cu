@@ -213,6 +213,30 @@ __device__ __forceinline__ float extended(const Tile& T, const StageBParams& p, 
     return above_top(p, y, top) ? topval : T.fd.c[(size_t)y * T.fd.c_pitch + x];
 }
 
+// Whether E (C after step 5) is empty in frame column x from row 0 to row
+// `last`: C is empty above the column's top row (its first non-empty one),
+// and step 5 writes nothing there when it is off or capped short of `last`.
+// Reads the top itself: the tops of load_tops are cleared when step 5 is off.
+__device__ __forceinline__ bool column_empty_to(const Tile& T, const StageBParams& p, int x, int last)
+{
+    const unsigned long long t = __ldg(T.fd.top + x);
+    if (t == kNoTopPacked) return true;
+    const int top = (int)(t >> 32);
+    if (top <= last) return false;
+    return !p.extend_top || (p.extend_rows >= 0 && last < top - p.extend_rows);
+}
+
+// The output of a tile whose median is empty everywhere: 0 (step 8 writes 0
+// where the median is empty, whatever the blur).
+__device__ void store_zero_tile(const Tile& T)
+{
+    for (int i = threadIdx.x; i < kTBH * kTBW; i += kThreadsB) {
+        const int a = i / kTBW, b = i - a * kTBW;
+        const int y = T.y0 + a, x = T.x0 + b;
+        if (y < T.fd.H && x < T.fd.W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = 0.0f;
+    }
+}
+
 // The median output region M (kMR x kMS): 16-bit keys (Mk) after the packed
 // median, floats (Mf) otherwise.  These read one value as a float.
 template <bool KEYS>
@@ -868,8 +892,16 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
         const bool const_tile = __syncthreads_and(
             p.extend_top && p.extend_rows < 0 &&
             (tid >= kEC || (ctop[tid] != kNoTop && ctop[tid] > T.y0 - 4 + kER - 1)));
+        // without step 6, a region empty in every column down to its last row
+        // has an empty median everywhere (every window holds only empty
+        // values): the tile's output is 0
+        const bool void_tile = !p.large_fill_on && p.stop == kStopFull &&
+                               __syncthreads_and(tid >= kEC || column_empty_to(T, p, clampi(T.x0 - 4 + tid, W),
+                                                                               min(H - 1, T.y0 - 4 + kER - 1)));
         if (const_tile) {
             constant_tile_store(T, p, cval, scratch);
+        } else if (void_tile) {
+            store_zero_tile(T);
         } else {
         // step 5 in place, empty pixels, packed keys: row pairs (kp, kp + kHalf)
         // of one column chunk per thread
@@ -1086,7 +1118,17 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
     }
 }
 
-// Phase 2: tiles from the worklist, with step 6.
+// Row stride of the wide region in phase 2: 16-byte rows with room for the
+// shift of the region's first column down to a 16-byte boundary.
+__host__ __device__ constexpr int fill_row_stride(int GC) { return (GC + 6) / 4 * 4; }
+// Floats of RM: GR rows of GC + 1 (an odd stride), rounded to 16 bytes.
+__host__ __device__ constexpr int fill_rm_floats(int GR, int GC) { return (GR * (GC + 1) + 3) / 4 * 4; }
+
+// Phase 2: tiles from the worklist, with step 6.  Shared memory: G (E over
+// the wide region, rows of GS floats, 16-byte aligned, frame column gx at
+// offset sh; then the window maxima D), RM (column maxima S; the median
+// output once they are used), F (the step-6 output over tile + 4) and the
+// region's column tops.
 __global__ void __launch_bounds__(kThreadsB, 1)
 stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
              const int* __restrict__ worklist)
@@ -1094,52 +1136,147 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
     extern __shared__ __align__(16) float dyn[];
     const int Rl = p.large_radius;
     const int GR = kER + 2 * Rl, GC = kEC + 2 * Rl;  // the wide region
-    float* G = dyn;                       // E over the wide region, out of frame -inf
-    float* RM = G + GR * GC;              // row maxima
-    float* F = RM + GR * GC;              // F over tile + 4, border replicated
-    float* M = F + kER * kES;
-    int* ctop = reinterpret_cast<int*>(M + kMR * kMS);
+    const int GS = fill_row_stride(GC);
+    float* G = dyn;
+    float* RM = G + GR * GS;
+    float* F = RM + fill_rm_floats(GR, GC);
+    float* M = RM;
+    int* ctop = reinterpret_cast<int*>(F + kER * kES);
     float* cval = reinterpret_cast<float*>(ctop + GC);
     float* R = G;
 
     const int count = worklist[0];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int w = blockIdx.x; w < count; w += gridDim.x) {
         __syncthreads();
         const Tile T = tile_of(frames, n_frames, worklist[3 + w], p.row_stride);
         const int H = T.fd.H, W = T.fd.W;
-        const int gy = T.y0 - 4 - Rl, gx = T.x0 - 4 - Rl;  // frame position of G(0, 0)
+        const int gy = T.y0 - 4 - Rl, gx = T.x0 - 4 - Rl;  // frame position of the wide region's (0, 0)
         load_tops(T, p, gx, GC, ctop, cval);
-        __syncthreads();
-        for (int i = tid; i < GR * GC; i += kThreadsB) {
-            const int k = i / GC, l = i - k * GC;
-            const int y = gy + k, x = gx + l;
-            float e = ninf();
-            if (y >= 0 && y < H && x >= 0 && x < W) e = extended(T, p, y, x, ctop[l], cval[l]);
-            G[i] = e;
+        // a wide region empty in every column: every window of step 6 holds
+        // only empty values, so does the median, and the output is 0
+        if (p.stop == kStopFull) {
+            bool empty_cols = true;
+            const int last = min(H - 1, gy + GR - 1);
+            for (int l = tid; l < GC; l += kThreadsB) {
+                const int x = gx + l;
+                if (x >= 0 && x < W) empty_cols = empty_cols && column_empty_to(T, p, x, last);
+            }
+            if (__syncthreads_and(empty_cols)) {
+                store_zero_tile(T);
+                continue;
+            }
         }
-        __syncthreads();
-        // row maxima over 2 Rl + 1 columns, for columns [Rl, GC - Rl)
-        for (int i = tid; i < GR * GC; i += kThreadsB) {
-            const int k = i / GC, l = i - k * GC;
-            if (l < Rl || l >= GC - Rl) continue;
-            float m = ninf();
-            for (int d = -Rl; d <= Rl; ++d) m = fmaxf(m, G[i + d]);
-            RM[i] = m;
+        // E over the wide region: C by 16-byte asynchronous copies (chunk j
+        // of a row is frame columns gxa + 4 j .. + 3), the few chunks across
+        // the frame's left or right edge by plain loads, -inf outside it
+        const int gxa = (gx >> 2) << 2, sh = gx - gxa;
+        const int nch = (sh + GC + 3) >> 2;
+        for (int k = warp; k < GR; k += kThreadsB / 32) {
+            const int y = gy + k;
+            float* grow = G + k * GS;
+            if (y < 0 || y >= H) {
+                for (int j = lane; j < GS; j += 32) grow[j] = ninf();
+                continue;
+            }
+            const float* crow = T.fd.c + (size_t)y * T.fd.c_pitch;
+            for (int j = lane; j < nch; j += 32) {
+                const int x = gxa + 4 * j;
+                if (x >= 0 && x + 3 < W) {
+                    cp_async16(grow + 4 * j, crow + x);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        grow[4 * j + e] = (x + e >= 0 && x + e < W) ? crow[x + e] : ninf();
+                }
+            }
         }
+        cp_async_commit();
+        cp_async_wait_all();
         __syncthreads();
-        // column maxima and the fill of empty pixels, tile + 4, replicated border
+        // step 5: the rows above each in-frame column's top (within the cap)
+        if (p.extend_top) {
+            for (int l = tid; l < GC; l += kThreadsB) {
+                const int top = ctop[l], x = gx + l;
+                if (top == kNoTop || x < 0 || x >= W) continue;
+                const int klo = max(-gy, p.extend_rows < 0 ? 0 : top - p.extend_rows - gy);
+                const int khi = min(GR, top - gy);
+                const float v = cval[l];
+                for (int k = max(0, klo); k < khi; ++k) G[k * GS + sh + l] = v;
+            }
+            __syncthreads();
+        }
+        // E over tile + 4, border replicated, kept in F: G is scratch below
         for (int i = tid; i < kER * kEC; i += kThreadsB) {
             const int k = i / kEC, l = i - k * kEC;
             const int y = clampi(T.y0 - 4 + k, H), x = clampi(T.x0 - 4 + l, W);
-            const int gk = y - gy, gl = x - gx;
-            float e = G[gk * GC + gl];
-            if (is_empty(e)) {
-                float m = e;
-                for (int d = -Rl; d <= Rl; ++d) m = fmaxf(m, RM[(gk + d) * GC + gl]);
-                e = m;
+            F[k * kES + l] = G[(y - gy) * GS + sh + (x - gx)];
+        }
+        // The window maxima, separable, by van Herk's method: over blocks of
+        // wl = 2 Rl + 1 consecutive elements, suffix maxima (backward scan)
+        // and prefix maxima (forward scan); the window [j - 2 Rl, j] is the
+        // end of one block and the start of the next, so its maximum is the
+        // suffix maximum at j - 2 Rl with the prefix maximum at j, and goes
+        // where that suffix maximum was (no longer needed).  About three
+        // operations per element whatever the width.  Columns first, one
+        // thread per column (neighbouring threads, neighbouring banks), then
+        // the kER rows the tile needs, over odd row strides.
+        const int wl = 2 * Rl + 1, SS = GC + 1;
+        // columns: S[r][c] = max G[r .. r + 2 Rl][c] (centre row r + Rl), in RM
+        for (int c = tid; c < GC; c += kThreadsB) {
+            const float* __restrict__ gc = G + sh + c;
+            float* __restrict__ sc = RM + c;
+            int q = (GR - 1) % wl;  // position within its block
+            float h = ninf();
+#pragma unroll 4
+            for (int r = GR - 1; r >= 0; --r) {
+                const float v = gc[r * GS];
+                h = (q == wl - 1 || r == GR - 1) ? v : fmaxf(h, v);
+                sc[r * SS] = h;
+                q = (q == 0) ? wl - 1 : q - 1;
             }
-            F[k * kES + l] = e;
+            float pm = ninf();
+            q = 0;
+#pragma unroll 4
+            for (int r = 0; r < GR; ++r) {
+                const float v = gc[r * GS];
+                pm = (q == 0) ? v : fmaxf(pm, v);
+                if (r >= 2 * Rl) sc[(r - 2 * Rl) * SS] = fmaxf(sc[(r - 2 * Rl) * SS], pm);
+                q = (q == wl - 1) ? 0 : q + 1;
+            }
+        }
+        __syncthreads();
+        // rows: D[k][c] = max S[k][c .. c + 2 Rl], the maximum over the window
+        // centred at (k + Rl, c + Rl) of G, for k < kER, c < kEC; D in G
+        for (int k = tid; k < kER; k += kThreadsB) {
+            const float* __restrict__ sr = RM + k * SS;
+            float* __restrict__ dr = G + k * SS;
+            int q = (GC - 1) % wl;
+            float h = ninf();
+#pragma unroll 4
+            for (int l = GC - 1; l >= 0; --l) {
+                const float v = sr[l];
+                h = (q == wl - 1 || l == GC - 1) ? v : fmaxf(h, v);
+                dr[l] = h;
+                q = (q == 0) ? wl - 1 : q - 1;
+            }
+            float pm = ninf();
+            q = 0;
+#pragma unroll 4
+            for (int l = 0; l < GC; ++l) {
+                pm = (q == 0) ? sr[l] : fmaxf(pm, sr[l]);
+                if (l >= 2 * Rl) dr[l - 2 * Rl] = fmaxf(dr[l - 2 * Rl], pm);
+                q = (q == wl - 1) ? 0 : q + 1;
+            }
+        }
+        __syncthreads();
+        // the fill of empty pixels, tile + 4, replicated border
+        for (int i = tid; i < kER * kEC; i += kThreadsB) {
+            const int k = i / kEC, l = i - k * kEC;
+            const int y = clampi(T.y0 - 4 + k, H), x = clampi(T.x0 - 4 + l, W);
+            const int dk = y - gy - Rl, dl = x - gx - Rl;  // the window's centre in D
+            const float e = F[k * kES + l];
+            if (is_empty(e)) F[k * kES + l] = fmaxf(e, G[dk * SS + dl]);
         }
         __syncthreads();
         if (p.stop == kStopFillLarge) {
@@ -1158,8 +1295,8 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
 
 size_t stage_b_fill_smem_bytes(int large_radius)
 {
-    const size_t GR = kER + 2 * large_radius, GC = kEC + 2 * large_radius;
-    return sizeof(float) * (2 * GR * GC + kER * kES + kMR * kMS + 2 * GC);
+    const int GR = kER + 2 * large_radius, GC = kEC + 2 * large_radius;
+    return sizeof(float) * ((size_t)GR * fill_row_stride(GC) + fill_rm_floats(GR, GC) + kER * kES + 2 * GC);
 }
 
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,

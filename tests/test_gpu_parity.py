@@ -153,6 +153,29 @@ def test_point_cloud_variants(ctx, variant):
                 oracle.complete(f, stop_after=stop, **variant), stop, str(variant))
 
 
+@pytest.mark.parametrize("variant", [dict(extend_top=False, large_fill_on=False),
+                                     dict(extend_rows=5, large_fill_on=False),
+                                     dict(extend_top=False), dict(extend_rows=50),
+                                     dict(extend_rows=20, large_fill=51)])
+@pytest.mark.parametrize("lone_point", [False, True])
+def test_empty_regions(ctx, variant, lone_point):
+    # full-size frames whose upper third holds no return: without step 5 (or
+    # with it capped) whole tiles, or the wide windows of step 6, see only
+    # empty values; a lone return near the top makes the tiles around its
+    # column differ from their neighbours
+    frames = synth.make_batch(2, synth.ONE_FRAME, config=11)
+    if lone_point:
+        frames[0, 8, 610] = 37.5
+        frames[1, 70, 3] = 12.25
+    got = gpu_run(ctx, frames, **variant)
+    for stop in ("fill_large", "median", "full"):
+        if stop != "full":
+            got_s = gpu_run(ctx, frames, stop_after=stop, **variant)
+        for i in range(2):
+            compare(got[i] if stop == "full" else got_s[i],
+                    oracle.complete(frames[i], stop_after=stop, **variant), stop, f"{variant} frame {i}")
+
+
 @pytest.mark.parametrize("hw", [(1, 1), (1, 37), (41, 1), (2, 2), (3, 5), (7, 64), (33, 65),
                                 (64, 128), (65, 129), (5, 300)])
 def test_edge_shapes(ctx, hw):
