@@ -828,7 +828,10 @@ static_assert(5 * ((kMainSmemFloats * 4 + kMainStaticSmem + 127) / 128 * 128 + 1
 // unclaimed tile from a counter.  One region buffer and 16-bit median output
 // (45 KB of shared memory in all) let five CTAs share an SM: while one waits
 // for its region (cp.async) the others compute, which hides the copy better
-// than a second buffer would (that costs CTAs per SM).
+// than a second buffer would (that costs CTAs per SM).  kFill: step 6 on
+// (one instantiation per setting, so that neither carries the other's code:
+// the kernel's speed is sensitive to its instruction footprint).
+template <bool kFill>
 __global__ void __launch_bounds__(kThreadsB, 5)
 stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles, StageBParams p,
              int* __restrict__ worklist, const __grid_constant__ CUtensorMap cmap, int* __restrict__ err)
@@ -895,7 +898,7 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
         // without step 6, a region empty in every column down to its last row
         // has an empty median everywhere (every window holds only empty
         // values): the tile's output is 0
-        const bool void_tile = !p.large_fill_on && p.stop == kStopFull &&
+        const bool void_tile = !kFill && p.stop == kStopFull &&
                                __syncthreads_and(tid >= kEC || column_empty_to(T, p, clampi(T.x0 - 4 + tid, W),
                                                                                min(H - 1, T.y0 - 4 + kER - 1)));
         if (const_tile) {
@@ -950,7 +953,7 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
                             if (e < ncol) em |= (is_empty(v[e]) ? 1u : 0u) << e;
                     // rows kHalf .. kPR - 1 appear in both halves: count them once
                     const bool counted = (h == 0) || (kp >= kPR - kHalf);
-                    if (em && counted && p.large_fill_on) {
+                    if (em && counted && kFill) {
                         const int slot0 = atomicAdd(ecount, __popc(em));
                         int slot = slot0;
 #pragma unroll
@@ -970,7 +973,7 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
             }
         }
         __syncthreads();
-        const int n_empty = *ecount;
+        const int n_empty = kFill ? *ecount : 0;  // no empties are counted without step 6
 
         auto store_tile = [&](const float* buf) {
             for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
@@ -1311,7 +1314,9 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
         cudaError_t e = cudaFuncSetAttribute(stage_b_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)stage_b_fill_smem_bytes(kMaxLargeFill / 2));
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(stage_b_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)main_smem);
+        e = cudaFuncSetAttribute(stage_b_main<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)main_smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(stage_b_main<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)main_smem);
         if (e != cudaSuccess) return e;
         configured_dev = dev;
     }
@@ -1323,7 +1328,12 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
     if (p.tma && cmap) map = *cmap;
     StageBParams q = p;
     q.tma = (p.tma && cmap) ? 1 : 0;
-    stage_b_main<<<main_grid, kThreadsB, main_smem, stream>>>(d_frames, n_frames, total_tiles, q, worklist, map, err);
+    if (p.large_fill_on)
+        stage_b_main<true><<<main_grid, kThreadsB, main_smem, stream>>>(d_frames, n_frames, total_tiles, q, worklist,
+                                                                       map, err);
+    else
+        stage_b_main<false><<<main_grid, kThreadsB, main_smem, stream>>>(d_frames, n_frames, total_tiles, q, worklist,
+                                                                        map, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !p.large_fill_on || p.stop == kStopExtend) return e;
     int grid = 2 * sm_count;
