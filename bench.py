@@ -66,9 +66,9 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def measured_traffic(stage):
-    """DRAM bytes per launch of a stage from the committed ncu summary, or
-    None if the kernel source changed since that capture."""
+def measured_counters(stage):
+    """A stage's ncu counters per launch from the committed summary, or None
+    if the kernel source changed since that capture."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
@@ -76,9 +76,35 @@ def measured_traffic(stage):
         with open(os.path.join(ROOT, entry["source"]), "rb") as fh:
             if hashlib.sha256(fh.read()).hexdigest() != entry["source_sha256"]:
                 return None
-        return int(entry["dram_read_bytes"]) + int(entry["dram_write_bytes"])
+        return entry
     except Exception:
         return None
+
+
+def measured_traffic(stage):
+    """DRAM bytes per launch of a stage (ncu), or None."""
+    entry = measured_counters(stage)
+    if entry is None:
+        return None
+    return int(entry["dram_read_bytes"]) + int(entry["dram_write_bytes"])
+
+
+# The ALU pipe (min/max, integer and logic operations) of one SM issues 2
+# warp-instructions per clock (4 sub-partitions x 16 lanes); 152 SMs at 2070 MHz.
+ALU_PEAK_G_WARP_INST = 152 * 2 * 2.070
+
+
+def alu_roofline(stage, launch_ms):
+    """The second bound: the kernel's ALU-pipe warp instructions per launch
+    (ncu count of the same workload) over its CUDA-event launch time."""
+    entry = measured_counters(stage)
+    if entry is None or "alu_pipe_warp_insts" not in entry or not launch_ms:
+        return None
+    achieved = float(entry["alu_pipe_warp_insts"]) / (launch_ms / 1e3) / 1e9
+    return {"bound": "alu", "achieved": round(achieved, 1), "peak": round(ALU_PEAK_G_WARP_INST, 1),
+            "unit": "G warp-instructions/s (ALU pipe)", "frac": round(achieved / ALU_PEAK_G_WARP_INST, 4),
+            "basis": "executed ALU-pipe instructions per launch (ncu, profiles/traffic.json) over the "
+                     "CUDA-event launch time; peak 152 SMs x 2 per clock x 2070 MHz"}
 
 
 def dist_setup(n_gpus):
@@ -382,6 +408,7 @@ def run_gpu(args, world, rank, local):
             "bytes_per_px": BYTES_PER_PX,
             "path_achieved": round(BYTES_PER_PX * px * fps / 1e9, 1),
             "path_frac": round(BYTES_PER_PX * px * fps / 1e9 / hbm, 4),
+            "alu": alu_roofline(dom, dom_ms) if B == BATCH else None,
         },
         "kernels_ms": {"stage_a": round(a_ms, 4) if a_ms else None, "stage_b": round(b_ms, 4) if b_ms else None,
                        "calls_timed": len(ktimes)},
