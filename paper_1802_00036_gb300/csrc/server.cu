@@ -2,8 +2,9 @@
 //
 // The paper has no serving system; this serves the chain to several sensors
 // whose frames arrive one at a time.  One worker thread owns all device work:
-//   admit     a submitted frame takes a free device slot (input + output frame
-//             of the largest size, rows at that pitch) and is copied in on the
+//   admit     a submitted frame takes a free device slot (room for an input
+//             and an output frame of the largest size; the frame lies dense in
+//             it, so each copy is contiguous) and is copied in on the
 //             upload stream; with no free slot it waits (back-pressure);
 //   batch     the uploaded frames form a batch when max_batch are ready or the
 //             oldest has waited deadline_us since its submission, and the batch
@@ -113,10 +114,10 @@ void dc_server::run()
             waiting.pop_front();
             r.slot = free_slots.back();
             free_slots.pop_back();
+            // a frame lies dense in its slot (row pitch W): one contiguous copy
             float* dst = d_in + (size_t)r.slot * slot_floats;
-            if (cudaMemcpy2DAsync(dst, (size_t)Wmax * sizeof(float), r.in, (size_t)r.W * sizeof(float),
-                                  (size_t)r.W * sizeof(float), (size_t)r.H, cudaMemcpyHostToDevice,
-                                  upload) != cudaSuccess ||
+            if (cudaMemcpyAsync(dst, r.in, (size_t)r.H * r.W * sizeof(float), cudaMemcpyHostToDevice,
+                                upload) != cudaSuccess ||
                 cudaEventRecord(up_ev[up_next], upload) != cudaSuccess) {
                 cudaGetLastError();
                 fail(DC_ERR_CUDA);
@@ -164,7 +165,7 @@ void dc_server::run()
             for (int i = 0; i < n; ++i) {
                 const Req& r = l.batch[(size_t)i];
                 frames[(size_t)i] = dc_frame{d_in + (size_t)r.slot * slot_floats, d_out + (size_t)r.slot * slot_floats,
-                                             r.H, r.W, Wmax, Wmax};
+                                             r.H, r.W, r.W, r.W};
                 last_ev = r.ev;  // uploads are in order: the last one covers the batch
             }
             dc_status s = DC_OK;
@@ -172,9 +173,8 @@ void dc_server::run()
             if (s == DC_OK) s = dc_complete(l.ctx, frames.data(), n, &params, l.st);
             for (int i = 0; s == DC_OK && i < n; ++i) {
                 const Req& r = l.batch[(size_t)i];
-                if (cudaMemcpy2DAsync(r.out, (size_t)r.W * sizeof(float), d_out + (size_t)r.slot * slot_floats,
-                                      (size_t)Wmax * sizeof(float), (size_t)r.W * sizeof(float), (size_t)r.H,
-                                      cudaMemcpyDeviceToHost, l.st) != cudaSuccess)
+                if (cudaMemcpyAsync(r.out, d_out + (size_t)r.slot * slot_floats, (size_t)r.H * r.W * sizeof(float),
+                                    cudaMemcpyDeviceToHost, l.st) != cudaSuccess)
                     s = DC_ERR_CUDA;
             }
             if (s == DC_OK && cudaEventRecord(l.done, l.st) != cudaSuccess) s = DC_ERR_CUDA;

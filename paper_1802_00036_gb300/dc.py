@@ -217,10 +217,15 @@ def dc_server_submit(srv, host_in: int, host_out: int, H: int, W: int, tag: int)
            "dc_server_submit")
 
 
-def dc_server_poll(srv, max_n: int = 4096):
-    """[(tag, latency_ms), ...] of the frames done since the last poll."""
-    tags = (ctypes.c_ulonglong * max_n)()
-    lat = (ctypes.c_double * max_n)()
+def poll_buffers(max_n: int = 4096):
+    """Tag and latency arrays for dc_server_poll, to be reused across polls."""
+    return (ctypes.c_ulonglong * max_n)(), (ctypes.c_double * max_n)()
+
+
+def dc_server_poll(srv, max_n: int = 4096, buffers=None):
+    """[(tag, latency_ms), ...] of the frames done since the last poll (at
+    most max_n; `buffers` from poll_buffers(max_n) saves allocating them)."""
+    tags, lat = buffers if buffers is not None else poll_buffers(max_n)
     n = ctypes.c_int()
     _check(load().dc_server_poll(srv, tags, lat, max_n, ctypes.byref(n)), "dc_server_poll")
     return [(tags[i], lat[i]) for i in range(n.value)]

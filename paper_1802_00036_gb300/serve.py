@@ -285,12 +285,13 @@ class NativeServer:
         self.max_hw = max_hw
         self.h = dc.dc_server_create(device, max_hw[0], max_hw[1], int(budget_bytes), int(round(deadline_ms * 1e3)),
                                      int(max_batch), int(lanes), params if params is not None else dc.params())
+        self._poll = dc.poll_buffers(4096)
 
     def submit(self, host_in: int, host_out: int, H: int, W: int, tag: int) -> None:
         dc.dc_server_submit(self.h, host_in, host_out, H, W, tag)
 
     def poll(self):
-        return dc.dc_server_poll(self.h)
+        return dc.dc_server_poll(self.h, 4096, self._poll)
 
     def stats(self) -> dict:
         return dc.dc_server_get_stats(self.h)
@@ -313,6 +314,8 @@ def drive_native(server: NativeServer, frames_by_sensor, rate_hz: float, seconds
     times, ids = poisson_schedule(rate_hz, len(frames_by_sensor), seconds, seed)
     Hm, Wm = server.max_hw
     outs = [torch.empty((Hm, Wm)).pin_memory() for _ in range(outstanding)]
+    out_ptrs = [o.data_ptr() for o in outs]
+    pools = [[(f.data_ptr(), f.shape[0], f.shape[1]) for f in pool] for pool in frames_by_sensor]
     free = list(range(outstanding))
     in_flight = {}
     lat = []
@@ -341,13 +344,12 @@ def drive_native(server: NativeServer, frames_by_sensor, rate_hz: float, seconds
                 break
             if not collect() and due - now > 1e-4:
                 time.sleep(min(due - now, 1e-3) * 0.5)
-        pool = frames_by_sensor[s]
-        f = pool[counters[s] % len(pool)]
+        pool = pools[s]
+        ptr, H, W = pool[counters[s] % len(pool)]
         counters[s] += 1
         b = free.pop()
-        H, W = f.shape
         in_flight[k] = (b, due, time.perf_counter())
-        server.submit(f.data_ptr(), outs[b].data_ptr(), H, W, k)
+        server.submit(ptr, out_ptrs[b], H, W, k)
     while in_flight:
         if not collect():
             time.sleep(5e-5)

@@ -246,6 +246,28 @@ def test_batched_375x1242_sampled_and_batch_independent(ctx):
             assert np.array_equal(alone.view(np.uint32), got[i].view(np.uint32)), i
 
 
+def test_bench_workload_sampled(ctx):
+    # the benchmark's own batch: 64 frames of 352x1216 (its seeds), one call
+    # in its launch shape (16 stage-A warps per SM, 5 stage-B CTAs per SM,
+    # step-6 threshold 160; one shape, so the region arrives by tensor copy);
+    # the depths are 1/256 m steps, so sampled frames equal the oracle bit for
+    # bit through the blur, and every eighth frame equals its own run alone
+    from paper_1802_00036_gb300 import dc
+    frames = synth.make_batch(64, synth.ONE_FRAME, config=0)
+    dc.dc_set_tuning(ctx.h, 16, 5, 160)
+    try:
+        got = gpu_run(ctx, frames)
+        for i in (0, 21, 42, 63):
+            want = oracle.complete(frames[i])
+            bad = np.argwhere(got[i].view(np.uint32) != want.view(np.uint32))
+            assert len(bad) == 0, f"frame {i}: {len(bad)} mismatches, first {bad[:5].tolist()}"
+        for i in range(0, 64, 8):
+            alone = gpu_run(ctx, frames[i:i + 1])[0]
+            assert np.array_equal(alone.view(np.uint32), got[i].view(np.uint32)), i
+    finally:
+        dc.dc_set_tuning(ctx.h, 8, 5, 160)
+
+
 def test_bilateral_full_size(ctx):
     f = synth.make_frame(synth.UNIFORM_375, synth.frame_seed(1, 3))
     compare(gpu_run(ctx, f[None], blur="bilateral")[0], oracle.complete(f, blur="bilateral"),
