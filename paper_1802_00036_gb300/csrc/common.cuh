@@ -85,6 +85,33 @@ __device__ __forceinline__ bool is_empty(float v) { return !(v >= kEmptyBelow); 
 __device__ __forceinline__ float ninf() { return __int_as_float(0xff800000); }
 __device__ __forceinline__ float pinf() { return __int_as_float(0x7f800000); }
 
+// Programmatic dependent launch.  The stage kernels are launched so that the
+// GPU may start them while the previous kernel of the stream is finishing;
+// each first waits until that kernel has completed and its writes are
+// visible (without the launch attribute the wait returns at once).  The
+// kernel before lets them launch once all of its blocks have started: its
+// grids are persistent (every block resident from the start), so the next
+// kernel's blocks only take the room its finished blocks leave.
+__device__ __forceinline__ void wait_previous_kernel() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_next_kernel() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+inline cudaError_t launch_after_previous(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                         cudaStream_t stream, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Frame owning flat tile t: the last f with base(f) <= t.
 template <bool kStageA>
 __device__ __forceinline__ int find_frame(const FrameDesc* __restrict__ d, int n, int t)

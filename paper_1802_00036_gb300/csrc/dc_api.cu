@@ -196,6 +196,7 @@ template <int K>
 __global__ void table_put(const __grid_constant__ TableChunk<K> src, FrameDesc* __restrict__ dst, int n,
                           unsigned long long* __restrict__ top, size_t top_ints, int* __restrict__ counter)
 {
+    allow_next_kernel();  // stage A may launch; it waits for this kernel's writes
     const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     if (counter && tid == 0) *counter = 0;

@@ -63,6 +63,7 @@ __global__ void noalloc_prepare(FrameDesc* table, unsigned long long* top, float
                                 int n, int H, int W, int c_pitch, int tiles_x_a, int tiles_a, int band_a,
                                 int tiles_x_b, int tiles_b, int top_ints, int* counter)
 {
+    allow_next_kernel();  // stage A may launch; it waits for this kernel's writes
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     if (tid == 0) *counter = 0;  // stage A's unit counter

@@ -511,6 +511,8 @@ __global__ void __launch_bounds__(kThreadsA, 12)
 stage_a_stream(const FrameDesc* __restrict__ frames, int n_frames, int total_units, int stop,
                int* __restrict__ work, int band_stride)
 {
+    wait_previous_kernel();  // the frame table, the reset tops and counter
+    allow_next_kernel();
     const int lane = threadIdx.x & 31;
     int unit = blockIdx.x * (kThreadsA / 32) + (threadIdx.x >> 5);
     if (unit == 0 && lane < 2) work[lane] = 0;  // step-6 count, stage-B tile counter
@@ -531,8 +533,8 @@ cudaError_t launch_shape(const FrameDesc* d_frames, int n_frames, int total_unit
     int grid = (total_units + per_block - 1) / per_block;
     if (grid > 12 * sm_count) grid = 12 * sm_count;  // twelve one-warp CTAs per SM (registers), persistent
     if (grid < 1) return cudaSuccess;
-    stage_a_stream<S><<<grid, kThreadsA, 0, stream>>>(d_frames, n_frames, total_units, stop, work, band_stride);
-    return cudaGetLastError();
+    return launch_after_previous(stage_a_stream<S>, dim3(grid), dim3(kThreadsA), 0, stream, d_frames, n_frames,
+                                 total_units, stop, work, band_stride);
 }
 
 }  // namespace

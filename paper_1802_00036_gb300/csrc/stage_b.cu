@@ -836,6 +836,8 @@ __global__ void __launch_bounds__(kThreadsB, 5)
 stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles, StageBParams p,
              int* __restrict__ worklist, const __grid_constant__ CUtensorMap cmap, int* __restrict__ err)
 {
+    wait_previous_kernel();  // C, the tops and counters of stage A
+    allow_next_kernel();
     extern __shared__ __align__(128) float smem[];  // the tensor copy wants 128-byte alignment
     float* Ebuf = smem;                                                      // the region
     unsigned* K = reinterpret_cast<unsigned*>(smem + kER * kES);             // packed keys
@@ -1136,6 +1138,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
 stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
              const int* __restrict__ worklist)
 {
+    wait_previous_kernel();  // the worklist and outputs of the main pass
     extern __shared__ __align__(16) float dyn[];
     const int Rl = p.large_radius;
     const int GR = kER + 2 * Rl, GC = kEC + 2 * Rl;  // the wide region
@@ -1328,19 +1331,14 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
     if (p.tma && cmap) map = *cmap;
     StageBParams q = p;
     q.tma = (p.tma && cmap) ? 1 : 0;
-    if (p.large_fill_on)
-        stage_b_main<true><<<main_grid, kThreadsB, main_smem, stream>>>(d_frames, n_frames, total_tiles, q, worklist,
-                                                                       map, err);
-    else
-        stage_b_main<false><<<main_grid, kThreadsB, main_smem, stream>>>(d_frames, n_frames, total_tiles, q, worklist,
-                                                                        map, err);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_after_previous(p.large_fill_on ? stage_b_main<true> : stage_b_main<false>, dim3(main_grid),
+                                          dim3(kThreadsB), main_smem, stream, d_frames, n_frames, total_tiles, q,
+                                          worklist, map, err);
     if (e != cudaSuccess || !p.large_fill_on || p.stop == kStopExtend) return e;
     int grid = 2 * sm_count;
     if (grid > total_tiles) grid = total_tiles;
-    stage_b_fill<<<grid, kThreadsB, stage_b_fill_smem_bytes(p.large_radius), stream>>>(d_frames, n_frames, p,
-                                                                                       worklist);
-    return cudaGetLastError();
+    return launch_after_previous(stage_b_fill, dim3(grid), dim3(kThreadsB), stage_b_fill_smem_bytes(p.large_radius),
+                                 stream, d_frames, n_frames, p, static_cast<const int*>(worklist));
 }
 
 }  // namespace dcgb
