@@ -211,11 +211,15 @@ dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, in
 /* Number of kernel launches the last dc_complete* call queued. */
 int dc_last_launch_count(const dc_ctx* ctx);
 
-/* Per-kernel timing.  With profiling on, every later call records CUDA
- * events around each of its kernels on the call's stream (a ring of the last
- * DC_PROFILE_CALLS calls).  Turning it on allocates the events. */
+/* Per-kernel timing.  With every >= 1, one later call in `every` (the
+ * first, then each every-th) records CUDA events around each of its kernels
+ * on the call's stream (a ring of the last DC_PROFILE_CALLS profiled calls);
+ * 0 turns it off.  Each call restarts the ring.  An event between two
+ * kernels keeps the second from being launched while the first finishes, so
+ * profiling one call in several leaves the others' overlap intact.  Turning
+ * it on allocates the events; every < 0 is DC_ERR_INVALID_ARG. */
 #define DC_PROFILE_CALLS 4096
-dc_status dc_set_profiling(dc_ctx* ctx, int on);
+dc_status dc_set_profiling(dc_ctx* ctx, int every);
 
 /* Wait for the profiled calls and write, for each of the last `max_calls`
  * profiled calls (oldest first), the milliseconds of stage A (steps 1-4)

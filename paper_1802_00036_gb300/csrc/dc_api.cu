@@ -65,6 +65,8 @@ struct dc_ctx {
     dc_status sticky = DC_OK;
     // profiling ring: 3 events per call (before A, between, after B)
     bool profiling = false;
+    int prof_every = 1;                 // profile one call in prof_every
+    unsigned long long prof_tick = 0;   // calls since profiling was turned on
     cudaEvent_t* prof_ev = nullptr;
     int prof_next = 0;     // next ring entry
     int prof_count = 0;    // valid entries
@@ -346,7 +348,7 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         return DC_ERR_CUDA;
 
     cudaEvent_t* ev = nullptr;
-    if (ctx->profiling) {
+    if (ctx->profiling && ctx->prof_tick++ % (unsigned long long)ctx->prof_every == 0) {
         ev = ctx->prof_ev + 3 * ctx->prof_next;
         ctx->prof_has_b[ctx->prof_next] = need_b ? 1 : 0;
         ctx->prof_next = (ctx->prof_next + 1) % DC_PROFILE_CALLS;
@@ -748,9 +750,10 @@ dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, in
     return s;
 }
 
-dc_status dc_set_profiling(dc_ctx* ctx, int on)
+dc_status dc_set_profiling(dc_ctx* ctx, int every)
 {
-    if (!ctx) return DC_ERR_INVALID_ARG;
+    if (!ctx || every < 0) return DC_ERR_INVALID_ARG;
+    const bool on = every > 0;
     DeviceGuard g(ctx->device);
     if (on && !ctx->prof_ev) {
         ctx->prof_ev = new (std::nothrow) cudaEvent_t[3 * DC_PROFILE_CALLS]();
@@ -758,7 +761,9 @@ dc_status dc_set_profiling(dc_ctx* ctx, int on)
         for (int i = 0; i < 3 * DC_PROFILE_CALLS; ++i)
             if (cudaEventCreate(&ctx->prof_ev[i]) != cudaSuccess) { cudaGetLastError(); return DC_ERR_CUDA; }
     }
-    ctx->profiling = on != 0;
+    ctx->profiling = on;
+    ctx->prof_every = on ? every : 1;
+    ctx->prof_tick = 0;
     ctx->prof_next = 0;
     ctx->prof_count = 0;
     return DC_OK;

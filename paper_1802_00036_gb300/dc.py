@@ -300,8 +300,10 @@ def dc_last_launch_count(ctx) -> int:
 DC_PROFILE_CALLS = 4096
 
 
-def dc_set_profiling(ctx, on: bool) -> None:
-    _check(load().dc_set_profiling(ctx, int(bool(on))), "dc_set_profiling")
+def dc_set_profiling(ctx, every) -> None:
+    """Profile one call in `every` (True: every call; False or 0: off)."""
+    every = int(every) if not isinstance(every, bool) else int(every)
+    _check(load().dc_set_profiling(ctx, every), "dc_set_profiling")
 
 
 def dc_kernel_times(ctx, max_calls: int = DC_PROFILE_CALLS):

@@ -375,6 +375,29 @@ def test_results_do_not_depend_on_tuning(ctx):
         dc.dc_set_tuning(ctx.h, 0, 3)
 
 
+def test_profiling_one_call_in_several(ctx):
+    # every third call of seven is profiled (calls 0, 3 and 6), with both
+    # stages timed; the results do not depend on it
+    from paper_1802_00036_gb300 import dc
+    frames = synth.make_batch(2, SMALL, config=12)
+    x = torch.from_numpy(frames).cuda()
+    want = gpu_run(ctx, frames)
+    dc.dc_set_profiling(ctx.h, 3)
+    try:
+        for _ in range(7):
+            y = torch.full_like(x, -1.0)
+            ctx.complete(x, y)
+        torch.cuda.synchronize()
+        times = dc.dc_kernel_times(ctx.h)
+        assert len(times) == 3 and all(a > 0 and b > 0 for a, b in times)
+        assert np.array_equal(y.cpu().numpy().view(np.uint32), want.view(np.uint32))
+    finally:
+        dc.dc_set_profiling(ctx.h, 0)
+    assert dc.dc_kernel_times(ctx.h) == []
+    with pytest.raises(dc.DcError):
+        dc.dc_set_profiling(ctx.h, -1)
+
+
 def test_invalid_arguments_are_refused(ctx):
     from paper_1802_00036_gb300 import dc
     x = torch.zeros((2, 16, 16), device="cuda")
