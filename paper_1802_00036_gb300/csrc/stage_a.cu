@@ -331,6 +331,10 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
     const int cx = sx + lane * kV;             // frame column of this lane's first column
     const bool edge = sx + kSW > W;            // strip crosses the frame's right edge
     const bool at_left = sx == 0;
+    // the rows written: C, or the output at a stop before step 5 (held in
+    // registers: re-reading the descriptor for every row measured 3 % slower)
+    float* const dst0 = (stop == kStopFull ? fd.c : fd.out) + cx;
+    const size_t dst_pitch = stop == kStopFull ? (size_t)fd.c_pitch : (size_t)fd.out_pitch;
     bool col_in[kV], col_out[kV];
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
@@ -395,7 +399,7 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
                         : stop == kStopClose  ? t - R1 - 4
                                               : t - Rh;
             if (r >= r0 && r < r1) {
-                float* dst = (stop == kStopFull ? fd.c + (size_t)r * fd.c_pitch : fd.out + (size_t)r * fd.out_pitch) + cx;
+                float* dst = dst0 + (size_t)r * dst_pitch;
 #pragma unroll
                 for (int v = 0; v < kV; ++v)
                     if (col_out[v]) dst[v] = 0.0f;
@@ -449,7 +453,7 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
         const int rc = rb - 3;  // == t - Rh
         if (stop == kStopFull) {
             if (rc >= r0 && rc < r1) {
-                float* dst = fd.c + (size_t)rc * fd.c_pitch + cx;
+                float* dst = dst0 + (size_t)rc * dst_pitch;
 #pragma unroll
                 for (int v = 0; v < kV; ++v)
                     if (col_out[v]) dst[v] = c[v];
@@ -481,7 +485,7 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
             if (stop == kStopDilate) r = ra;
             if (stop == kStopClose) r = rb;
             if (r >= r0 && r < r1) {
-                float* dst = fd.out + (size_t)r * fd.out_pitch + cx;
+                float* dst = dst0 + (size_t)r * dst_pitch;
 #pragma unroll
                 for (int v = 0; v < kV; ++v)
                     if (col_out[v]) dst[v] = val[v];
