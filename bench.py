@@ -346,6 +346,22 @@ def run_gpu(args, world, rank, local):
     torch.cuda.synchronize()
     pf_fps = B * pf_steps / (e0.elapsed_time(e1) / 1e3)
 
+    # the batched step replayed from CUDA graphs (dc_set_graph_cache): one graph
+    # per input set, captured on its first call
+    dc.dc_set_graph_cache(ctx.h, ROTATE)
+    for i in range(2 * ROTATE):
+        step(i)
+    stream.synchronize()
+    g_steps = max(20, min(args.steps // 2, 200))
+    e0.record(stream)
+    for i in range(g_steps):
+        step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    g_ms = e0.elapsed_time(e1) / g_steps
+    g_graphs = dc.dc_graph_cache_entries(ctx.h)
+    dc.dc_set_graph_cache(ctx.h, 0)
+
     # end to end through the host-buffer entry points (pinned), copies inside the timed region:
     # a stream of batches (each call's copy in overlaps the previous call's copy out; one wait
     # at the end), and one synchronous call per batch
@@ -416,6 +432,8 @@ def run_gpu(args, world, rank, local):
         "kernels_ms": {"stage_a": round(a_ms, 4) if a_ms else None, "stage_b": round(b_ms, 4) if b_ms else None,
                        "calls_timed": len(ktimes), "profiled_every": PROFILE_EVERY},
         "per_frame": {"value": round(pf_fps, 1), "unit": "frames/s", "note": "one dc_complete call per frame"},
+        "graph": {"value": round(B / g_ms * 1e3, 1), "unit": "frames/s", "ms_per_step": round(g_ms, 4),
+                  "graphs": g_graphs, "note": "the batched step replayed from CUDA graphs (dc_set_graph_cache)"},
         "e2e": {"value": round(e2e_fps, 1), "unit": "frames/s",
                 "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
                 "note": "dc_complete_host_async on pinned host buffers, one batch per call, every copy in "
@@ -576,9 +594,20 @@ def run_configs(args):
         ms = timed(lambda i: dc.dc_complete_uniform(ctx.h, ins[i].data_ptr(), outs[i].data_ptr(), n, H, W, p, sp), 4)
         ms1 = timed(lambda i: [dc.dc_complete_uniform(ctx.h, ins[i][k].data_ptr(), outs[i][k].data_ptr(), 1, H, W,
                                                       p, sp) for k in range(n)], 4)
+        # the same from CUDA graphs (dc_set_graph_cache): the batch as one graph
+        # launch per call; the 64 per-frame calls of one buffer set as 64 graphs
+        dc.dc_set_graph_cache(ctx.h, 4)
+        msg = timed(lambda i: dc.dc_complete_uniform(ctx.h, ins[i].data_ptr(), outs[i].data_ptr(), n, H, W, p, sp),
+                    4)
+        dc.dc_set_graph_cache(ctx.h, 64)
+        msg1 = timed(lambda i: [dc.dc_complete_uniform(ctx.h, ins[0][k].data_ptr(), outs[0][k].data_ptr(), 1, H, W,
+                                                       p, sp) for k in range(n)], 1)
+        dc.dc_set_graph_cache(ctx.h, 0)
         print(json.dumps({"workload": f"64 x 375x1242, 4-6 % valid, 1-90 m, median + {blur}",
                           "batched_frames_per_s": round(n / ms * 1e3, 1),
                           "per_frame_frames_per_s": round(n / ms1 * 1e3, 1),
+                          "batched_graph_frames_per_s": round(n / msg * 1e3, 1),
+                          "per_frame_graph_frames_per_s": round(n / msg1 * 1e3, 1),
                           "batched_GBps": round(n * H * W * 8 / ms / 1e6, 1)}), flush=True)
 
     # the four-resolution mix: 32 frames of each, one call (dc_complete) and per resolution

@@ -221,6 +221,24 @@ int dc_last_launch_count(const dc_ctx* ctx);
 #define DC_PROFILE_CALLS 4096
 dc_status dc_set_profiling(dc_ctx* ctx, int every);
 
+/* CUDA graphs for repeated calls (a stream of batches in the same buffers,
+ * one launch for a whole batch).  With max_graphs >= 1, a dc_complete or
+ * dc_complete_uniform call whose frames (pointers, sizes, pitches), params
+ * and tuning equal those of a recent call is queued as one graph launch of
+ * that call's kernels; another call runs as usual and is then captured, from
+ * a stream of the context, into a graph kept among the max_graphs most
+ * recently used.  The graphs read the frames' current contents: only the
+ * pointers must match.  Results, ordering and errors are those of the call
+ * without a graph; calls made while profiling is on are never captured, and
+ * growing the scratch drops the graphs.  0 turns the cache off (the
+ * default).  max_graphs outside 0..DC_MAX_GRAPHS is DC_ERR_INVALID_ARG.
+ * Changing the size waits for the context's last call and drops the graphs. */
+#define DC_MAX_GRAPHS 64
+dc_status dc_set_graph_cache(dc_ctx* ctx, int max_graphs);
+
+/* Number of graphs the context holds now (0 without a context). */
+int dc_graph_cache_entries(const dc_ctx* ctx);
+
 /* Wait for the profiled calls and write, for each of the last `max_calls`
  * profiled calls (oldest first), the milliseconds of stage A (steps 1-4)
  * and of stage B (steps 5-8; 0 when not launched) to ms[2*i], ms[2*i+1].

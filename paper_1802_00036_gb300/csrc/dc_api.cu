@@ -41,6 +41,20 @@ struct dc_ctx {
     FrameDesc* table = nullptr;  // frame descriptors of the current call (device)
     int frames_cap = 0;          // descriptors
     cudaEvent_t done = nullptr;  // recorded after each call's last kernel
+    // graphs of recent calls (dc_set_graph_cache): the call they replay, the
+    // executable, its launches and when it was last used
+    struct CachedGraph {
+        std::vector<dc_frame> frames;
+        dc_params params;
+        Tuning tune;
+        cudaGraphExec_t exec;
+        int launches;
+        unsigned long long used;
+    };
+    std::vector<CachedGraph> graphs;
+    int graph_max = 0;
+    unsigned long long graph_tick = 0;
+    cudaStream_t s_cap = nullptr;  // stream the graphs are captured from
     unsigned long long calls = 0;
     // staging for host calls: copy streams and events of the chunk pipeline
     // two staging sets, used by turns, so that one call's copy in can run
@@ -117,6 +131,12 @@ bool overlap(const void* a, size_t na, const void* b, size_t nb)
     return a0 < b0 + nb && b0 < a0 + na;
 }
 
+void drop_graphs(dc_ctx* ctx)
+{
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+}
+
 dc_status grow(dc_ctx* ctx, size_t c_floats, size_t top_ints, int frames, size_t io_floats,
                size_t work_ints = 0)
 {
@@ -131,6 +151,7 @@ dc_status grow(dc_ctx* ctx, size_t c_floats, size_t top_ints, int frames, size_t
     if (ctx->budget && scratch_bytes(nc, nt, nf, ni, nw) > ctx->budget) return DC_ERR_OOM;
     // queued work may still use the old buffers
     if (cudaDeviceSynchronize() != cudaSuccess) return DC_ERR_CUDA;
+    drop_graphs(ctx);  // they hold the scratch pointers
     if (nc > ctx->c_cap) {
         cudaFree(ctx->c);
         ctx->c = nullptr;
@@ -293,7 +314,11 @@ bool c_tensor_map(dc_ctx* ctx, const float* base, int n, int H, int W, int pitch
     return true;
 }
 
-dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cudaStream_t stream)
+// Queue one call.  With `capture` the launches go into a stream capture:
+// no wait on the previous call's event, no profiling, no bookkeeping (the
+// replay of the graph does those).
+dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cudaStream_t stream,
+              bool capture = false)
 {
     ctx->last_launches = 0;
     if (n == 0) return DC_OK;
@@ -338,7 +363,7 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
     }
 
     // calls share the scratch: order this one after the previous call
-    if (ctx->last_done && stream != ctx->last_stream &&
+    if (!capture && ctx->last_done && stream != ctx->last_stream &&
         cudaStreamWaitEvent(stream, ctx->last_done, 0) != cudaSuccess)
         return DC_ERR_CUDA;
     // the descriptors and the reset of the tops, written by a kernel
@@ -348,7 +373,7 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         return DC_ERR_CUDA;
 
     cudaEvent_t* ev = nullptr;
-    if (ctx->profiling && ctx->prof_tick++ % (unsigned long long)ctx->prof_every == 0) {
+    if (!capture && ctx->profiling && ctx->prof_tick++ % (unsigned long long)ctx->prof_every == 0) {
         ev = ctx->prof_ev + 3 * ctx->prof_next;
         ctx->prof_has_b[ctx->prof_next] = need_b ? 1 : 0;
         ctx->prof_next = (ctx->prof_next + 1) % DC_PROFILE_CALLS;
@@ -389,10 +414,71 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         ctx->last_launches = table_launches + ((bp.large_fill_on && bp.stop != kStopExtend) ? 3 : 2);
     }
     if (ev && cudaEventRecord(ev[2], stream) != cudaSuccess) return DC_ERR_CUDA;
+    if (capture) return DC_OK;
     if (cudaEventRecord(ctx->done, stream) != cudaSuccess) return DC_ERR_CUDA;
     ctx->last_done = ctx->done;
     ctx->last_stream = stream;
     ++ctx->calls;
+    return DC_OK;
+}
+
+// run() through the graph cache.  A call equal to a recent one (frames,
+// params, tuning) replays its graph; another runs as usual and is then
+// captured, from the context's own stream, for the next time (scratch has
+// grown by then, so the capture allocates nothing).  A capture that fails
+// only leaves the call without a graph.
+dc_status run_cached(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cudaStream_t stream)
+{
+    if (ctx->graph_max <= 0 || ctx->profiling || n == 0) return run(ctx, frames, n, p, stream);
+    for (auto& g : ctx->graphs) {
+        if ((int)g.frames.size() != n || std::memcmp(&g.params, p, sizeof(dc_params)) != 0 ||
+            std::memcmp(&g.tune, &ctx->tune, sizeof(Tuning)) != 0 ||
+            std::memcmp(g.frames.data(), frames, sizeof(dc_frame) * (size_t)n) != 0)
+            continue;
+        if (ctx->last_done && stream != ctx->last_stream &&
+            cudaStreamWaitEvent(stream, ctx->last_done, 0) != cudaSuccess)
+            return DC_ERR_CUDA;
+        if (cudaGraphLaunch(g.exec, stream) != cudaSuccess || cudaEventRecord(ctx->done, stream) != cudaSuccess)
+            return DC_ERR_CUDA;
+        ctx->last_done = ctx->done;
+        ctx->last_stream = stream;
+        ctx->last_launches = g.launches;
+        ++ctx->calls;
+        g.used = ++ctx->graph_tick;
+        return DC_OK;
+    }
+    dc_status s = run(ctx, frames, n, p, stream);
+    if (s != DC_OK) return s;
+    const int launches = ctx->last_launches;
+    if (!ctx->s_cap && cudaStreamCreateWithFlags(&ctx->s_cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return DC_OK;
+    }
+    if (cudaStreamBeginCapture(ctx->s_cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return DC_OK;
+    }
+    const dc_status cs = run(ctx, frames, n, p, ctx->s_cap, true);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->s_cap, &graph);
+    cudaGraphExec_t exec = nullptr;
+    const bool ok = cs == DC_OK && ce == cudaSuccess && graph &&
+                    cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    ctx->last_launches = launches;
+    if (!ok) {
+        cudaGetLastError();
+        return DC_OK;
+    }
+    if ((int)ctx->graphs.size() >= ctx->graph_max) {  // the least recently used makes room
+        size_t lru = 0;
+        for (size_t i = 1; i < ctx->graphs.size(); ++i)
+            if (ctx->graphs[i].used < ctx->graphs[lru].used) lru = i;
+        cudaGraphExecDestroy(ctx->graphs[lru].exec);
+        ctx->graphs.erase(ctx->graphs.begin() + (long)lru);
+    }
+    ctx->graphs.push_back(dc_ctx::CachedGraph{std::vector<dc_frame>(frames, frames + n), *p, ctx->tune, exec,
+                                              launches, ++ctx->graph_tick});
     return DC_OK;
 }
 
@@ -492,7 +578,7 @@ dc_status dc_complete(dc_ctx* ctx, const dc_frame* frames, int n_frames, const d
         return s;
     }
     DeviceGuard g(ctx->device);
-    return note(ctx, run(ctx, frames, n_frames, params, (cudaStream_t)stream));
+    return note(ctx, run_cached(ctx, frames, n_frames, params, (cudaStream_t)stream));
 }
 
 dc_status dc_complete_uniform(dc_ctx* ctx, const float* in, float* out, int n, int H, int W,
@@ -514,7 +600,7 @@ dc_status dc_complete_uniform(dc_ctx* ctx, const float* in, float* out, int n, i
     if (((uintptr_t)in % sizeof(float)) != 0 || ((uintptr_t)out % sizeof(float)) != 0)
         return DC_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
-    return note(ctx, run(ctx, fr.data(), n, params, (cudaStream_t)stream));
+    return note(ctx, run_cached(ctx, fr.data(), n, params, (cudaStream_t)stream));
 }
 
 namespace {
@@ -769,6 +855,20 @@ dc_status dc_set_profiling(dc_ctx* ctx, int every)
     return DC_OK;
 }
 
+dc_status dc_set_graph_cache(dc_ctx* ctx, int max_graphs)
+{
+    if (!ctx || max_graphs < 0 || max_graphs > DC_MAX_GRAPHS) return DC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (max_graphs != ctx->graph_max) {
+        if (cudaStreamSynchronize(ctx->last_stream) != cudaSuccess) return note(ctx, DC_ERR_CUDA);
+        drop_graphs(ctx);
+    }
+    ctx->graph_max = max_graphs;
+    return DC_OK;
+}
+
+int dc_graph_cache_entries(const dc_ctx* ctx) { return ctx ? (int)ctx->graphs.size() : 0; }
+
 dc_status dc_kernel_times(dc_ctx* ctx, float* ms, int max_calls, int* n_out)
 {
     if (!ctx || !ms || max_calls < 0 || !n_out) return DC_ERR_INVALID_ARG;
@@ -834,6 +934,8 @@ void dc_destroy(dc_ctx* ctx)
         cudaFree(ctx->acc);
         cudaFree(ctx->table);
         cudaFree(ctx->err);
+        drop_graphs(ctx);
+        if (ctx->s_cap) cudaStreamDestroy(ctx->s_cap);
         if (ctx->done) cudaEventDestroy(ctx->done);
         for (int k = 0; k < 2; ++k) {
             cudaFree(ctx->io_in[k]);

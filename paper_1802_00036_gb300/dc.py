@@ -98,6 +98,8 @@ SIGNATURES = [
                                    ctypes.c_int, ctypes.POINTER(dc_params), ctypes.c_void_p,
                                    ctypes.POINTER(dc_tuning)]),
     ("dc_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("dc_set_graph_cache", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("dc_graph_cache_entries", ctypes.c_int, [ctypes.c_void_p]),
     ("dc_kernel_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int)]),
     ("dc_last_async_error", ctypes.c_int, [ctypes.c_void_p]),
@@ -298,6 +300,16 @@ def dc_last_launch_count(ctx) -> int:
 
 
 DC_PROFILE_CALLS = 4096
+DC_MAX_GRAPHS = 64
+
+
+def dc_set_graph_cache(ctx, max_graphs: int) -> None:
+    """Replay repeated calls from up to `max_graphs` CUDA graphs (0: off)."""
+    _check(load().dc_set_graph_cache(ctx, int(max_graphs)), "dc_set_graph_cache")
+
+
+def dc_graph_cache_entries(ctx) -> int:
+    return int(load().dc_graph_cache_entries(ctx))
 
 
 def dc_set_profiling(ctx, every) -> None:

@@ -398,6 +398,77 @@ def test_profiling_one_call_in_several(ctx):
         dc.dc_set_profiling(ctx.h, -1)
 
 
+def test_graph_cache_replays_calls(ctx):
+    # with the cache on, a repeated call is one graph launch of the same
+    # kernels: the same bits as without, the current contents of the same
+    # buffers, other buffers captured anew, least recently used evicted,
+    # profiled calls run directly, scratch growth drops the graphs, and a
+    # call on another stream is still ordered after the previous one
+    from paper_1802_00036_gb300 import dc
+    spec = synth.FrameSpec(120, 250, 32, 0.05, 2.0, 80.0)
+    sets = [synth.make_batch(3, spec, config=13, first=10 * k) for k in range(3)]
+    want = [gpu_run(ctx, f) for f in sets]
+    xs = [torch.from_numpy(f).cuda() for f in sets]
+    ys = [torch.empty_like(x) for x in xs]
+    p = dc.params()
+    st = torch.cuda.current_stream().cuda_stream
+    launches = None
+
+    def call(k, stream=st):
+        ys[k].fill_(-3.0)
+        if stream != st:
+            torch.cuda.synchronize()          # the fill above ran on the current stream
+        dc.dc_complete_uniform(ctx.h, xs[k].data_ptr(), ys[k].data_ptr(), 3, spec.H, spec.W, p, stream)
+
+    def check(k, expect):
+        torch.cuda.synchronize()
+        assert np.array_equal(ys[k].cpu().numpy().view(np.uint32), expect.view(np.uint32)), k
+
+    dc.dc_set_graph_cache(ctx.h, 2)
+    try:
+        for rep in range(3):                  # capture, then replays
+            call(0)
+            check(0, want[0])
+            if launches is None:
+                launches = ctx.launches()
+            assert ctx.launches() == launches
+            assert dc.dc_graph_cache_entries(ctx.h) == 1
+        xs[0].copy_(xs[1])                    # new contents, same buffers
+        call(0)
+        check(0, want[1])
+        xs[0].copy_(torch.from_numpy(sets[0]).cuda())
+        for k in (1, 2, 0, 1):                # three buffer sets through two graphs
+            call(k)
+            check(k, want[k])
+            assert dc.dc_graph_cache_entries(ctx.h) == 2
+        other = torch.cuda.Stream()
+        call(2, other.cuda_stream)            # ordered after the call before it
+        other.synchronize()
+        check(2, want[2])
+        dc.dc_set_profiling(ctx.h, 1)         # profiled calls are not captured
+        dc.dc_set_graph_cache(ctx.h, 3)       # (a new size drops the graphs)
+        assert dc.dc_graph_cache_entries(ctx.h) == 0
+        call(1)
+        check(1, want[1])
+        assert dc.dc_graph_cache_entries(ctx.h) == 0
+        assert len(dc.dc_kernel_times(ctx.h)) == 1
+        dc.dc_set_profiling(ctx.h, 0)
+        big = synth.make_batch(40, synth.ONE_FRAME, config=13)
+        got_big = gpu_run(ctx, big)            # may grow the scratch: the graphs go
+        assert np.array_equal(got_big[5].view(np.uint32), gpu_run(ctx, big[5:6])[0].view(np.uint32))
+        for k in (0, 1):
+            call(k)
+            check(k, want[k])
+        assert dc.dc_graph_cache_entries(ctx.h) >= 1
+    finally:
+        dc.dc_set_graph_cache(ctx.h, 0)
+        dc.dc_set_profiling(ctx.h, 0)
+    assert dc.dc_graph_cache_entries(ctx.h) == 0
+    for bad in (-1, dc.DC_MAX_GRAPHS + 1):
+        with pytest.raises(dc.DcError):
+            dc.dc_set_graph_cache(ctx.h, bad)
+
+
 def test_invalid_arguments_are_refused(ctx):
     from paper_1802_00036_gb300 import dc
     x = torch.zeros((2, 16, 16), device="cuda")
