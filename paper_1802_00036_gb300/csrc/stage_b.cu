@@ -42,6 +42,7 @@ constexpr int kPR = kHalf + 4;      // packed key rows: input rows of one half
 static_assert(kMR % 4 == 0 && kMC % 8 == 0, "median blocks are 2 x 8, two per thread");
 static_assert((kHalf / 2) * (kMC / 8) == kThreadsB, "two median blocks per thread");
 static_assert(kES % 4 == 0 && kEC % 4 == 0 && kTBW % 4 == 0, "16-byte rows and chunks");
+static_assert(kER * kES >= kMR * kMS, "the median output as floats fits in the region buffer");
 
 struct FloatOps {
     static __device__ __forceinline__ float min2(float a, float b) { return fminf(a, b); }
@@ -422,7 +423,16 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
         return;
     }
     // bilateral or no blur, masked by the median, inverted, stored: each
-    // thread takes kStripRows rows of one column
+    // thread takes kStripRows rows of one column.  The bilateral reads the
+    // median output as floats, converted from keys once (into R, free now)
+    const float* Mv = Mf;
+    if constexpr (KEYS) {
+        if (p.blur == kBlurBilateral) {
+            for (int i = tid; i < kMR * kMS; i += kThreadsB) R[i] = value_of(Mk[i]);
+            __syncthreads();
+            Mv = R;
+        }
+    }
     constexpr int kStrips = kThreadsB / 64;
     constexpr int kStripRows = kTBH / kStrips;
     static_assert(kTBW <= 64 && kTBH % kStrips == 0, "column-pass mapping");
@@ -442,9 +452,11 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
                     for (int dx = -2; dx <= 2; ++dx) {
                         const int r2 = dy * dy + dx * dx;
                         if (r2 > 4) continue;
-                        const float v = m_at<KEYS>(Mf, Mk, (a + 2 + dy) * kMS + b + 2 + dx);
+                        const float v = Mv[(a + 2 + dy) * kMS + b + 2 + dx];
                         const float d = v - m;
-                        const float wgt = p.ws[r2] * expf(-(d * d) * p.inv_2sc2);
+                        // CUDA's fast exponential: its relative error (a few ulp for the
+                        // weights that count) moves the blur by well under 1e-4 m
+                        const float wgt = p.ws[r2] * __expf(-(d * d) * p.inv_2sc2);
                         num = fmaf(v, wgt, num);
                         den += wgt;
                     }
@@ -781,7 +793,7 @@ __device__ void constant_tile_store(const Tile& T, const StageBParams& p, const 
                             if (r2 > 4) continue;
                             const float v = Mrow[b + 2 + dx];
                             const float d = v - mc;
-                            const float wgt = p.ws[r2] * expf(-(d * d) * p.inv_2sc2);
+                            const float wgt = p.ws[r2] * __expf(-(d * d) * p.inv_2sc2);  // as in blur_store
                             num = fmaf(v, wgt, num);
                             den += wgt;
                         }
