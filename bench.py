@@ -221,13 +221,38 @@ def oracle_throughput(frames, threads: int, rounds: int = 1):
     return len(frames) * rounds / dt, dt
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(frames_pool):
     cores = os.cpu_count() or 1
     sample = [frames_pool[i % len(frames_pool)] for i in range(8 * cores)]
     fps, dt = oracle_throughput(sample, cores)
+    one = [frames_pool[i % len(frames_pool)] for i in range(8)]
+    fps1, dt1 = oracle_throughput(one, 1)
     return {"value": round(fps, 3), "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"{len(sample)} frames of 352x1216 (8 per core) through the single-threaded C oracle, "
                       f"one frame per thread on {cores} threads; {dt:.1f} s wall",
+            "single_thread": {"value": round(fps1, 3), "unit": "frames/s",
+                              "sample": f"{len(one)} frames on one thread; {dt1:.1f} s wall"},
             "context": PAPER_CONTEXT}
 
 
@@ -254,6 +279,7 @@ def run_reference(args, world, rank):
         "config": dict(workload_config(args.batch, args.blur),
                        sample=f"oracle on {cores} of the batch's frames per step, one per thread"),
         "cpu_baseline": {"value": round(fps, 3), "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "cpu_model": cpu_model(),
                          "sample": f"{cores} frames per step, one per thread"},
         "e2e": {"value": round(fps, 3), "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
