@@ -469,6 +469,26 @@ def test_graph_cache_replays_calls(ctx):
             dc.dc_set_graph_cache(ctx.h, bad)
 
 
+def test_graph_cache_with_host_buffer_calls(ctx):
+    # a stream of host-buffer calls replays the graphs of its chunks (two
+    # staging sets x two chunks) and returns every batch as computed directly
+    from paper_1802_00036_gb300 import dc
+    batches = [synth.make_batch(16, synth.ONE_FRAME, config=14, first=20 * i) for i in range(5)]
+    want = [gpu_run(ctx, b) for b in batches]
+    hins = [torch.from_numpy(b).pin_memory() for b in batches]
+    houts = [torch.full_like(h, -1.0).pin_memory() for h in hins]
+    dc.dc_set_graph_cache(ctx.h, 8)
+    try:
+        for h_in, h_out in zip(hins, houts):
+            dc.dc_complete_host_async(ctx.h, h_in.data_ptr(), h_out.data_ptr(), 16, 352, 1216, dc.params())
+        dc.dc_host_wait(ctx.h)
+        assert dc.dc_graph_cache_entries(ctx.h) == 4
+    finally:
+        dc.dc_set_graph_cache(ctx.h, 0)
+    for w, h_out in zip(want, houts):
+        assert np.array_equal(h_out.numpy().view(np.uint32), w.view(np.uint32))
+
+
 def test_invalid_arguments_are_refused(ctx):
     from paper_1802_00036_gb300 import dc
     x = torch.zeros((2, 16, 16), device="cuda")
