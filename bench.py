@@ -567,7 +567,7 @@ def run_serving(seconds):
            "server": "dc_server (native worker): batches of up to 64 on 2 lanes; one frame per launch on 3 lanes",
            "client": "results into a ring of 256 pinned buffers (32 per sensor)",
            "latency": "scheduled arrival to result in pinned host memory", "rates": []}
-    for rate in (125.0, 1000.0, 4000.0, 8000.0):
+    for rate in (10.0, 125.0, 1000.0, 4000.0, 8000.0):
         row = {"per_sensor_hz": rate}
         for name, kw in (("batched", dict(deadline_ms=2.0, max_batch=64, lanes=2)),
                          ("per_frame", dict(deadline_ms=0.0, max_batch=1, lanes=3))):
