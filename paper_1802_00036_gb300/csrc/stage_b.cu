@@ -1138,15 +1138,14 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
 // Row stride of the wide region in phase 2: 16-byte rows with room for the
 // shift of the region's first column down to a 16-byte boundary.
 __host__ __device__ constexpr int fill_row_stride(int GC) { return (GC + 6) / 4 * 4; }
-// Floats of RM: GR rows of GC + 1 (an odd stride), rounded to 16 bytes.
-__host__ __device__ constexpr int fill_rm_floats(int GR, int GC) { return (GR * (GC + 1) + 3) / 4 * 4; }
 
 // Phase 2: tiles from the worklist, with step 6.  Shared memory: G (E over
 // the wide region, rows of GS floats, 16-byte aligned, frame column gx at
-// offset sh; then the window maxima D), RM (column maxima S; the median
-// output once they are used), F (the step-6 output over tile + 4) and the
-// region's column tops.
-__global__ void __launch_bounds__(kThreadsB, 1)
+// offset sh; the window maxima are taken in place there, then it holds the
+// median output), F (E, then the step-6 output, over tile + 4; the blur's
+// buffer once the median has read it) and the region's column tops.  About
+// 60 KB at the paper's 31 x 31: three CTAs per SM.
+__global__ void __launch_bounds__(kThreadsB, 3)
 stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
              const int* __restrict__ worklist)
 {
@@ -1156,12 +1155,11 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
     const int GR = kER + 2 * Rl, GC = kEC + 2 * Rl;  // the wide region
     const int GS = fill_row_stride(GC);
     float* G = dyn;
-    float* RM = G + GR * GS;
-    float* F = RM + fill_rm_floats(GR, GC);
-    float* M = RM;
+    float* F = G + GR * GS;
+    float* M = G;
     int* ctop = reinterpret_cast<int*>(F + kER * kES);
     float* cval = reinterpret_cast<float*>(ctop + GC);
-    float* R = G;
+    float* R = F;
 
     const int count = worklist[0];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1230,61 +1228,51 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
             const int y = clampi(T.y0 - 4 + k, H), x = clampi(T.x0 - 4 + l, W);
             F[k * kES + l] = G[(y - gy) * GS + sh + (x - gx)];
         }
-        // The window maxima, separable, by van Herk's method: over blocks of
-        // wl = 2 Rl + 1 consecutive elements, suffix maxima (backward scan)
-        // and prefix maxima (forward scan); the window [j - 2 Rl, j] is the
-        // end of one block and the start of the next, so its maximum is the
-        // suffix maximum at j - 2 Rl with the prefix maximum at j, and goes
-        // where that suffix maximum was (no longer needed).  About three
-        // operations per element whatever the width.  Columns first, one
-        // thread per column (neighbouring threads, neighbouring banks), then
-        // the kER rows the tile needs, over odd row strides.
-        const int wl = 2 * Rl + 1, SS = GC + 1;
-        // columns: S[r][c] = max G[r .. r + 2 Rl][c] (centre row r + Rl), in RM
+        // The window maxima, separable and in place, by doubling: a pass with
+        // step s leaves at each index the maximum of the next 2 s elements
+        // (reading index + s, which that pass has not yet written), until the
+        // largest power of two P <= wl; then max(at j, at j + wl - P) covers
+        // [j, j + wl - 1].  G is E over the wide region; F keeps E over
+        // tile + 4 for the fill below.
+        __syncthreads();
+        const int wl = 2 * Rl + 1;
+        int P = 1;
+        while (2 * P <= wl) P *= 2;
+        // columns, one thread each (neighbouring threads, neighbouring banks):
+        // rows [0, kER) end with the maximum over [r, r + 2 Rl]
         for (int c = tid; c < GC; c += kThreadsB) {
-            const float* __restrict__ gc = G + sh + c;
-            float* __restrict__ sc = RM + c;
-            int q = (GR - 1) % wl;  // position within its block
-            float h = ninf();
-#pragma unroll 4
-            for (int r = GR - 1; r >= 0; --r) {
-                const float v = gc[r * GS];
-                h = (q == wl - 1 || r == GR - 1) ? v : fmaxf(h, v);
-                sc[r * SS] = h;
-                q = (q == 0) ? wl - 1 : q - 1;
-            }
-            float pm = ninf();
-            q = 0;
-#pragma unroll 4
-            for (int r = 0; r < GR; ++r) {
-                const float v = gc[r * GS];
-                pm = (q == 0) ? v : fmaxf(pm, v);
-                if (r >= 2 * Rl) sc[(r - 2 * Rl) * SS] = fmaxf(sc[(r - 2 * Rl) * SS], pm);
-                q = (q == wl - 1) ? 0 : q + 1;
-            }
+            float* __restrict__ col = G + sh + c;
+            for (int st = 1; st < P; st *= 2)
+                for (int r = 0; r + st < GR; ++r) col[r * GS] = fmaxf(col[r * GS], col[(r + st) * GS]);
+            if (wl > P)
+                for (int r = 0; r < kER; ++r) col[r * GS] = fmaxf(col[r * GS], col[(r + wl - P) * GS]);
         }
         __syncthreads();
-        // rows: D[k][c] = max S[k][c .. c + 2 Rl], the maximum over the window
-        // centred at (k + Rl, c + Rl) of G, for k < kER, c < kEC; D in G
-        for (int k = tid; k < kER; k += kThreadsB) {
-            const float* __restrict__ sr = RM + k * SS;
-            float* __restrict__ dr = G + k * SS;
-            int q = (GC - 1) % wl;
-            float h = ninf();
-#pragma unroll 4
-            for (int l = GC - 1; l >= 0; --l) {
-                const float v = sr[l];
-                h = (q == wl - 1 || l == GC - 1) ? v : fmaxf(h, v);
-                dr[l] = h;
-                q = (q == 0) ? wl - 1 : q - 1;
-            }
-            float pm = ninf();
-            q = 0;
-#pragma unroll 4
-            for (int l = 0; l < GC; ++l) {
-                pm = (q == 0) ? sr[l] : fmaxf(pm, sr[l]);
-                if (l >= 2 * Rl) dr[l - 2 * Rl] = fmaxf(dr[l - 2 * Rl], pm);
-                q = (q == wl - 1) ? 0 : q + 1;
+        // rows [0, kER), one warp each: lanes read a pass's pairs, then write;
+        // columns [0, kEC) end with the maximum over [c, c + 2 Rl]
+        {
+            constexpr int kPer = (kEC + 2 * (kMaxLargeFill / 2) + 31) / 32;  // columns a lane holds
+            const int warp = tid >> 5, lane = tid & 31;
+            for (int k = warp; k < kER; k += kThreadsB / 32) {
+                float* __restrict__ row = G + k * GS + sh;
+                for (int st = 1; st <= P; st *= 2) {
+                    const int step = st < P ? st : wl - P;  // the last pass combines at wl - P
+                    const int n = st < P ? GC - 2 * st + 1 : kEC;
+                    if (st == P && wl == P) break;
+                    float v[kPer];
+#pragma unroll
+                    for (int j = 0; j < kPer; ++j) {
+                        const int c = lane + 32 * j;
+                        v[j] = c < n ? fmaxf(row[c], row[c + step]) : 0.0f;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int j = 0; j < kPer; ++j) {
+                        const int c = lane + 32 * j;
+                        if (c < n) row[c] = v[j];
+                    }
+                    __syncwarp();
+                }
             }
         }
         __syncthreads();
@@ -1292,9 +1280,9 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
         for (int i = tid; i < kER * kEC; i += kThreadsB) {
             const int k = i / kEC, l = i - k * kEC;
             const int y = clampi(T.y0 - 4 + k, H), x = clampi(T.x0 - 4 + l, W);
-            const int dk = y - gy - Rl, dl = x - gx - Rl;  // the window's centre in D
+            const int dk = y - gy - Rl, dl = x - gx - Rl;  // the window's corner
             const float e = F[k * kES + l];
-            if (is_empty(e)) F[k * kES + l] = fmaxf(e, G[dk * SS + dl]);
+            if (is_empty(e)) F[k * kES + l] = fmaxf(e, G[dk * GS + sh + dl]);
         }
         __syncthreads();
         if (p.stop == kStopFillLarge) {
@@ -1314,7 +1302,7 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
 size_t stage_b_fill_smem_bytes(int large_radius)
 {
     const int GR = kER + 2 * large_radius, GC = kEC + 2 * large_radius;
-    return sizeof(float) * ((size_t)GR * fill_row_stride(GC) + fill_rm_floats(GR, GC) + kER * kES + 2 * GC);
+    return sizeof(float) * ((size_t)GR * fill_row_stride(GC) + kER * kES + 2 * GC);
 }
 
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,
@@ -1347,7 +1335,12 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
                                           dim3(kThreadsB), main_smem, stream, d_frames, n_frames, total_tiles, q,
                                           worklist, map, err);
     if (e != cudaSuccess || !p.large_fill_on || p.stop == kStopExtend) return e;
-    int grid = 2 * sm_count;
+    // as many CTAs per SM as shared memory holds, three at most (registers)
+    const size_t fill_smem = stage_b_fill_smem_bytes(p.large_radius);
+    int per_sm = (int)(233472 / (fill_smem + 1024));
+    if (per_sm > 3) per_sm = 3;
+    if (per_sm < 1) per_sm = 1;
+    int grid = per_sm * sm_count;
     if (grid > total_tiles) grid = total_tiles;
     return launch_after_previous(stage_b_fill, dim3(grid), dim3(kThreadsB), stage_b_fill_smem_bytes(p.large_radius),
                                  stream, d_frames, n_frames, p, static_cast<const int*>(worklist));
