@@ -78,3 +78,19 @@ def test_params_struct_layout_matches_header():
     # ten 4-byte fields, no padding
     assert ctypes.sizeof(dc.dc_params) == 40
     assert ctypes.sizeof(dc.dc_frame) == 2 * ctypes.sizeof(ctypes.c_void_p) + 16
+
+
+def test_calls_without_a_context_are_refused(lib):
+    # checked before any CUDA call: no GPU needed
+    L = dc.load()
+    INVALID = 1
+    assert L.dc_set_graph_cache(None, 1) == INVALID
+    assert L.dc_set_profiling(None, 1) == INVALID
+    assert L.dc_host_wait(None) == INVALID
+    assert L.dc_graph_cache_entries(None) == 0
+    assert L.dc_last_launch_count(None) == 0
+    n = ctypes.c_int(-1)
+    buf = (ctypes.c_float * 2)()
+    assert L.dc_kernel_times(None, buf, 1, ctypes.byref(n)) == INVALID
+    p = dc.dc_params_default()
+    assert L.dc_complete_uniform(None, None, None, 1, 8, 8, ctypes.byref(p), None) == INVALID
