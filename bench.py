@@ -52,6 +52,9 @@ def parse():
                     help="seconds of Poisson arrivals per rate in the serving leg (0: skip)")
     ap.add_argument("--quick", action="store_true",
                     help="timed batched steps only (no per-frame, e2e or CPU legs): for profiling")
+    ap.add_argument("--tuning", default=None,
+                    help="launch shape 'a_warps_per_sm,b_ctas_per_sm,b_sparse_fill' instead of the tuning "
+                         "cache or the autotuner (e.g. 16,5,160: profile captures name it)")
     ap.add_argument("--configs", action="store_true",
                     help="instead of the bench line: one JSON line per further workload (the 375x1242 "
                          "batch with both blurs, the four-resolution mix, the element x fill-size sweep)")
@@ -309,7 +312,12 @@ def run_gpu(args, world, rank, local):
     p = dc.params(blur=args.blur)
     dc.dc_reserve(ctx.h, B, H, W)
     from paper_1802_00036_gb300 import tune
-    tuning = tune.tuned(ctx, ins[0], outs[0], p, stream)  # before any timed region
+    if args.tuning:
+        t = tuple(int(v) for v in args.tuning.split(","))
+        dc.dc_set_tuning(ctx.h, *t)
+        tuning = (t, "command line")
+    else:
+        tuning = tune.tuned(ctx, ins[0], outs[0], p, stream)  # before any timed region
 
     def step(i):
         dc.dc_complete_uniform(ctx.h, ins[i % ROTATE].data_ptr(), outs[i % ROTATE].data_ptr(), B, H, W, p, sp)

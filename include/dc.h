@@ -288,7 +288,7 @@ void dc_destroy(dc_ctx* ctx);
 #define DC_NOALLOC_MAX_COLUMNS 131072
 #define DC_NOALLOC_WORK_INTS 65536 /* tile worklist; enough for any batch within the limits above */
 #define DC_NOALLOC_SCRATCH_BYTES \
-    (4 * DC_NOALLOC_MAX_PIXELS + 8 * DC_NOALLOC_MAX_COLUMNS + 4 * DC_NOALLOC_WORK_INTS + 65536)
+    (6 * DC_NOALLOC_MAX_PIXELS + 8 * DC_NOALLOC_MAX_COLUMNS + 4 * DC_NOALLOC_WORK_INTS + 65536)
 dc_status dc_complete_noalloc(const float* in, float* out, int n, int H, int W,
                               const dc_params* params, void* stream);
 

@@ -12,7 +12,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/dc.h"
+
 namespace dcgb {
+
+// The checks every entry point applies to a dc_params (dc_api.cu).
+bool params_ok(const dc_params* p);
 
 // A pixel is empty below 0.1 (Section IV-1: empty pixels hold 0, valid
 // inverted depths lie 20 m or more above them).
@@ -23,13 +28,42 @@ constexpr float kInvertFrom = 100.0f;
 // A column's top row as stage B keeps it (any real row is smaller).
 constexpr int kNoTop = 0x7F7F7F7F;
 
-// A column's top in scratch: the row in the high half, the bits of the
-// (positive) C value there in the low half, so that one 64-bit atomicMin
-// keeps the smallest row with its value and one load brings both.
-constexpr unsigned long long kNoTopPacked = ~0ull;
-__device__ __forceinline__ unsigned long long top_pack(int row, float v)
+// The step-4 map C between the kernels is kept as 16-bit keys: a value v
+// that is k / 256 for an integer k (KITTI stores depth as 16-bit fixed
+// point, depth x 256, and every such inverted depth stays on that grid
+// through steps 1-4, which only select values) is stored as k, an exact,
+// order-preserving encoding; any other value is stored as kKeyOff, with the
+// value itself at the same position of a float map.  Inverted depths of
+// valid inputs lie below 100, so a real key is at most kKeyMax.
+constexpr unsigned kKeyOff = 0xFFFFu;
+constexpr unsigned kKeyMax = 25600u;
+
+// 16-bit key of v: k with v == k / 256 exactly, k < 65536; `ok` is cleared
+// when v has no such key.  fma(v, 256, 2^23) holds 2^23 + k exactly iff
+// v * 256 is an integer in [0, 2^23): the nearest k is in its low mantissa
+// bits, and rebuilding k / 256 from them gives v back only when v is on the
+// grid and in [0, 256).
+__device__ __forceinline__ unsigned key_of(float v, bool& ok)
 {
-    return ((unsigned long long)(unsigned)row << 32) | (unsigned long long)__float_as_uint(v);
+    const unsigned k = __float_as_uint(fmaf(v, 256.0f, 8388608.0f)) & 0xFFFFu;
+    ok = ok && (__uint_as_float(0x47000000u | k) - 32768.0f) == v;
+    return k;
+}
+
+// The float value of a 16-bit key: exactly k / 256.
+__device__ __forceinline__ float key_value(unsigned k)
+{
+    return __uint_as_float(0x47000000u | k) - 32768.0f;  // (2^15 + k / 256) - 2^15
+}
+
+// A column's top in scratch: the row in the high half, the key of the C
+// value there (kKeyOff: the value is in the float map) in the low half, so
+// that one 64-bit atomicMin keeps the smallest row with its value and one
+// load brings both.
+constexpr unsigned long long kNoTopPacked = ~0ull;
+__device__ __forceinline__ unsigned long long top_pack(int row, unsigned key)
+{
+    return ((unsigned long long)(unsigned)row << 32) | (unsigned long long)key;
 }
 
 // Stage A: one warp streams one (strip, band) unit; 4 units per block.
@@ -39,6 +73,11 @@ constexpr int kThreadsA = 32;  // one warp per CTA: the block scheduler spreads 
 constexpr int kTileBH = 60;
 constexpr int kTileBW = 60;
 constexpr int kThreadsB = 128;
+// Stage B's region of C (tile + 4 ring) comes as one box of keys whose first
+// column is rounded down to a multiple of 8 (16 bytes), hence 4 more columns.
+constexpr int kKeyBoxW = kTileBW + 12;
+constexpr int kKeyBoxH = kTileBH + 8;
+static_assert(kTileBW % 8 == 4 || kTileBW % 8 == 0, "the region starts 0 or 4 columns into its key box");
 
 // Largest step-6 square side the kernels accept.
 constexpr int kMaxLargeFill = 63;
@@ -55,10 +94,11 @@ enum Stop {
 struct FrameDesc {
     const float* in;   // sparse depth, in_pitch floats per row
     float* out;        // result, out_pitch floats per row
-    float* c;          // step-4 map, c_pitch floats per row (scratch)
-    unsigned long long* top;  // W entries: top_pack(topmost non-empty row of C, C there); kNoTopPacked: none
+    unsigned short* ck;  // step-4 map as keys, c_pitch per row (scratch)
+    float* c;          // step-4 values whose key is kKeyOff, c_pitch floats per row (scratch)
+    unsigned long long* top;  // W entries: top_pack(topmost non-empty row of C, its key); kNoTopPacked: none
     int H, W;
-    int in_pitch, out_pitch, c_pitch;
+    int in_pitch, out_pitch, c_pitch;  // c_pitch: a multiple of 32 elements
     int tiles_x_a, base_a;  // stage A: strips per frame, first flat unit
     int band_a;             // stage A: rows per band
     int tiles_x_b, base_b;  // stage B: same
@@ -110,6 +150,20 @@ inline cudaError_t launch_after_previous(void (*kernel)(KArgs...), dim3 grid, di
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// C at frame pixel (y, x) as a float.
+__device__ __forceinline__ float c_at(const FrameDesc& fd, int y, int x)
+{
+    const size_t i = (size_t)y * fd.c_pitch + x;
+    const unsigned k = fd.ck[i];
+    return k == kKeyOff ? fd.c[i] : key_value(k);
+}
+
+// The value of a column top (row, key) of frame column x as a float.
+__device__ __forceinline__ float top_value(const FrameDesc& fd, int row, unsigned key, int x)
+{
+    return key == kKeyOff ? fd.c[(size_t)row * fd.c_pitch + x] : key_value(key);
 }
 
 // Frame owning flat tile t: the last f with base(f) <= t.

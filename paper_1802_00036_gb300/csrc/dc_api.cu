@@ -14,6 +14,24 @@
 
 using namespace dcgb;
 
+namespace dcgb {
+
+bool params_ok(const dc_params* p)
+{
+    if (!p) return false;
+    if (p->first_kernel < DC_K_DIAMOND5 || p->first_kernel > DC_K_FULL7) return false;
+    if (p->large_fill_on && (p->large_fill < 1 || p->large_fill > kMaxLargeFill || (p->large_fill % 2) == 0))
+        return false;
+    if (p->blur < DC_BLUR_NONE || p->blur > DC_BLUR_BILATERAL) return false;
+    if (p->blur == DC_BLUR_BILATERAL && (!(p->sigma_space > 0.0f) || !(p->sigma_color > 0.0f) ||
+                                         !std::isfinite(p->sigma_space) || !std::isfinite(p->sigma_color)))
+        return false;
+    if (p->stop_after < DC_STOP_FULL || p->stop_after > DC_STOP_BLUR) return false;
+    return true;
+}
+
+}  // namespace dcgb
+
 // dc_complete_host splits a batch into at most this many chunks so that the
 // copy in of chunk i + 1, the kernels of chunk i and the copy out of chunk
 // i - 1 overlap.
@@ -25,8 +43,9 @@ struct dc_ctx {
     size_t budget = 0;  // 0 = unlimited
     Tuning tune = kDefaultTuning;
     // scratch
-    float* c = nullptr;       // step-4 maps, all frames
+    float* c = nullptr;       // step-4 values off the key grid, all frames
     size_t c_cap = 0;         // floats
+    unsigned short* ck = nullptr;  // step-4 maps as keys, all frames (same layout as c)
     unsigned long long* top = nullptr;  // per-column tops (top_pack), all frames
     size_t top_cap = 0;                 // entries
     int* work = nullptr;      // counters of both stages, then the step-6 tile list
@@ -34,7 +53,7 @@ struct dc_ctx {
     double* acc = nullptr;    // accuracy sums and results, 10 doubles per frame
     int acc_cap = 0;          // frames
     int* err = nullptr;          // set by a device-side wait that gave up (device int)
-    // the tensor map of C for batches of one shape, kept while the layout holds
+    // the tensor map of C's keys for batches of one shape, kept while the layout holds
     CUtensorMap cmap{};
     const void* cmap_base = nullptr;
     int cmap_W = 0, cmap_H = 0, cmap_n = 0, cmap_pitch = 0;
@@ -105,25 +124,13 @@ struct DeviceGuard {
 
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
+// The step-4 map takes a key (2 bytes) and a float (4 bytes) per position.
 size_t scratch_bytes(size_t c_floats, size_t top_ints, int frames, size_t io_floats, size_t work_ints)
 {
-    return c_floats * sizeof(float) + top_ints * sizeof(unsigned long long) + work_ints * sizeof(int) +
-           (size_t)frames * sizeof(FrameDesc) + 4 * io_floats * sizeof(float);
+    return c_floats * (sizeof(float) + sizeof(unsigned short)) + top_ints * sizeof(unsigned long long) +
+           work_ints * sizeof(int) + (size_t)frames * sizeof(FrameDesc) + 4 * io_floats * sizeof(float);
 }
 
-bool params_ok(const dc_params* p)
-{
-    if (!p) return false;
-    if (p->first_kernel < DC_K_DIAMOND5 || p->first_kernel > DC_K_FULL7) return false;
-    if (p->large_fill_on && (p->large_fill < 1 || p->large_fill > kMaxLargeFill || (p->large_fill % 2) == 0))
-        return false;
-    if (p->blur < DC_BLUR_NONE || p->blur > DC_BLUR_BILATERAL) return false;
-    if (p->blur == DC_BLUR_BILATERAL && (!(p->sigma_space > 0.0f) || !(p->sigma_color > 0.0f) ||
-                                         !std::isfinite(p->sigma_space) || !std::isfinite(p->sigma_color)))
-        return false;
-    if (p->stop_after < DC_STOP_FULL || p->stop_after > DC_STOP_BLUR) return false;
-    return true;
-}
 
 bool overlap(const void* a, size_t na, const void* b, size_t nb)
 {
@@ -154,9 +161,16 @@ dc_status grow(dc_ctx* ctx, size_t c_floats, size_t top_ints, int frames, size_t
     drop_graphs(ctx);  // they hold the scratch pointers
     if (nc > ctx->c_cap) {
         cudaFree(ctx->c);
+        cudaFree(ctx->ck);
         ctx->c = nullptr;
+        ctx->ck = nullptr;
         ctx->c_cap = 0;
-        if (cudaMalloc(&ctx->c, nc * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return DC_ERR_OOM; }
+        ctx->cmap_base = nullptr;
+        if (cudaMalloc(&ctx->c, nc * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&ctx->ck, nc * sizeof(unsigned short)) != cudaSuccess) {
+            cudaGetLastError();
+            return DC_ERR_OOM;
+        }
         ctx->c_cap = nc;
     }
     if (nt > ctx->top_cap) {
@@ -287,22 +301,24 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// The tensor map of n step-4 maps of H x W (rows `pitch` floats apart,
-// frames H pitch floats apart) at `base`, with a box of the stage-B region;
-// false if it cannot be made (then the regions come by cp.async).
-bool c_tensor_map(dc_ctx* ctx, const float* base, int n, int H, int W, int pitch)
+// The tensor map of n step-4 key maps of H x W (rows `pitch` keys apart,
+// frames H pitch keys apart) at `base`, with the box of stage B's region
+// (kKeyBoxW x kKeyBoxH keys); false if it cannot be made (then the regions
+// come by cp.async).
+bool c_tensor_map(dc_ctx* ctx, const unsigned short* base, int n, int H, int W, int pitch)
 {
     if (ctx->cmap_base == base && ctx->cmap_n == n && ctx->cmap_H == H && ctx->cmap_W == W &&
         ctx->cmap_pitch == pitch)
         return true;
     ctx->cmap_base = nullptr;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc || (reinterpret_cast<uintptr_t>(base) % 16) != 0 || (pitch * sizeof(float)) % 16 != 0) return false;
+    const size_t row_bytes = (size_t)pitch * sizeof(unsigned short);
+    if (!enc || (reinterpret_cast<uintptr_t>(base) % 16) != 0 || row_bytes % 16 != 0) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
-    const cuuint64_t strides[2] = {(cuuint64_t)pitch * sizeof(float), (cuuint64_t)pitch * sizeof(float) * H};
-    const cuuint32_t box[3] = {(cuuint32_t)(kTileBW + 8), (cuuint32_t)(kTileBH + 8), 1};
+    const cuuint64_t strides[2] = {(cuuint64_t)row_bytes, (cuuint64_t)row_bytes * H};
+    const cuuint32_t box[3] = {(cuuint32_t)kKeyBoxW, (cuuint32_t)kKeyBoxH, 1};
     const cuuint32_t estride[3] = {1, 1, 1};
-    if (enc(&ctx->cmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estride,
+    if (enc(&ctx->cmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<unsigned short*>(base), dims, strides, box, estride,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
@@ -347,6 +363,7 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         tiles_a += (long long)d.tiles_x_a * ceil_div(f.H, d.band_a);
         tiles_b += (long long)d.tiles_x_b * ceil_div(f.H, kTileBH);
         d.c = reinterpret_cast<float*>(c_off);  // offsets until scratch is known
+        d.ck = reinterpret_cast<unsigned short*>(c_off);
         d.top = reinterpret_cast<unsigned long long*>(top_off);
         c_off += frame_c_floats(f.H, f.W);
         top_off += frame_top_ints(f.W);
@@ -358,6 +375,7 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
                        need_b ? (size_t)tiles_b + 3 : 3);
     if (s != DC_OK) return s;
     for (auto& d : desc) {
+        d.ck = need_b ? ctx->ck + reinterpret_cast<size_t>(d.ck) : nullptr;
         d.c = need_b ? ctx->c + reinterpret_cast<size_t>(d.c) : nullptr;
         d.top = need_b ? ctx->top + reinterpret_cast<size_t>(d.top) : nullptr;
     }
@@ -404,8 +422,8 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         const double sc = p->blur == DC_BLUR_BILATERAL ? p->sigma_color : 1.0;
         for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));
         bp.inv_2sc2 = (float)(1.0 / (2.0 * sc * sc));
-        // frames of one shape: C is one W x H x n array, one tensor map
-        const bool tma = one_shape && c_tensor_map(ctx, desc[0].c, n, frames[0].H, frames[0].W, desc[0].c_pitch);
+        // frames of one shape: C's keys are one W x H x n array, one tensor map
+        const bool tma = one_shape && c_tensor_map(ctx, desc[0].ck, n, frames[0].H, frames[0].W, desc[0].c_pitch);
         bp.tma = tma ? 1 : 0;
         e = launch_stage_b(ctx->table, n, (int)tiles_b, bp, ctx->work, ctx->sm_count, ctx->tune.b_ctas_per_sm,
                            tma ? &ctx->cmap : nullptr, ctx->err, stream);
@@ -929,6 +947,7 @@ void dc_destroy(dc_ctx* ctx)
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
         cudaFree(ctx->c);
+        cudaFree(ctx->ck);
         cudaFree(ctx->top);
         cudaFree(ctx->work);
         cudaFree(ctx->acc);

@@ -4,8 +4,8 @@
 // All scratch (frame table, per-column tops, step-4 map) sits in one
 // file-scope device array.  Host code must not use the array's name as a
 // pointer: here it is only a host-side stand-in, and a kernel handed it would
-// fault or read the wrong memory.  The device address is looked up once per
-// device with cudaGetSymbolAddress, with that device current, and cached.
+// fault or read the wrong memory.  The device address is looked up on each
+// call with cudaGetSymbolAddress, with the caller's device current.
 #include "../../include/dc.h"
 #include "common.cuh"
 
@@ -20,38 +20,41 @@ namespace {
 constexpr size_t kTableBytes = 65536;
 constexpr size_t kTopBytes = 8u * DC_NOALLOC_MAX_COLUMNS;
 constexpr size_t kWorkBytes = 4u * DC_NOALLOC_WORK_INTS;
+constexpr size_t kKeyBytes = 2u * DC_NOALLOC_MAX_PIXELS;
 constexpr size_t kMapBytes = 4u * DC_NOALLOC_MAX_PIXELS;
-static_assert(kTableBytes + kTopBytes + kWorkBytes + kMapBytes == DC_NOALLOC_SCRATCH_BYTES, "layout");
+static_assert(kTableBytes + kTopBytes + kWorkBytes + kKeyBytes + kMapBytes == DC_NOALLOC_SCRATCH_BYTES, "layout");
 static_assert(DC_NOALLOC_MAX_FRAMES * sizeof(FrameDesc) <= kTableBytes, "frame table");
 
-// Layout: [frame table | tops | worklist | step-4 maps]; each part 256-byte aligned.
+// Layout: [frame table | tops | worklist | step-4 keys | step-4 values];
+// each part 256-byte aligned.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[DC_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned char* g_dev_ptr[kMaxDevices] = {};  // device address of the array, per device
-int g_sm_count[kMaxDevices] = {};
+int g_sm_count[kMaxDevices] = {};  // per device, looked up once
 
-// Per-device set-up; must run with `dev` current.
+// The array's device address in the current context (looked up on every
+// call: a cached address would go stale under another context of the same
+// device or after a device reset) and the device's SM count; must run with
+// `dev` current.
 dc_status setup(int dev, unsigned char** ptr, int* sms)
 {
     if (dev < 0 || dev >= kMaxDevices) return DC_ERR_UNSUPPORTED;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return DC_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_dev_ptr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return DC_ERR_CUDA;
-        }
+    if (g_sm_count[dev] == 0) {
         int n = 0;
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
             cudaGetLastError();
             return DC_ERR_CUDA;
         }
         g_sm_count[dev] = n;
-        g_dev_ptr[dev] = static_cast<unsigned char*>(p);
     }
-    *ptr = g_dev_ptr[dev];
+    *ptr = static_cast<unsigned char*>(p);
     *sms = g_sm_count[dev];
     return DC_OK;
 }
@@ -59,19 +62,24 @@ dc_status setup(int dev, unsigned char** ptr, int* sms)
 // Writes the frame table for n packed frames, resets the tops and stage A's
 // unit counter: the only preparation the two stage kernels need, done on
 // the device so that the call copies nothing from the host.
-__global__ void noalloc_prepare(FrameDesc* table, unsigned long long* top, float* cmap, const float* in, float* out,
+__global__ void noalloc_prepare(FrameDesc* table, unsigned long long* top, unsigned short* ckeys, float* cmap,
+                                const float* in, float* out,
                                 int n, int H, int W, int c_pitch, int tiles_x_a, int tiles_a, int band_a,
-                                int tiles_x_b, int tiles_b, int top_ints, int* counter)
+                                int tiles_x_b, int tiles_b, int top_ints, int* counter, int* err)
 {
     allow_next_kernel();  // stage A may launch; it waits for this kernel's writes
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
-    if (tid == 0) *counter = 0;  // stage A's unit counter
+    if (tid == 0) {
+        *counter = 0;  // stage A's unit counter
+        *err = 0;      // stage B's error word (set only by its tensor-copy wait, which this path does not use)
+    }
     for (int i = tid; i < n; i += stride) {
         FrameDesc d;
         d.in = in + (size_t)i * H * W;
         d.out = out + (size_t)i * H * W;
         d.c = cmap ? cmap + (size_t)i * H * c_pitch : nullptr;
+        d.ck = ckeys ? ckeys + (size_t)i * H * c_pitch : nullptr;
         d.top = top ? top + (size_t)i * c_pitch : nullptr;
         d.H = H;
         d.W = W;
@@ -89,25 +97,13 @@ __global__ void noalloc_prepare(FrameDesc* table, unsigned long long* top, float
         for (int i = tid; i < top_ints; i += stride) top[i] = kNoTopPacked;
 }
 
-bool params_valid(const dc_params* p)
-{
-    if (!p) return false;
-    if (p->first_kernel < DC_K_DIAMOND5 || p->first_kernel > DC_K_FULL7) return false;
-    if (p->large_fill_on && (p->large_fill < 1 || p->large_fill > kMaxLargeFill || (p->large_fill % 2) == 0))
-        return false;
-    if (p->blur < DC_BLUR_NONE || p->blur > DC_BLUR_BILATERAL) return false;
-    if (p->blur == DC_BLUR_BILATERAL && (!(p->sigma_space > 0.0f) || !(p->sigma_color > 0.0f) ||
-                                         !std::isfinite(p->sigma_space) || !std::isfinite(p->sigma_color)))
-        return false;
-    return p->stop_after >= DC_STOP_FULL && p->stop_after <= DC_STOP_BLUR;
-}
 
 }  // namespace
 
 extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int H, int W,
                                          const dc_params* params, void* stream)
 {
-    if (n < 0 || !params_valid(params)) return DC_ERR_INVALID_ARG;
+    if (n < 0 || !params_ok(params)) return DC_ERR_INVALID_ARG;
     if (n == 0) return DC_OK;
     if (!in || !out || H < 1 || W < 1) return DC_ERR_INVALID_ARG;
     if (((uintptr_t)in % sizeof(float)) != 0 || ((uintptr_t)out % sizeof(float)) != 0)
@@ -130,7 +126,8 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     FrameDesc* table = reinterpret_cast<FrameDesc*>(base);
     unsigned long long* top = reinterpret_cast<unsigned long long*>(base + kTableBytes);
     int* work = reinterpret_cast<int*>(base + kTableBytes + kTopBytes);
-    float* cmap = reinterpret_cast<float*>(base + kTableBytes + kTopBytes + kWorkBytes);
+    unsigned short* ckeys = reinterpret_cast<unsigned short*>(base + kTableBytes + kTopBytes + kWorkBytes);
+    float* cmap = reinterpret_cast<float*>(base + kTableBytes + kTopBytes + kWorkBytes + kKeyBytes);
     const bool need_b = (params->stop_after == DC_STOP_FULL || params->stop_after >= DC_STOP_EXTEND);
     const int tiles_x_a = stage_a_strips(W, params->first_kernel);
     const int band_a = stage_a_band_rows(H, (long long)tiles_x_a * n,
@@ -146,9 +143,11 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     const int threads = 256;
     int blocks = (top_ints > n ? top_ints : n) / threads + 1;
     if (blocks > 1024) blocks = 1024;
-    noalloc_prepare<<<blocks, threads, 0, st>>>(table, need_b ? top : nullptr, need_b ? cmap : nullptr,
+    noalloc_prepare<<<blocks, threads, 0, st>>>(table, need_b ? top : nullptr, need_b ? ckeys : nullptr,
+                                                 need_b ? cmap : nullptr,
                                                  in, out, n, H, W, (int)c_pitch, tiles_x_a, tiles_a, band_a,
-                                                 tiles_x_b, tiles_b, top_ints, work + 2);
+                                                 tiles_x_b, tiles_b, top_ints, work + 2,
+                                                 work + DC_NOALLOC_WORK_INTS - 1);
     if (cudaGetLastError() != cudaSuccess) return DC_ERR_CUDA;
 
     const int stop_a = need_b ? kStopFull : params->stop_after;
@@ -170,6 +169,8 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
         const double sc = params->blur == DC_BLUR_BILATERAL ? params->sigma_color : 1.0;
         for (int r2 = 0; r2 < 5; ++r2) bp.ws[r2] = (float)std::exp(-(double)r2 / (2.0 * ss * ss));
         bp.inv_2sc2 = (float)(1.0 / (2.0 * sc * sc));
+        // regions by cp.async (no tensor map: the map would have to be written
+        // for the array's address); the error word is zeroed by noalloc_prepare
         if (launch_stage_b(table, n, tiles_b * n, bp, work, sms, kDefaultTuning.b_ctas_per_sm, nullptr,
                            work + DC_NOALLOC_WORK_INTS - 1, st) != cudaSuccess)
             return DC_ERR_CUDA;

@@ -19,10 +19,11 @@
 // each side are only halo: strips overlap by that much, bands by as many
 // rows, and the rings start with values that only reach rows above the band.
 //
-// Output: C (the step-4 map) into scratch, and for each column the smallest
-// row with a non-empty C and its value, by a 64-bit atomicMin on top[]
-// (step 5 needs them).  With a
-// stop before step 5 the requested map goes to the output instead.
+// Output: C (the step-4 map) into scratch as 16-bit keys (k for a value
+// k / 256; a value off that grid as kKeyOff, the value itself in the float
+// map), and for each column the smallest row with a non-empty C and its key,
+// by a 64-bit atomicMin on top[] (step 5 needs them).  With a stop before
+// step 5 the requested map goes to the output instead.
 #include "common.cuh"
 
 #include <climits>
@@ -331,9 +332,11 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
     const int cx = sx + lane * kV;             // frame column of this lane's first column
     const bool edge = sx + kSW > W;            // strip crosses the frame's right edge
     const bool at_left = sx == 0;
-    // the rows written: C, or the output at a stop before step 5 (held in
-    // registers: re-reading the descriptor for every row measured 3 % slower)
+    // the rows written: C's keys (off-grid values in the float map), or the
+    // output at a stop before step 5 (held in registers: re-reading the
+    // descriptor for every row measured 3 % slower)
     float* const dst0 = (stop == kStopFull ? fd.c : fd.out) + cx;
+    unsigned short* const kdst0 = stop == kStopFull ? fd.ck + cx : nullptr;
     const size_t dst_pitch = stop == kStopFull ? (size_t)fd.c_pitch : (size_t)fd.out_pitch;
     bool col_in[kV], col_out[kV];
 #pragma unroll
@@ -342,6 +345,13 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
         col_in[v] = c < W;
         col_out[v] = col_in[v] && (j >= Rh || at_left) && j < Rh + OW;
     }
+    // a lane writes its four keys by one 8-byte store, or two 4-byte ones
+    // (cx is even: strips start at even columns), unless some of its columns
+    // are halo or beyond the frame
+    bool all_out = true;
+#pragma unroll
+    for (int v = 0; v < kV; ++v) all_out = all_out && col_out[v];
+    const bool al8 = (cx & 3) == 0;
 
     FirstDilation<S> s2;
     Square5<true> s3d;
@@ -352,11 +362,11 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
     s3e.init(pinf());
     s4.init();
     int top_row[kV];
-    float top_val[kV];
+    unsigned top_key[kV];
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
         top_row[v] = INT_MAX;
-        top_val[v] = 0.0f;
+        top_key[v] = 0u;
     }
     bool tops_pending = (stop == kStopFull);
 
@@ -399,10 +409,21 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
                         : stop == kStopClose  ? t - R1 - 4
                                               : t - Rh;
             if (r >= r0 && r < r1) {
-                float* dst = dst0 + (size_t)r * dst_pitch;
+                if (stop == kStopFull) {  // C: key 0
+                    unsigned short* kd = kdst0 + (size_t)r * dst_pitch;
+                    if (all_out && al8) {
+                        *reinterpret_cast<uint2*>(kd) = make_uint2(0u, 0u);
+                    } else {
 #pragma unroll
-                for (int v = 0; v < kV; ++v)
-                    if (col_out[v]) dst[v] = 0.0f;
+                        for (int v = 0; v < kV; ++v)
+                            if (col_out[v]) kd[v] = 0;
+                    }
+                } else {
+                    float* dst = dst0 + (size_t)r * dst_pitch;
+#pragma unroll
+                    for (int v = 0; v < kV; ++v)
+                        if (col_out[v]) dst[v] = 0.0f;
+                }
             }
             return;
         }
@@ -453,17 +474,42 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
         const int rc = rb - 3;  // == t - Rh
         if (stop == kStopFull) {
             if (rc >= r0 && rc < r1) {
-                float* dst = dst0 + (size_t)rc * dst_pitch;
+                unsigned k[kV];
+                bool grid = true;
 #pragma unroll
-                for (int v = 0; v < kV; ++v)
-                    if (col_out[v]) dst[v] = c[v];
+                for (int v = 0; v < kV; ++v) {
+                    bool ok = true;
+                    k[v] = key_of(c[v], ok);
+                    if (!ok) k[v] = kKeyOff;
+                    grid = grid && ok;
+                }
+                unsigned short* kd = kdst0 + (size_t)rc * dst_pitch;
+                if (all_out) {
+                    const unsigned w0 = __byte_perm(k[0], k[1], 0x5410), w1 = __byte_perm(k[2], k[3], 0x5410);
+                    if (al8) {
+                        *reinterpret_cast<uint2*>(kd) = make_uint2(w0, w1);
+                    } else {
+                        reinterpret_cast<unsigned*>(kd)[0] = w0;
+                        reinterpret_cast<unsigned*>(kd)[1] = w1;
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < kV; ++v)
+                        if (col_out[v]) kd[v] = (unsigned short)k[v];
+                }
+                if (!grid) {  // values off the key grid, by value
+                    float* dst = dst0 + (size_t)rc * dst_pitch;
+#pragma unroll
+                    for (int v = 0; v < kV; ++v)
+                        if (col_out[v] && k[v] == kKeyOff) dst[v] = c[v];
+                }
                 if (tops_pending) {
                     bool left = false;
 #pragma unroll
                     for (int v = 0; v < kV; ++v) {
                         if (col_out[v] && !is_empty(c[v]) && top_row[v] == INT_MAX) {
                             top_row[v] = rc;
-                            top_val[v] = c[v];
+                            top_key[v] = k[v];
                         }
                         left |= col_out[v] && top_row[v] == INT_MAX;
                     }
@@ -502,7 +548,7 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
     if (stop == kStopFull) {
 #pragma unroll
         for (int v = 0; v < kV; ++v)
-            if (col_out[v] && top_row[v] != INT_MAX) atomicMin(&fd.top[cx + v], top_pack(top_row[v], top_val[v]));
+            if (col_out[v] && top_row[v] != INT_MAX) atomicMin(&fd.top[cx + v], top_pack(top_row[v], top_key[v]));
     }
 }
 

@@ -75,27 +75,8 @@ struct PackedKeyOps {
     }
 };
 
-// 16-bit key of v: k with v == k / 256 exactly, k < 65536; `ok` is cleared
-// when v has no such key.  fma(v, 256, 2^23) holds 2^23 + k exactly iff
-// v * 256 is an integer in [0, 2^23).
-__device__ __forceinline__ unsigned key_of(float v, bool& ok)
-{
-    // the nearest k / 256 (2^23 + 256 v rounded: k in the low mantissa bits),
-    // then the check that it is v itself, which fails for v outside [0, 256)
-    // and for v between two keys
-    const unsigned k = __float_as_uint(fmaf(v, 256.0f, 8388608.0f)) & 0xFFFFu;
-    ok = ok && (__uint_as_float(0x47000000u | k) - 32768.0f) == v;
-    return k;
-}
-
 // A key k is empty (k / 256 < 0.1) exactly when k <= 25.
 constexpr unsigned kEmptyKeyMax = 25;
-
-// The float value of a 16-bit key: exactly k / 256.
-__device__ __forceinline__ float value_of(unsigned k)
-{
-    return __uint_as_float(0x47000000u | k) - 32768.0f;  // (2^15 + k / 256) - 2^15
-}
 
 __device__ __forceinline__ int clampi(int p, int n) { return p < 0 ? 0 : (p >= n ? n - 1 : p); }
 
@@ -181,24 +162,35 @@ __device__ __forceinline__ Tile tile_of(const FrameDesc* __restrict__ frames, in
     return T;
 }
 
-// Column tops and their values for columns [xa, xa + n) (clamped into the
-// frame), into ctop / cval.
+// Column tops and the keys of their values for columns [xa, xa + n)
+// (clamped into the frame), into ctop / ctv (kNoTop, 0: none, or step 5 off).
 __device__ __forceinline__ void load_tops(const Tile& T, const StageBParams& p, int xa, int n,
-                                          int* ctop, float* cval)
+                                          int* ctop, unsigned* ctv)
 {
     for (int i = threadIdx.x; i < n; i += kThreadsB) {
         const int x = clampi(xa + i, T.fd.W);
         int top = kNoTop;
-        float v = 0.0f;
+        unsigned k = 0u;
         if (p.extend_top) {
-            const unsigned long long t = T.fd.top[x];  // row and value in one load
+            const unsigned long long t = T.fd.top[x];  // row and key in one load
             if (t != kNoTopPacked) {
                 top = (int)(t >> 32);
-                v = __uint_as_float((unsigned)t);
+                k = (unsigned)t;
             }
         }
         ctop[i] = top;
-        cval[i] = v;
+        ctv[i] = k;
+    }
+}
+
+// The top values of load_tops as floats, in place (ctv's words become the
+// floats' bits): k / 256, or the float map's value for an off-grid one.
+__device__ __forceinline__ void tops_to_floats(const Tile& T, int xa, int n, const int* ctop, unsigned* ctv)
+{
+    for (int i = threadIdx.x; i < n; i += kThreadsB) {
+        const int top = ctop[i];
+        const float v = top == kNoTop ? 0.0f : top_value(T.fd, top, ctv[i], clampi(xa + i, T.fd.W));
+        ctv[i] = __float_as_uint(v);
     }
 }
 
@@ -211,7 +203,14 @@ __device__ __forceinline__ bool above_top(const StageBParams& p, int y, int top)
 __device__ __forceinline__ float extended(const Tile& T, const StageBParams& p, int y, int x,
                                           int top, float topval)
 {
-    return above_top(p, y, top) ? topval : T.fd.c[(size_t)y * T.fd.c_pitch + x];
+    return above_top(p, y, top) ? topval : c_at(T.fd, y, x);
+}
+
+// The same as a key (kKeyOff where C is off the key grid).
+__device__ __forceinline__ unsigned extended_key(const Tile& T, const StageBParams& p, int y, int x,
+                                                 int top, unsigned topkey)
+{
+    return above_top(p, y, top) ? topkey : (unsigned)T.fd.ck[(size_t)y * T.fd.c_pitch + x];
 }
 
 // Whether E (C after step 5) is empty in frame column x from row 0 to row
@@ -243,7 +242,7 @@ __device__ void store_zero_tile(const Tile& T)
 template <bool KEYS>
 __device__ __forceinline__ float m_at(const float* __restrict__ Mf, const unsigned short* __restrict__ Mk, int i)
 {
-    if constexpr (KEYS) return value_of(Mk[i]);
+    if constexpr (KEYS) return key_value(Mk[i]);
     else return Mf[i];
 }
 
@@ -258,8 +257,8 @@ __device__ __forceinline__ void m_row8(const float* __restrict__ Mf, const unsig
         const unsigned w[4] = {lo.x, lo.y, hi.x, hi.y};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            v[2 * j] = value_of(w[j] & 0xFFFFu);
-            v[2 * j + 1] = value_of(w[j] >> 16);
+            v[2 * j] = key_value(w[j] & 0xFFFFu);
+            v[2 * j + 1] = key_value(w[j] >> 16);
         }
     } else {
         const float4 lo = *reinterpret_cast<const float4*>(Mf + i);
@@ -428,7 +427,7 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
     const float* Mv = Mf;
     if constexpr (KEYS) {
         if (p.blur == kBlurBilateral) {
-            for (int i = tid; i < kMR * kMS; i += kThreadsB) R[i] = value_of(Mk[i]);
+            for (int i = tid; i < kMR * kMS; i += kThreadsB) R[i] = key_value(Mk[i]);
             __syncthreads();
             Mv = R;
         }
@@ -468,21 +467,35 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
     }
 }
 
+// Region position (k, l) from the packed keys K: rows k < kPR are the low
+// halves of K row k, rows k >= kHalf the high halves of K row k - kHalf.
+__device__ __forceinline__ unsigned key_at(const unsigned* K, int k, int l)
+{
+    const unsigned short* h = reinterpret_cast<const unsigned short*>(K);
+    return k < kPR ? h[2 * (k * kES + l)] : h[2 * ((k - kHalf) * kES + l) + 1];
+}
+
 // The shared tail.  F: the median input (kER x kES floats, border
 // replicated).  K: the same values as packed 16-bit keys (row k of the top
 // half in the low halves of K row k, row k + kHalf in the high halves) when
-// `keys` is set.  The median goes to Mk as 16-bit keys when it ran on keys,
-// else to Mf as floats (Mf may alias K and Mk, which are then idle), then
-// blur_store.  R (kMR x kRS floats) may alias F, not Mf or Mk.
+// `keys` is set (F is then not read).  The median goes to Mk as 16-bit keys
+// when it ran on keys, else to Mf as floats (Mf may alias K and Mk, which
+// are then idle), then blur_store.  R (kMR x kRS floats) may alias F, not Mf
+// or Mk.
 __device__ void median_blur_store(const Tile& T, const StageBParams& p, const float* __restrict__ F,
                                   const unsigned* __restrict__ K, bool keys, float* __restrict__ Mf,
                                   unsigned short* __restrict__ Mk, float* __restrict__ R)
 {
     const int tid = threadIdx.x;
-    const bool use_keys = keys && p.median;
+    const bool use_keys = keys;
     // -- step 7: median, blocks (rb, cb) and (rb + kHalf / 2, cb) of 2 x 8
     const int rb = tid / (kMC / 8), cb = tid % (kMC / 8);
-    if (!p.median) {
+    if (!p.median && use_keys) {
+        for (int i = tid; i < kMR * kMC; i += kThreadsB) {
+            const int a = i / kMC, b = i - a * kMC;
+            Mk[a * kMS + b] = (unsigned short)key_at(K, a + 2, b + 2);
+        }
+    } else if (!p.median) {
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -567,7 +580,7 @@ __device__ float large_fill_at(const Tile& T, const StageBParams& p, int y, int 
                 const unsigned long long t = T.fd.top[xx];
                 if (t != kNoTopPacked) {
                     top = (int)(t >> 32);
-                    tv = __uint_as_float((unsigned)t);
+                    tv = top_value(T.fd, top, (unsigned)t, xx);
                 }
             }
 #pragma unroll 4
@@ -583,9 +596,7 @@ __device__ float large_fill_at(const Tile& T, const StageBParams& p, int y, int 
 // more than StageBParams::sparse_fill_max (<= this) goes to the worklist.
 constexpr int kMaxSparseFill = 160;
 
-// The median input region as 16-byte chunks: kER rows x kChunksPerRow.  The
-// region's first column x0 - 4 is a multiple of 4 (tiles start at multiples
-// of 60) and rows of C are 128-byte aligned, so every chunk is aligned.
+// Region work is split by column chunk of 4: kER rows x kChunksPerRow.
 constexpr int kChunksPerRow = kEC / 4;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
@@ -596,12 +607,17 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// The region by one tensor copy (TMA): thread 0 arms the CTA's mbarrier with
-// the byte count and starts the copy of the kER x kEC box at (x, y, frame) of
-// C; parts outside the frame arrive as zeros (they are never read as pixels).
-// Every thread then waits for the barrier's phase, a bounded number of times.
-constexpr unsigned kRegionBytes = kER * kEC * sizeof(float);
-static_assert(kEC == kES && (kEC * sizeof(float)) % 16 == 0, "dense 16-byte rows in the tensor box");
+// The region's keys arrive as a kKeyBoxH x kKeyBoxW box Ek (16-bit, dense
+// rows) whose first column is the region's first column x0 - 4 rounded down
+// to a multiple of 8 (16 bytes): region column l is box column l + ko, ko 0
+// or 4.  By one tensor copy (TMA): thread 0 arms the CTA's mbarrier with the
+// byte count and starts the copy of the box at (x, y, frame) of C's keys;
+// parts outside the frame arrive as zeros.  Every thread then waits for the
+// barrier's phase, a bounded number of times.
+static_assert(kKeyBoxW == kEC + 4 && kKeyBoxH == kER && (kKeyBoxW * 2) % 16 == 0, "the key box");
+static_assert(kKeyBoxW * kKeyBoxH * 2 <= kER * kES * 4, "the key box fits in the region buffer");
+constexpr unsigned kRegionBytes = kKeyBoxW * kKeyBoxH * 2;
+__device__ __forceinline__ int key_box_x(int x0) { return (x0 - 4) & ~7; }
 
 __device__ __forceinline__ unsigned smem_addr(const void* p)
 {
@@ -651,23 +667,19 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* mbar, unsigned par
 // kChunksPerRow, so its column bounds and column tops are computed once.
 constexpr int kRowGroups = kThreadsB / kChunksPerRow;
 
-// Start copying a tile's region of C into `dst` (kER x kES): the in-frame
-// chunks (a chunk straddling the right edge reads the row padding of C,
-// which is allocated).
-__device__ __forceinline__ void issue_region(const Tile& T, float* dst)
+// Start copying a tile's key box into `dst` by 16-byte cp.async chunks of 8
+// keys: the in-frame ones (rows of C's keys are padded to 32 keys, so a chunk
+// straddling the right edge reads allocated padding; key_box_x is a multiple
+// of 8, so no chunk straddles the left edge).  The rest is left as it was.
+__device__ __forceinline__ void issue_region_keys(const Tile& T, unsigned short* dst)
 {
-    const int tid = threadIdx.x;
-    if (tid < kRowGroups * kChunksPerRow) {
-        const int g = tid / kChunksPerRow, q = tid - g * kChunksPerRow;
-        const int xs = T.x0 - 4 + 4 * q;
-        if (xs >= 0 && xs < T.fd.W) {
-            const int klo = max(0, 4 - T.y0), khi = min(kER, T.fd.H - T.y0 + 4);  // in-frame rows
-            int k = g;
-            while (k < klo) k += kRowGroups;
-            const float* src = T.fd.c + (size_t)(T.y0 - 4 + k) * T.fd.c_pitch + xs;
-            const size_t step = (size_t)kRowGroups * T.fd.c_pitch;
-            for (; k < khi; k += kRowGroups, src += step) cp_async16(dst + k * kES + 4 * q, src);
-        }
+    constexpr int kChunks = kKeyBoxW / 8;
+    const int xb = key_box_x(T.x0);
+    for (int i = threadIdx.x; i < kKeyBoxH * kChunks; i += kThreadsB) {
+        const int k = i / kChunks, j = i - k * kChunks;
+        const int y = T.y0 - 4 + k, x = xb + 8 * j;
+        if (y >= 0 && y < T.fd.H && x >= 0 && x < T.fd.W)
+            cp_async16(dst + k * kKeyBoxW + 8 * j, T.fd.ck + (size_t)y * T.fd.c_pitch + x);
     }
     cp_async_commit();
 }
@@ -817,14 +829,17 @@ __device__ void constant_tile_store(const Tile& T, const StageBParams& p, const 
     }
 }
 
-// Shared memory of phase 1: the region E, the packed keys K, the median
-// output as 16-bit keys Mk (the float median output Mf lies over K and Mk,
-// which are idle on that path), extra step-6 scratch X, column tops, the
-// empty pixels (list, and their columns as a bitmap, a list and an index).
-// Before the median, Mk and X are step-6 scratch (kSmallScratch floats); a
-// tile that needs more also takes K and rebuilds its keys afterwards
-// (kBigScratch floats).  The total leaves room for five CTAs per SM
-// (233,472 bytes; allocations in 128-byte units, 1 KB reserved per CTA).
+// Shared memory of phase 1: the region (its key box on the key path, E as
+// floats on the float path; the Gaussian's row-pass buffer after the
+// median), the packed keys K, the median output as 16-bit keys Mk (the float
+// median output Mf lies over K and Mk, which are idle on that path), extra
+// step-6 scratch X, column tops, the empty pixels (list, and their columns
+// as a bitmap, a list and an index).  Before the median, Mk and X are step-6
+// scratch (kSmallScratch floats); on the float path a tile that needs more
+// also takes K and rebuilds its keys afterwards (kBigScratch floats), on the
+// key path the region buffer is free once K holds the keys.  The total
+// leaves room for five CTAs per SM (233,472 bytes; allocations in 128-byte
+// units, 1 KB reserved per CTA).
 constexpr int kScratchExtra = 1792;
 constexpr int kSmallScratch = kMR * kMS / 2 + kScratchExtra;
 constexpr int kBigScratch = kPR * kES + kSmallScratch;
@@ -836,13 +851,551 @@ static_assert((kER * kES) % 4 == 0 && (kPR * kES) % 4 == 0 && kMS % 8 == 0, "16-
 static_assert(5 * ((kMainSmemFloats * 4 + kMainStaticSmem + 127) / 128 * 128 + 1024) <= 233472,
               "five CTAs per SM");
 
+// The CTA's buffers of phase 1.
+struct MainSmem {
+    float* E;            // the region: key box (key path), floats (float path); later the row-pass buffer
+    unsigned* K;         // the region as packed keys
+    unsigned short* Mk;  // median output, keys
+    float* Mf;           // median output, floats (over K and Mk)
+    float* scratch;      // kSmallScratch floats (Mk and X), idle until the median
+    int* ctop;           // the region's column tops
+    unsigned* ctv;       // their keys; their values' bits after tops_to_floats
+    int* elist;          // empty pixels, (region row << 16) | region column
+    int* ecount;
+    unsigned* ecols;     // bitmap of region columns with empty pixels
+    int* ecol_list;      // those columns, in order
+    int* ecol_idx;       // region column -> position in the list
+    int* ebox;           // region rows spanned by the empty pixels: kmin, kmax
+};
+
+__device__ __forceinline__ void reset_empties(const MainSmem& S)
+{
+    if (threadIdx.x == 0) {
+        *S.ecount = 0;
+        S.ebox[0] = 1 << 20;
+        S.ebox[1] = -1;
+        S.ecols[0] = S.ecols[1] = S.ecols[2] = 0u;
+    }
+}
+
+// Record the empty pixels `em` (bit e: column 4 q + e) of region row k.
+__device__ __forceinline__ void note_empties(const MainSmem& S, int k, int q, unsigned em)
+{
+    int slot = atomicAdd(S.ecount, __popc(em));
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if ((em >> e) & 1u) {
+            if (slot < kMaxSparseFill) S.elist[slot] = (k << 16) | (4 * q + e);
+            ++slot;
+        }
+    atomicMin(S.ebox + 0, k);
+    atomicMax(S.ebox + 1, k);
+    atomicOr(S.ecols + ((4 * q) >> 5), em << ((4 * q) & 31));
+}
+
+// The output of a tile from K (a stop after step 5 or 6: the map itself).
+__device__ void store_keys_tile(const Tile& T, const unsigned* K)
+{
+    for (int i = threadIdx.x; i < kTBH * kTBW; i += kThreadsB) {
+        const int a = i / kTBW, b = i - a * kTBW;
+        const int y = T.y0 + a, x = T.x0 + b;
+        if (y < T.fd.H && x < T.fd.W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = key_value(key_at(K, a + 4, b + 4));
+    }
+}
+
+// Step 6 at one empty pixel (y, x) on keys: the maximum key of E over the
+// in-frame part of its window, from C's keys with step 5 applied; one warp
+// per pixel, lane = column offset, the maximum in every lane.  `bad` is set
+// when the window holds a value off the key grid (kKeyOff is the largest key).
+__device__ unsigned large_fill_key_at(const Tile& T, const StageBParams& p, int y, int x, int lane, bool& bad)
+{
+    const int Rl = p.large_radius, H = T.fd.H, W = T.fd.W;
+    const int ylo = max(0, y - Rl), yhi = min(H - 1, y + Rl);
+    unsigned m = 0u;
+    for (int dx0 = -Rl; dx0 <= Rl; dx0 += 32) {
+        const int dx = dx0 + lane;
+        const int xx = x + dx;
+        if (dx <= Rl && xx >= 0 && xx < W) {
+            int top = kNoTop;
+            unsigned tk = 0u;
+            if (p.extend_top) {
+                const unsigned long long t = T.fd.top[xx];
+                if (t != kNoTopPacked) {
+                    top = (int)(t >> 32);
+                    tk = (unsigned)t;
+                }
+            }
+#pragma unroll 4
+            for (int yy = ylo; yy <= yhi; ++yy) m = max(m, extended_key(T, p, yy, xx, top, tk));
+        }
+    }
+    bad = bad || m > kKeyMax;
+    return __reduce_max_sync(0xffffffffu, m);
+}
+
+// The empty pixels' distinct columns as a list (ecol_list, in order; ecol_idx
+// maps a region column to its position), their number and the first and
+// last.  Warps 0-2 take the bitmap's words.
+__device__ __forceinline__ void empty_columns(const MainSmem& S, int& ND, int& lmin, int& lmax)
+{
+    const int tid = threadIdx.x;
+    const unsigned w0 = S.ecols[0], w1 = S.ecols[1], w2 = S.ecols[2];
+    if (tid < 96) {
+        const int w = tid >> 5, lane = tid & 31;
+        const unsigned bits = w == 0 ? w0 : (w == 1 ? w1 : w2);
+        const int pos = (w > 0 ? __popc(w0) : 0) + (w > 1 ? __popc(w1) : 0) + __popc(bits & ((1u << lane) - 1u));
+        if ((bits >> lane) & 1u) {
+            S.ecol_list[pos] = tid;
+            S.ecol_idx[tid] = pos;
+        }
+    }
+    ND = __popc(w0) + __popc(w1) + __popc(w2);
+    lmin = w0 ? __ffs(w0) - 1 : (w1 ? 31 + __ffs(w1) : 63 + __ffs(w2));
+    lmax = w2 ? 95 - __clz(w2) : (w1 ? 63 - __clz(w1) : 31 - __clz(w0));
+}
+
+// Step 6 at the few empty pixels of a tile on keys (K holds the region with
+// step 5 applied): the union of their windows (box) streams in row bands
+// through the region buffer, idle now, keeping row maxima at their distinct
+// columns in the scratch, then column maxima at each pixel; or, when that
+// does not fit, one warp per pixel reading its window from C.  Writes the
+// fills into K.  False (block-uniform) when a value read is off the key grid.
+__device__ bool fill_keys(const Tile& T, const StageBParams& p, const MainSmem& S, int n_empty)
+{
+    const int tid = threadIdx.x, H = T.fd.H, W = T.fd.W, Rl = p.large_radius;
+    int ND, lmin, lmax;
+    empty_columns(S, ND, lmin, lmax);
+    const int by0 = max(0, T.y0 - 4 + S.ebox[0] - Rl), by1 = min(H - 1, T.y0 - 4 + S.ebox[1] + Rl);
+    const int bx0 = max(0, T.x0 - 4 + lmin - Rl), bx1 = min(W - 1, T.x0 - 4 + lmax + Rl);
+    const int BR = by1 - by0 + 1, BC = bx1 - bx0 + 1;
+    constexpr int kBandWords = kER * kES;
+    bool bad = false;
+    if (BR * ND <= kSmallScratch && 3 * BC <= kBandWords) {
+        unsigned* rmax = reinterpret_cast<unsigned*>(S.scratch);
+        int* btop = reinterpret_cast<int*>(S.E);
+        unsigned* btk = reinterpret_cast<unsigned*>(btop + BC);
+        unsigned* band = btk + BC;
+        const int RB = min(BR, (kBandWords - 2 * BC) / BC);
+        for (int c = tid; c < BC; c += kThreadsB) {
+            int top = kNoTop;
+            unsigned tk = 0u;
+            if (p.extend_top) {
+                const unsigned long long t2 = __ldg(T.fd.top + bx0 + c);
+                if (t2 != kNoTopPacked) {
+                    top = (int)(t2 >> 32);
+                    tk = (unsigned)t2;
+                }
+            }
+            btop[c] = top;
+            btk[c] = tk;
+        }
+        __syncthreads();
+        for (int r0 = 0; r0 < BR; r0 += RB) {
+            const int nb = min(RB, BR - r0);
+            // the band of E: inside the tile's region from K, elsewhere from C
+            for (int i = tid; i < nb * BC; i += kThreadsB) {
+                const int r = i / BC, c = i - r * BC;
+                const int k = by0 + r0 + r - (T.y0 - 4), l = bx0 + c - (T.x0 - 4);
+                unsigned v;
+                if ((unsigned)k < (unsigned)kER && (unsigned)l < (unsigned)kEC) {
+                    v = key_at(S.K, k, l);
+                } else {
+                    v = extended_key(T, p, by0 + r0 + r, bx0 + c, btop[c], btk[c]);
+                    bad = bad || v > kKeyMax;
+                }
+                band[i] = v;
+            }
+            __syncthreads();
+            // its row maxima over the window width at the empty columns
+            for (int i = tid; i < nb * ND; i += kThreadsB) {
+                const int r = i / ND, j = i - r * ND;
+                const int c = T.x0 - 4 + S.ecol_list[j];
+                const int lo = max(c - Rl, bx0) - bx0, hi = min(c + Rl, bx1) - bx0;
+                unsigned m = 0u;
+                for (int x = lo; x <= hi; ++x) m = max(m, band[r * BC + x]);
+                rmax[(r0 + r) * ND + j] = m;
+            }
+            __syncthreads();
+        }
+        // column maxima at each empty pixel
+        for (int j = tid; j < n_empty; j += kThreadsB) {
+            const int k = S.elist[j] >> 16, l = S.elist[j] & 0xFFFF;
+            const int y = T.y0 - 4 + k;
+            const int lo = max(y - Rl, by0) - by0, hi = min(y + Rl, by1) - by0;
+            const int jc = S.ecol_idx[l];
+            unsigned m = 0u;
+            for (int r = lo; r <= hi; ++r) m = max(m, rmax[r * ND + jc]);
+            put_key(S.K, k, l, m);
+        }
+    } else {
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int j = warp; j < n_empty; j += kThreadsB / 32) {
+            const int k = S.elist[j] >> 16, l = S.elist[j] & 0xFFFF;
+            const unsigned m = large_fill_key_at(T, p, T.y0 - 4 + k, T.x0 - 4 + l, lane, bad);
+            if (lane == 0) put_key(S.K, k, l, m);
+        }
+    }
+    return !__syncthreads_or(bad);
+}
+
+// Steps 5-8 of one tile on keys, from the key box in S.E (region column l
+// at box column l + ko).  The fix pass moves the box into K: row pairs
+// (kp, kp + kHalf) of one column chunk per thread, two 8-byte loads and four
+// byte permutes per chunk, out-of-frame positions zeroed, step 5 applied
+// from the column tops, empty pixels recorded (step 6).  Returns false,
+// having stored nothing, when a value the tile needs is off the key grid.
+template <bool kFill>
+__device__ bool tile_keys(const Tile& T, const StageBParams& p, const MainSmem& S, int t, int* worklist,
+                          bool ext_tile)
+{
+    const int tid = threadIdx.x, H = T.fd.H, W = T.fd.W;
+    const unsigned short* Ek = reinterpret_cast<const unsigned short*>(S.E);
+    unsigned* K = S.K;
+    const int ko = (T.x0 - 4) - key_box_x(T.x0);
+    unsigned mx = 0u;  // packed maximum of the keys this thread moved
+    if (tid < kRowGroups * kChunksPerRow) {
+        const int g = tid / kChunksPerRow, q = tid - g * kChunksPerRow;
+        const int xs = T.x0 - 4 + 4 * q;
+        const int ncol = (xs >= 0 && xs < W) ? min(4, W - xs) : 0;  // in-frame columns of the chunk
+        const unsigned m0 = (ncol > 0 ? 0xFFFFu : 0u) | (ncol > 1 ? 0xFFFF0000u : 0u);
+        const unsigned m1 = (ncol > 2 ? 0xFFFFu : 0u) | (ncol > 3 ? 0xFFFF0000u : 0u);
+        const int klo = max(0, 4 - T.y0), khi = min(kER, H - T.y0 + 4);  // in-frame region rows
+        int ct[4];
+        unsigned ck[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            ct[e] = ext_tile ? S.ctop[4 * q + e] : kNoTop;
+            ck[e] = S.ctv[4 * q + e];
+        }
+        const unsigned short* src = Ek + ko + 4 * q;
+        for (int kp = g; kp < kPR; kp += kRowGroups) {
+            const int kb = kp + kHalf;
+            uint2 a = *reinterpret_cast<const uint2*>(src + kp * kKeyBoxW);
+            uint2 b = *reinterpret_cast<const uint2*>(src + kb * kKeyBoxW);
+            const bool ina = kp >= klo && kp < khi, inb = kb >= klo && kb < khi;
+            const unsigned ma0 = ina ? m0 : 0u, ma1 = ina ? m1 : 0u;
+            const unsigned mb0 = inb ? m0 : 0u, mb1 = inb ? m1 : 0u;
+            a.x &= ma0;
+            a.y &= ma1;
+            b.x &= mb0;
+            b.y &= mb1;
+            if (ext_tile) {  // step 5: a position above its column's top takes the top's key
+                const int ya = T.y0 - 4 + kp, yb = ya + kHalf;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const unsigned sh = (e & 1) * 16, hm = 0xFFFFu << sh, kv = ck[e] << sh;
+                    unsigned& wa = e < 2 ? a.x : a.y;
+                    unsigned& wb = e < 2 ? b.x : b.y;
+                    if (((e < 2 ? ma0 : ma1) & hm) && above_top(p, ya, ct[e])) wa = (wa & ~hm) | kv;
+                    if (((e < 2 ? mb0 : mb1) & hm) && above_top(p, yb, ct[e])) wb = (wb & ~hm) | kv;
+                }
+            }
+            mx = __vimax3_u16x2(mx, a.x, a.y);
+            mx = __vimax3_u16x2(mx, b.x, b.y);
+            if (kFill) {
+                // empty in-frame positions (key <= kEmptyKeyMax); out-of-frame ones
+                // are lifted out of the way.  Most chunks hold none: their
+                // smallest key tells
+                const unsigned la0 = a.x | ~ma0, la1 = a.y | ~ma1, lb0 = b.x | ~mb0, lb1 = b.y | ~mb1;
+                const unsigned mn = __vminu2(__vimin3_u16x2(la0, la1, lb0), lb1);
+                if ((mn & 0xFFFFu) <= kEmptyKeyMax || (mn >> 16) <= kEmptyKeyMax) {
+                    unsigned ea = 0u, eb = 0u;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const unsigned sh = (e & 1) * 16;
+                        ea |= ((((e < 2 ? la0 : la1) >> sh) & 0xFFFFu) <= kEmptyKeyMax ? 1u : 0u) << e;
+                        eb |= ((((e < 2 ? lb0 : lb1) >> sh) & 0xFFFFu) <= kEmptyKeyMax ? 1u : 0u) << e;
+                    }
+                    // rows kHalf .. kPR - 1 appear in both halves: count them once
+                    if (ea) note_empties(S, kp, q, ea);
+                    if (eb && kp >= kPR - kHalf) note_empties(S, kb, q, eb);
+                }
+            }
+            *reinterpret_cast<uint4*>(K + kp * kES + 4 * q) =
+                make_uint4(__byte_perm(a.x, b.x, 0x5410), __byte_perm(a.x, b.x, 0x7632),
+                           __byte_perm(a.y, b.y, 0x5410), __byte_perm(a.y, b.y, 0x7632));
+        }
+    }
+    if (__syncthreads_or((mx & 0xFFFFu) > kKeyMax || (mx >> 16) > kKeyMax)) return false;
+    const int n_empty = kFill ? *S.ecount : 0;  // no empties are counted without step 6
+    if (p.stop == kStopExtend) {
+        store_keys_tile(T, K);
+        return true;
+    }
+    if (n_empty > p.sparse_fill_max) {
+        if (tid == 0) {
+            const int slot = atomicAdd(worklist, 1);
+            worklist[3 + slot] = t;
+        }
+        return true;
+    }
+    if (n_empty > 0 && !fill_keys(T, p, S, n_empty)) return false;
+    // replicate the frame border into the two rows / columns beyond each
+    // edge (the median's rule; farther ones feed only mirrored outputs)
+    if (T.y0 < 2 || T.x0 < 2 || T.y0 + kTBH + 2 > H || T.x0 + kTBW + 2 > W) {
+        const Ring ring = ring_of(T, 4, kER, kEC);
+        for (int i = tid; i < ring.count(); i += kThreadsB) {
+            int k, l;
+            ring.at(i, k, l);
+            const int y = T.y0 - 4 + k, x = T.x0 - 4 + l;
+            if (y < -2 || y >= H + 2 || x < -2 || x >= W + 2) continue;
+            put_key(K, k, l, key_at(K, clampi(y, H) - (T.y0 - 4), clampi(x, W) - (T.x0 - 4)));
+        }
+    }
+    __syncthreads();
+    if (p.stop == kStopFillLarge) store_keys_tile(T, K);
+    else median_blur_store(T, p, nullptr, K, true, S.Mf, S.Mk, S.E);
+    return true;
+}
+
+// Steps 5-8 of one tile on floats, for a tile with some value off the key
+// grid: E from C's keys and the float map, then the same steps on floats
+// (the median and blur still run on keys when the region's values allow).
+template <bool kFill>
+__device__ void tile_floats(const Tile& T, const StageBParams& p, const MainSmem& S, int t, int* worklist,
+                            bool ext_tile)
+{
+    const int tid = threadIdx.x, H = T.fd.H, W = T.fd.W;
+    float* E = S.E;
+    unsigned* K = S.K;
+    unsigned short* Mk = S.Mk;
+    float* Mf = S.Mf;
+    float* scratch = S.scratch;
+    const int* ctop = S.ctop;
+    int* elist = S.elist;
+    int* ecount = S.ecount;
+    unsigned* ecols = S.ecols;
+    int* ecol_list = S.ecol_list;
+    int* ecol_idx = S.ecol_idx;
+    int* ebox = S.ebox;
+    __syncthreads();  // the key path is done with every buffer
+    reset_empties(S);
+    tops_to_floats(T, T.x0 - 4, kEC, S.ctop, S.ctv);
+    const float* cval = reinterpret_cast<const float*>(S.ctv);
+    for (int i = tid; i < kER * kEC; i += kThreadsB) {
+        const int k = i / kEC, l = i - k * kEC;
+        const int y = T.y0 - 4 + k, x = T.x0 - 4 + l;
+        if (y >= 0 && y < H && x >= 0 && x < W) E[k * kES + l] = c_at(T.fd, y, x);
+    }
+    __syncthreads();
+    // step 5 in place, empty pixels, packed keys: row pairs (kp, kp + kHalf)
+    // of one column chunk per thread
+    bool keys_ok = true;
+    if (tid < kRowGroups * kChunksPerRow) {
+        const int g = tid / kChunksPerRow, q = tid - g * kChunksPerRow;
+        const int xs = T.x0 - 4 + 4 * q;
+        const int ncol = (xs >= 0 && xs < W) ? min(4, W - xs) : 0;  // in-frame columns of the chunk
+        int ct[4];
+        float cv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            ct[e] = ext_tile ? ctop[4 * q + e] : kNoTop;
+            cv[e] = ext_tile ? cval[4 * q + e] : 0.0f;
+        }
+        for (int kp = g; kp < kPR; kp += kRowGroups) {
+            unsigned key[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = kp + h * kHalf;
+                const int y = T.y0 - 4 + k;
+                if (ncol == 0 || y < 0 || y >= H) continue;
+                float4* cell = reinterpret_cast<float4*>(E + k * kES + 4 * q);
+                const float4 c4 = *cell;
+                float v[4] = {c4.x, c4.y, c4.z, c4.w};
+                if (ext_tile) {
+                    bool moved = false;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (above_top(p, y, ct[e])) {
+                            v[e] = cv[e];
+                            moved = true;
+                        }
+                    if (moved) *cell = make_float4(v[0], v[1], v[2], v[3]);
+                }
+                unsigned em = 0u;  // empty in-frame columns of this chunk row
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (e < ncol) key[h][e] = key_of(v[e], keys_ok);
+                // most chunks hold no empty pixel: test their smallest value first
+                // (out-of-frame columns of a chunk at the right edge hold pixels
+                // of the next row's start or padding, and are masked below)
+                if (is_empty(fminf(fminf(v[0], v[1]), fminf(v[2], v[3]))))
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (e < ncol) em |= (is_empty(v[e]) ? 1u : 0u) << e;
+                // rows kHalf .. kPR - 1 appear in both halves: count them once
+                const bool counted = (h == 0) || (kp >= kPR - kHalf);
+                if (em && counted && kFill) {
+                    const int slot0 = atomicAdd(ecount, __popc(em));
+                    int slot = slot0;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if ((em >> e) & 1u) {
+                            if (slot < kMaxSparseFill) elist[slot] = (k << 16) | (4 * q + e);
+                            ++slot;
+                        }
+                    atomicMin(ebox + 0, k);
+                    atomicMax(ebox + 1, k);
+                    atomicOr(ecols + ((4 * q) >> 5), em << ((4 * q) & 31));
+                }
+            }
+            *reinterpret_cast<uint4*>(K + kp * kES + 4 * q) =
+                make_uint4(key[0][0] | (key[1][0] << 16), key[0][1] | (key[1][1] << 16),
+                           key[0][2] | (key[1][2] << 16), key[0][3] | (key[1][3] << 16));
+        }
+    }
+    __syncthreads();
+    const int n_empty = kFill ? *ecount : 0;  // no empties are counted without step 6
+
+    auto store_tile = [&](const float* buf) {
+        for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
+            const int a = i / kTBW, b = i - a * kTBW;
+            const int y = T.y0 + a, x = T.x0 + b;
+            if (y < H && x < W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = buf[(a + 4) * kES + b + 4];
+        }
+    };
+    if (p.stop == kStopExtend) {
+        store_tile(E);
+    } else if (n_empty > p.sparse_fill_max) {
+        if (tid == 0) {
+            const int slot = atomicAdd(worklist, 1);
+            worklist[3 + slot] = t;
+        }
+    } else {
+        if (n_empty > 0) {
+            // step 6 at the few empty pixels.  E and K are only written here (at
+            // empty pixels); the window maxima read C.
+            const int Rl = p.large_radius;
+            // their columns, in order (warps 0-2 take the bitmap's words)
+            const unsigned w0 = ecols[0], w1 = ecols[1], w2 = ecols[2];
+            if (tid < 96) {
+                const int w = tid >> 5, lane = tid & 31;
+                const unsigned bits = w == 0 ? w0 : (w == 1 ? w1 : w2);
+                const int pos = (w > 0 ? __popc(w0) : 0) + (w > 1 ? __popc(w1) : 0) +
+                                __popc(bits & ((1u << lane) - 1u));
+                if ((bits >> lane) & 1u) {
+                    ecol_list[pos] = tid;
+                    ecol_idx[tid] = pos;
+                }
+            }
+            const int ND = __popc(w0) + __popc(w1) + __popc(w2);
+            const int lmin = w0 ? __ffs(w0) - 1 : (w1 ? 31 + __ffs(w1) : 63 + __ffs(w2));
+            const int lmax = w2 ? 95 - __clz(w2) : (w1 ? 63 - __clz(w1) : 31 - __clz(w0));
+            // the union of their windows: frame rows [by0, by1], columns [bx0, bx1]
+            const int by0 = max(0, T.y0 - 4 + ebox[0] - Rl), by1 = min(H - 1, T.y0 - 4 + ebox[1] + Rl);
+            const int bx0 = max(0, T.x0 - 4 + lmin - Rl), bx1 = min(W - 1, T.x0 - 4 + lmax + Rl);
+            const int BR = by1 - by0 + 1, BC = bx1 - bx0 + 1;
+            // row maxima at the ND empty columns (BR x ND), each column's top
+            // and top value (2 x BC), then the box, which streams through the
+            // rest of the scratch in bands of rows
+            const int rm = BR * ND;
+            const bool small = rm + 3 * BC <= kSmallScratch;
+            const bool big = !small && rm + 3 * BC <= kBigScratch;
+            if (small || big) {
+                float* rmax = small ? scratch : reinterpret_cast<float*>(K);
+                int* btop = reinterpret_cast<int*>(rmax + rm);
+                float* btv = reinterpret_cast<float*>(btop + BC);
+                float* band = btv + BC;
+                const int RB = min(BR, ((small ? kSmallScratch : kBigScratch) - rm - 2 * BC) / BC);
+                for (int c = tid; c < BC; c += kThreadsB) {
+                    const int x = bx0 + c;
+                    int top = kNoTop;
+                    float tv = 0.0f;
+                    if (p.extend_top) {
+                        const unsigned long long t2 = __ldg(T.fd.top + x);
+                        if (t2 != kNoTopPacked) {
+                            top = (int)(t2 >> 32);
+                            tv = top_value(T.fd, top, (unsigned)t2, x);
+                        }
+                    }
+                    btop[c] = top;
+                    btv[c] = tv;
+                }
+                __syncthreads();
+                for (int r0 = 0; r0 < BR; r0 += RB) {
+                    const int nb = min(RB, BR - r0);
+                    // the band of E (step 5 applied): inside the tile's region from
+                    // shared memory, elsewhere from C ...
+                    for (int i = tid; i < nb * BC; i += kThreadsB) {
+                        const int r = i / BC, c = i - r * BC;
+                        const int k = by0 + r0 + r - (T.y0 - 4), l = bx0 + c - (T.x0 - 4);
+                        band[i] = ((unsigned)k < (unsigned)kER && (unsigned)l < (unsigned)kEC)
+                                      ? E[k * kES + l]
+                                      : extended(T, p, by0 + r0 + r, bx0 + c, btop[c], btv[c]);
+                    }
+                    __syncthreads();
+                    // ... its row maxima over the window width at the empty columns
+                    for (int i = tid; i < nb * ND; i += kThreadsB) {
+                        const int r = i / ND, j = i - r * ND;
+                        const int c = T.x0 - 4 + ecol_list[j];
+                        const int lo = max(c - Rl, bx0) - bx0, hi = min(c + Rl, bx1) - bx0;
+                        float m = ninf();
+                        for (int x = lo; x <= hi; ++x) m = fmaxf(m, band[r * BC + x]);
+                        rmax[(r0 + r) * ND + j] = m;
+                    }
+                    __syncthreads();
+                }
+                // column maxima at each empty pixel
+                for (int j = tid; j < n_empty; j += kThreadsB) {
+                    const int k = elist[j] >> 16, l = elist[j] & 0xFFFF;
+                    const int y = T.y0 - 4 + k;
+                    const int lo = max(y - Rl, by0) - by0, hi = min(y + Rl, by1) - by0;
+                    const int jc = ecol_idx[l];
+                    float m = ninf();
+                    for (int r = lo; r <= hi; ++r) m = fmaxf(m, rmax[r * ND + jc]);
+                    E[k * kES + l] = m;
+                    if (small) put_key(K, k, l, key_of(m, keys_ok));
+                }
+                if (big) {  // K held the row maxima: the keys again, from E
+                    __syncthreads();
+                    keys_ok = true;
+                    build_keys(T, E, K, keys_ok);
+                }
+            } else {
+                // too wide for the box: one warp per pixel, windows read from C
+                const int warp = tid >> 5, lane = tid & 31;
+                for (int j = warp; j < n_empty; j += kThreadsB / 32) {
+                    const int k = elist[j] >> 16, l = elist[j] & 0xFFFF;
+                    const float m = large_fill_at(T, p, T.y0 - 4 + k, T.x0 - 4 + l, lane);
+                    if (lane == 0) {
+                        E[k * kES + l] = m;
+                        put_key(K, k, l, key_of(m, keys_ok));
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // replicate the frame border into the two rows / columns beyond each
+        // edge (the median's rule; farther ones feed only mirrored outputs)
+        if (T.y0 < 2 || T.x0 < 2 || T.y0 + kTBH + 2 > H || T.x0 + kTBW + 2 > W) {
+            const Ring ring = ring_of(T, 4, kER, kEC);
+            for (int i = tid; i < ring.count(); i += kThreadsB) {
+                int k, l;
+                ring.at(i, k, l);
+                const int y = T.y0 - 4 + k, x = T.x0 - 4 + l;
+                if (y < -2 || y >= H + 2 || x < -2 || x >= W + 2) continue;
+                const int sk = clampi(y, H) - (T.y0 - 4), sl = clampi(x, W) - (T.x0 - 4);
+                const float v = E[sk * kES + sl];
+                E[k * kES + l] = v;
+                put_key(K, k, l, key_of(v, keys_ok));
+            }
+        }
+        const bool keys = __syncthreads_and(keys_ok);
+        if (p.stop == kStopFillLarge) store_tile(E);
+        else median_blur_store(T, p, E, K, keys, Mf, Mk, E);
+    }
+}
+
 // Phase 1, persistent: CTA i starts with tile i and then takes the next
 // unclaimed tile from a counter.  One region buffer and 16-bit median output
 // (45 KB of shared memory in all) let five CTAs share an SM: while one waits
-// for its region (cp.async) the others compute, which hides the copy better
-// than a second buffer would (that costs CTAs per SM).  kFill: step 6 on
-// (one instantiation per setting, so that neither carries the other's code:
-// the kernel's speed is sensitive to its instruction footprint).
+// for its region the others compute, which hides the copy better than a
+// second buffer would (that costs CTAs per SM).  A tile runs on keys (C's
+// key box, half the bytes of floats, moved into the median's packed layout
+// by byte permutes) unless a value it needs is off the key grid, then on
+// floats.  kFill: step 6 on (one instantiation per setting, so that neither
+// carries the other's code: the kernel's speed is sensitive to its
+// instruction footprint).
 template <bool kFill>
 __global__ void __launch_bounds__(kThreadsB, 5)
 stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles, StageBParams p,
@@ -851,19 +1404,21 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
     wait_previous_kernel();  // C, the tops and counters of stage A
     allow_next_kernel();
     extern __shared__ __align__(128) float smem[];  // the tensor copy wants 128-byte alignment
-    float* Ebuf = smem;                                                      // the region
-    unsigned* K = reinterpret_cast<unsigned*>(smem + kER * kES);             // packed keys
-    unsigned short* Mk = reinterpret_cast<unsigned short*>(K + kPR * kES);   // median output, keys
-    float* Mf = reinterpret_cast<float*>(K);                                 // median output, floats
-    float* scratch = reinterpret_cast<float*>(Mk);  // kSmallScratch floats, idle until the median
-    int* ctop = reinterpret_cast<int*>(scratch + kSmallScratch);
-    float* cval = reinterpret_cast<float*>(ctop + kEC);
-    int* elist = reinterpret_cast<int*>(cval + kEC);
-    int* ecount = elist + kMaxSparseFill;
-    unsigned* ecols = reinterpret_cast<unsigned*>(ecount + 4);  // bitmap of region columns with empties
-    int* ecol_list = reinterpret_cast<int*>(ecols + 4);          // those columns, in order
-    int* ecol_idx = ecol_list + kEC;                             // region column -> position in the list
-    __shared__ int ebox[2];  // region rows spanned by the empty pixels: kmin, kmax
+    __shared__ int ebox[2];
+    MainSmem S;
+    S.E = smem;
+    S.K = reinterpret_cast<unsigned*>(smem + kER * kES);
+    S.Mk = reinterpret_cast<unsigned short*>(S.K + kPR * kES);
+    S.Mf = reinterpret_cast<float*>(S.K);
+    S.scratch = reinterpret_cast<float*>(S.Mk);
+    S.ctop = reinterpret_cast<int*>(S.scratch + kSmallScratch);
+    S.ctv = reinterpret_cast<unsigned*>(S.ctop + kEC);
+    S.elist = reinterpret_cast<int*>(S.ctv + kEC);
+    S.ecount = S.elist + kMaxSparseFill;
+    S.ecols = reinterpret_cast<unsigned*>(S.ecount + 4);
+    S.ecol_list = reinterpret_cast<int*>(S.ecols + 4);
+    S.ecol_idx = S.ecol_list + kEC;
+    S.ebox = ebox;
 
     const int tid = threadIdx.x;
     int t = blockIdx.x;
@@ -874,22 +1429,16 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
     unsigned mbar_parity = 0;
     if (p.tma && tid == 0) mbar_init(&s_mbar);
     __syncthreads();
-    for (int it = 0;; ++it) {
-        float* E = Ebuf;
+    for (;;) {
         const int H = T.fd.H, W = T.fd.W;
         if (p.tma) {
-            if (tid == 0) tma_region(E, &cmap, T.x0 - 4, T.y0 - 4, T.f, &s_mbar);
+            if (tid == 0) tma_region(S.E, &cmap, key_box_x(T.x0), T.y0 - 4, T.f, &s_mbar);
         } else {
-            issue_region(T, E);
+            issue_region_keys(T, reinterpret_cast<unsigned short*>(S.E));
         }
-        load_tops(T, p, T.x0 - 4, kEC, ctop, cval);
-        if (tid == 0) {
-            *ecount = 0;
-            ebox[0] = 1 << 20;
-            ebox[1] = -1;
-            ecols[0] = ecols[1] = ecols[2] = 0u;
-            s_next = (int)gridDim.x + atomicAdd(worklist + 1, 1);
-        }
+        load_tops(T, p, T.x0 - 4, kEC, S.ctop, S.ctv);
+        reset_empties(S);
+        if (tid == 0) s_next = (int)gridDim.x + atomicAdd(worklist + 1, 1);
         if (p.tma) {
             const bool arrived = mbar_wait(&s_mbar, mbar_parity);
             mbar_parity ^= 1u;
@@ -901,14 +1450,15 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
             cp_async_wait_all();
             __syncthreads();
         }
-        const bool ext_tile = __syncthreads_or(tid < kEC && ctop[tid] != kNoTop && ctop[tid] > T.y0 - 4);
+        const bool ext_tile =
+            __syncthreads_or(tid < kEC && S.ctop[tid] != kNoTop && S.ctop[tid] > T.y0 - 4);
         const int tn = s_next;
         const bool more = tn < total_tiles;
 
         // a region entirely above its columns' tops: one row does for all
         const bool const_tile = __syncthreads_and(
             p.extend_top && p.extend_rows < 0 &&
-            (tid >= kEC || (ctop[tid] != kNoTop && ctop[tid] > T.y0 - 4 + kER - 1)));
+            (tid >= kEC || (S.ctop[tid] != kNoTop && S.ctop[tid] > T.y0 - 4 + kER - 1)));
         // without step 6, a region empty in every column down to its last row
         // has an empty median everywhere (every window holds only empty
         // values): the tile's output is 0
@@ -916,216 +1466,13 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
                                __syncthreads_and(tid >= kEC || column_empty_to(T, p, clampi(T.x0 - 4 + tid, W),
                                                                                min(H - 1, T.y0 - 4 + kER - 1)));
         if (const_tile) {
-            constant_tile_store(T, p, cval, scratch);
+            tops_to_floats(T, T.x0 - 4, kEC, S.ctop, S.ctv);
+            __syncthreads();
+            constant_tile_store(T, p, reinterpret_cast<const float*>(S.ctv), S.scratch);
         } else if (void_tile) {
             store_zero_tile(T);
-        } else {
-        // step 5 in place, empty pixels, packed keys: row pairs (kp, kp + kHalf)
-        // of one column chunk per thread
-        bool keys_ok = true;
-        if (tid < kRowGroups * kChunksPerRow) {
-            const int g = tid / kChunksPerRow, q = tid - g * kChunksPerRow;
-            const int xs = T.x0 - 4 + 4 * q;
-            const int ncol = (xs >= 0 && xs < W) ? min(4, W - xs) : 0;  // in-frame columns of the chunk
-            int ct[4];
-            float cv[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                ct[e] = ext_tile ? ctop[4 * q + e] : kNoTop;
-                cv[e] = ext_tile ? cval[4 * q + e] : 0.0f;
-            }
-            for (int kp = g; kp < kPR; kp += kRowGroups) {
-                unsigned key[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int k = kp + h * kHalf;
-                    const int y = T.y0 - 4 + k;
-                    if (ncol == 0 || y < 0 || y >= H) continue;
-                    float4* cell = reinterpret_cast<float4*>(E + k * kES + 4 * q);
-                    const float4 c4 = *cell;
-                    float v[4] = {c4.x, c4.y, c4.z, c4.w};
-                    if (ext_tile) {
-                        bool moved = false;
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (above_top(p, y, ct[e])) {
-                                v[e] = cv[e];
-                                moved = true;
-                            }
-                        if (moved) *cell = make_float4(v[0], v[1], v[2], v[3]);
-                    }
-                    unsigned em = 0u;  // empty in-frame columns of this chunk row
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (e < ncol) key[h][e] = key_of(v[e], keys_ok);
-                    // most chunks hold no empty pixel: test their smallest value first
-                    // (out-of-frame columns of a chunk at the right edge hold pixels
-                    // of the next row's start or padding, and are masked below)
-                    if (is_empty(fminf(fminf(v[0], v[1]), fminf(v[2], v[3]))))
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (e < ncol) em |= (is_empty(v[e]) ? 1u : 0u) << e;
-                    // rows kHalf .. kPR - 1 appear in both halves: count them once
-                    const bool counted = (h == 0) || (kp >= kPR - kHalf);
-                    if (em && counted && kFill) {
-                        const int slot0 = atomicAdd(ecount, __popc(em));
-                        int slot = slot0;
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if ((em >> e) & 1u) {
-                                if (slot < kMaxSparseFill) elist[slot] = (k << 16) | (4 * q + e);
-                                ++slot;
-                            }
-                        atomicMin(ebox + 0, k);
-                        atomicMax(ebox + 1, k);
-                        atomicOr(ecols + ((4 * q) >> 5), em << ((4 * q) & 31));
-                    }
-                }
-                *reinterpret_cast<uint4*>(K + kp * kES + 4 * q) =
-                    make_uint4(key[0][0] | (key[1][0] << 16), key[0][1] | (key[1][1] << 16),
-                               key[0][2] | (key[1][2] << 16), key[0][3] | (key[1][3] << 16));
-            }
-        }
-        __syncthreads();
-        const int n_empty = kFill ? *ecount : 0;  // no empties are counted without step 6
-
-        auto store_tile = [&](const float* buf) {
-            for (int i = tid; i < kTBH * kTBW; i += kThreadsB) {
-                const int a = i / kTBW, b = i - a * kTBW;
-                const int y = T.y0 + a, x = T.x0 + b;
-                if (y < H && x < W) T.fd.out[(size_t)y * T.fd.out_pitch + x] = buf[(a + 4) * kES + b + 4];
-            }
-        };
-        if (p.stop == kStopExtend) {
-            store_tile(E);
-        } else if (n_empty > p.sparse_fill_max) {
-            if (tid == 0) {
-                const int slot = atomicAdd(worklist, 1);
-                worklist[3 + slot] = t;
-            }
-        } else {
-            if (n_empty > 0) {
-                // step 6 at the few empty pixels.  E and K are only written here (at
-                // empty pixels); the window maxima read C.
-                const int Rl = p.large_radius;
-                // their columns, in order (warps 0-2 take the bitmap's words)
-                const unsigned w0 = ecols[0], w1 = ecols[1], w2 = ecols[2];
-                if (tid < 96) {
-                    const int w = tid >> 5, lane = tid & 31;
-                    const unsigned bits = w == 0 ? w0 : (w == 1 ? w1 : w2);
-                    const int pos = (w > 0 ? __popc(w0) : 0) + (w > 1 ? __popc(w1) : 0) +
-                                    __popc(bits & ((1u << lane) - 1u));
-                    if ((bits >> lane) & 1u) {
-                        ecol_list[pos] = tid;
-                        ecol_idx[tid] = pos;
-                    }
-                }
-                const int ND = __popc(w0) + __popc(w1) + __popc(w2);
-                const int lmin = w0 ? __ffs(w0) - 1 : (w1 ? 31 + __ffs(w1) : 63 + __ffs(w2));
-                const int lmax = w2 ? 95 - __clz(w2) : (w1 ? 63 - __clz(w1) : 31 - __clz(w0));
-                // the union of their windows: frame rows [by0, by1], columns [bx0, bx1]
-                const int by0 = max(0, T.y0 - 4 + ebox[0] - Rl), by1 = min(H - 1, T.y0 - 4 + ebox[1] + Rl);
-                const int bx0 = max(0, T.x0 - 4 + lmin - Rl), bx1 = min(W - 1, T.x0 - 4 + lmax + Rl);
-                const int BR = by1 - by0 + 1, BC = bx1 - bx0 + 1;
-                // row maxima at the ND empty columns (BR x ND), each column's top
-                // and top value (2 x BC), then the box, which streams through the
-                // rest of the scratch in bands of rows
-                const int rm = BR * ND;
-                const bool small = rm + 3 * BC <= kSmallScratch;
-                const bool big = !small && rm + 3 * BC <= kBigScratch;
-                if (small || big) {
-                    float* rmax = small ? scratch : reinterpret_cast<float*>(K);
-                    int* btop = reinterpret_cast<int*>(rmax + rm);
-                    float* btv = reinterpret_cast<float*>(btop + BC);
-                    float* band = btv + BC;
-                    const int RB = min(BR, ((small ? kSmallScratch : kBigScratch) - rm - 2 * BC) / BC);
-                    for (int c = tid; c < BC; c += kThreadsB) {
-                        const int x = bx0 + c;
-                        int top = kNoTop;
-                        float tv = 0.0f;
-                        if (p.extend_top) {
-                            const unsigned long long t2 = __ldg(T.fd.top + x);
-                            if (t2 != kNoTopPacked) {
-                                top = (int)(t2 >> 32);
-                                tv = __uint_as_float((unsigned)t2);
-                            }
-                        }
-                        btop[c] = top;
-                        btv[c] = tv;
-                    }
-                    __syncthreads();
-                    for (int r0 = 0; r0 < BR; r0 += RB) {
-                        const int nb = min(RB, BR - r0);
-                        // the band of E (step 5 applied): inside the tile's region from
-                        // shared memory, elsewhere from C ...
-                        for (int i = tid; i < nb * BC; i += kThreadsB) {
-                            const int r = i / BC, c = i - r * BC;
-                            const int k = by0 + r0 + r - (T.y0 - 4), l = bx0 + c - (T.x0 - 4);
-                            band[i] = ((unsigned)k < (unsigned)kER && (unsigned)l < (unsigned)kEC)
-                                          ? E[k * kES + l]
-                                          : extended(T, p, by0 + r0 + r, bx0 + c, btop[c], btv[c]);
-                        }
-                        __syncthreads();
-                        // ... its row maxima over the window width at the empty columns
-                        for (int i = tid; i < nb * ND; i += kThreadsB) {
-                            const int r = i / ND, j = i - r * ND;
-                            const int c = T.x0 - 4 + ecol_list[j];
-                            const int lo = max(c - Rl, bx0) - bx0, hi = min(c + Rl, bx1) - bx0;
-                            float m = ninf();
-                            for (int x = lo; x <= hi; ++x) m = fmaxf(m, band[r * BC + x]);
-                            rmax[(r0 + r) * ND + j] = m;
-                        }
-                        __syncthreads();
-                    }
-                    // column maxima at each empty pixel
-                    for (int j = tid; j < n_empty; j += kThreadsB) {
-                        const int k = elist[j] >> 16, l = elist[j] & 0xFFFF;
-                        const int y = T.y0 - 4 + k;
-                        const int lo = max(y - Rl, by0) - by0, hi = min(y + Rl, by1) - by0;
-                        const int jc = ecol_idx[l];
-                        float m = ninf();
-                        for (int r = lo; r <= hi; ++r) m = fmaxf(m, rmax[r * ND + jc]);
-                        E[k * kES + l] = m;
-                        if (small) put_key(K, k, l, key_of(m, keys_ok));
-                    }
-                    if (big) {  // K held the row maxima: the keys again, from E
-                        __syncthreads();
-                        keys_ok = true;
-                        build_keys(T, E, K, keys_ok);
-                    }
-                } else {
-                    // too wide for the box: one warp per pixel, windows read from C
-                    const int warp = tid >> 5, lane = tid & 31;
-                    for (int j = warp; j < n_empty; j += kThreadsB / 32) {
-                        const int k = elist[j] >> 16, l = elist[j] & 0xFFFF;
-                        const float m = large_fill_at(T, p, T.y0 - 4 + k, T.x0 - 4 + l, lane);
-                        if (lane == 0) {
-                            E[k * kES + l] = m;
-                            put_key(K, k, l, key_of(m, keys_ok));
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-            // replicate the frame border into the two rows / columns beyond each
-            // edge (the median's rule; farther ones feed only mirrored outputs)
-            if (T.y0 < 2 || T.x0 < 2 || T.y0 + kTBH + 2 > H || T.x0 + kTBW + 2 > W) {
-                const Ring ring = ring_of(T, 4, kER, kEC);
-                for (int i = tid; i < ring.count(); i += kThreadsB) {
-                    int k, l;
-                    ring.at(i, k, l);
-                    const int y = T.y0 - 4 + k, x = T.x0 - 4 + l;
-                    if (y < -2 || y >= H + 2 || x < -2 || x >= W + 2) continue;
-                    const int sk = clampi(y, H) - (T.y0 - 4), sl = clampi(x, W) - (T.x0 - 4);
-                    const float v = E[sk * kES + sl];
-                    E[k * kES + l] = v;
-                    put_key(K, k, l, key_of(v, keys_ok));
-                }
-            }
-            const bool keys = __syncthreads_and(keys_ok);
-            if (p.stop == kStopFillLarge) store_tile(E);
-            else median_blur_store(T, p, E, K, keys, Mf, Mk, E);
-        }
+        } else if (!tile_keys<kFill>(T, p, S, t, worklist, ext_tile)) {
+            tile_floats<kFill>(T, p, S, t, worklist, ext_tile);
         }
 
         __syncthreads();
@@ -1158,7 +1505,8 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
     float* F = G + GR * GS;
     float* M = G;
     int* ctop = reinterpret_cast<int*>(F + kER * kES);
-    float* cval = reinterpret_cast<float*>(ctop + GC);
+    unsigned* ctv = reinterpret_cast<unsigned*>(ctop + GC);
+    const float* cval = reinterpret_cast<const float*>(ctv);  // after tops_to_floats
     float* R = F;
 
     const int count = worklist[0];
@@ -1168,7 +1516,7 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
         const Tile T = tile_of(frames, n_frames, worklist[3 + w], p.row_stride);
         const int H = T.fd.H, W = T.fd.W;
         const int gy = T.y0 - 4 - Rl, gx = T.x0 - 4 - Rl;  // frame position of the wide region's (0, 0)
-        load_tops(T, p, gx, GC, ctop, cval);
+        load_tops(T, p, gx, GC, ctop, ctv);
         // a wide region empty in every column: every window of step 6 holds
         // only empty values, so does the median, and the output is 0
         if (p.stop == kStopFull) {
@@ -1183,11 +1531,10 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
                 continue;
             }
         }
-        // E over the wide region: C by 16-byte asynchronous copies (chunk j
-        // of a row is frame columns gxa + 4 j .. + 3), the few chunks across
-        // the frame's left or right edge by plain loads, -inf outside it
-        const int gxa = (gx >> 2) << 2, sh = gx - gxa;
-        const int nch = (sh + GC + 3) >> 2;
+        tops_to_floats(T, gx, GC, ctop, ctv);
+        // E over the wide region: C from its keys (and the float map), -inf
+        // outside the frame
+        constexpr int sh = 0;  // frame column gx at row offset 0
         for (int k = warp; k < GR; k += kThreadsB / 32) {
             const int y = gy + k;
             float* grow = G + k * GS;
@@ -1195,20 +1542,11 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
                 for (int j = lane; j < GS; j += 32) grow[j] = ninf();
                 continue;
             }
-            const float* crow = T.fd.c + (size_t)y * T.fd.c_pitch;
-            for (int j = lane; j < nch; j += 32) {
-                const int x = gxa + 4 * j;
-                if (x >= 0 && x + 3 < W) {
-                    cp_async16(grow + 4 * j, crow + x);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        grow[4 * j + e] = (x + e >= 0 && x + e < W) ? crow[x + e] : ninf();
-                }
+            for (int j = lane; j < GC; j += 32) {
+                const int x = gx + j;
+                grow[j] = (x >= 0 && x < W) ? c_at(T.fd, y, x) : ninf();
             }
         }
-        cp_async_commit();
-        cp_async_wait_all();
         __syncthreads();
         // step 5: the rows above each in-frame column's top (within the cap)
         if (p.extend_top) {
@@ -1335,10 +1673,13 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
                                           dim3(kThreadsB), main_smem, stream, d_frames, n_frames, total_tiles, q,
                                           worklist, map, err);
     if (e != cudaSuccess || !p.large_fill_on || p.stop == kStopExtend) return e;
-    // as many CTAs per SM as shared memory holds, three at most (registers)
+    // as many CTAs per SM as shared memory and registers hold
     const size_t fill_smem = stage_b_fill_smem_bytes(p.large_radius);
-    int per_sm = (int)(233472 / (fill_smem + 1024));
-    if (per_sm > 3) per_sm = 3;
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_b_fill, kThreadsB, fill_smem) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
     if (per_sm < 1) per_sm = 1;
     int grid = per_sm * sm_count;
     if (grid > total_tiles) grid = total_tiles;

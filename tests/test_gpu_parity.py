@@ -76,13 +76,15 @@ def test_large_fill_sizes(ctx, large):
                 oracle.complete(f, large_fill=large, stop_after=stop), stop, f"large {large}")
 
 
+@pytest.mark.parametrize("quantize", [False, True])
 @pytest.mark.parametrize("hole", [14, 22, 44])
 @pytest.mark.parametrize("large", [15, 31, 51])
-def test_large_fill_holes(ctx, hole, large):
+def test_large_fill_holes(ctx, hole, large, quantize):
     # a dense map with square holes: after steps 1-5 a hole of side s keeps
     # roughly (s - 6)^2 empty pixels, so small holes take the per-pixel fill
-    # inside the main stage-B pass and large ones the worklist pass
-    f = synth.random_sparse(150, 250, 1.0, 3 + hole, 2.0, 80.0)
+    # inside the main stage-B pass and large ones the worklist pass (on keys
+    # when the depths are in 1/256 m steps, else on floats)
+    f = synth.random_sparse(150, 250, 1.0, 3 + hole, 2.0, 80.0, quantize=quantize)
     for (y, x) in ((60, 40), (95, 130), (70, 200), (140, 5), (3, 246)):
         f[max(0, y - hole // 2):y + hole // 2, max(0, x - hole // 2):x + hole // 2] = 0.0
     for stop in ("fill_large", "median", "full"):
@@ -134,6 +136,63 @@ def test_step6_scattered_empties(ctx, layout):
         compare(gpu_run(ctx, f[None], stop_after=stop)[0], oracle.complete(f, stop_after=stop), stop, layout)
 
 
+@pytest.mark.parametrize("layout", ["banded", "keys_rebuilt", "per_pixel"])
+@pytest.mark.parametrize("off_grid_near", [False, True])
+def test_step6_scattered_empties_on_keys(ctx, layout, off_grid_near):
+    # the same holes in a map of 1/256 m depths: the tile fills them on keys
+    # (the box through the idle region buffer, or one warp per pixel).  With
+    # off-grid depths placed beside the holes, a value the fill reads may be
+    # off the key grid: that tile then runs on floats instead
+    rects = {
+        "banded": [(62, 75, 64, 77), (62, 75, 104, 117), (104, 117, 64, 77)],
+        "keys_rebuilt": [(60, 71, 58, 118), (110, 121, 58, 118)],
+        "per_pixel": [(52, 63, 50, 130), (116, 127, 50, 130)],
+    }[layout]
+    f = synth.random_sparse(180, 250, 1.0, 5, 2.0, 80.0, quantize=True)
+    for (y0, y1, x0, x1) in rects:
+        f[y0:y1, x0:x1] = 0.0
+        if off_grid_near:
+            for (y, x) in ((y0 - 12, x0 - 12), (y1 + 11, x1 + 11), ((y0 + y1) // 2, x0 - 14)):
+                if 0 <= y < f.shape[0] and 0 <= x < f.shape[1]:
+                    f[y, x] = 50.0 + 1.0 / 1000
+    for stop in ("fill_large", "median", "full"):
+        compare(gpu_run(ctx, f[None], stop_after=stop)[0], oracle.complete(f, stop_after=stop), stop, layout)
+
+
+def _mixed_grid_frame(seed):
+    """A 32-beam frame of 1/256 m depths in which one rectangle of depths is
+    moved off that grid: the tiles that see it run on floats, the others on
+    keys, in one call."""
+    f = synth.make_frame(synth.FrameSpec(200, 400, 32, 0.06, 2.0, 80.0), seed)
+    sub = f[110:170, 130:250]
+    sub[sub > 0] += 1.0 / 1024
+    return f
+
+
+@pytest.mark.parametrize("stop", ["fill7", "extend", "fill_large", "median", "blur", "full"])
+def test_grid_and_off_grid_tiles_in_one_frame(ctx, stop):
+    frames = np.stack([_mixed_grid_frame(4321), synth.make_frame(synth.FrameSpec(200, 400, 32, 0.06), 17),
+                       _mixed_grid_frame(99)])
+    got = gpu_run(ctx, frames, stop_after=stop)
+    for i in range(len(frames)):
+        compare(got[i], oracle.complete(frames[i], stop_after=stop), stop, f"mixed {i}")
+
+
+def test_off_grid_column_tops(ctx):
+    # the topmost return of every seventh column moved off the 1/256 m grid:
+    # step 5 copies off-grid values up those columns (and, after steps 2-4,
+    # their neighbours), from the float map
+    f = synth.make_frame(SMALL, 91)
+    for x in range(0, SMALL.W, 7):
+        ys = np.nonzero(f[:, x])[0]
+        if len(ys):
+            f[ys[0], x] += 1.0 / 512 + 1.0 / 4096
+    for stop in ("extend", "fill_large", "median", "full"):
+        for variant in (dict(), dict(extend_rows=6)):
+            compare(gpu_run(ctx, f[None], stop_after=stop, **variant)[0],
+                    oracle.complete(f, stop_after=stop, **variant), stop, f"tops {variant}")
+
+
 @pytest.mark.parametrize("blur", ["gauss", "bilateral", "none"])
 @pytest.mark.parametrize("median", [True, False])
 def test_blur_variants(ctx, blur, median):
@@ -176,11 +235,14 @@ def test_empty_regions(ctx, variant, lone_point):
                     oracle.complete(frames[i], stop_after=stop, **variant), stop, f"{variant} frame {i}")
 
 
+@pytest.mark.parametrize("quantize", [False, True])
 @pytest.mark.parametrize("hw", [(1, 1), (1, 37), (41, 1), (2, 2), (3, 5), (7, 64), (33, 65),
                                 (64, 128), (65, 129), (5, 300)])
-def test_edge_shapes(ctx, hw):
-    f = synth.random_sparse(*hw, 0.2, hw[0] * 1000 + hw[1])
-    for stop in ("fill7", "median", "full"):
+def test_edge_shapes(ctx, hw, quantize):
+    # quantised: every tile on keys (the key box crosses the frame's edges);
+    # otherwise on floats
+    f = synth.random_sparse(*hw, 0.2, hw[0] * 1000 + hw[1], quantize=quantize)
+    for stop in ("fill7", "extend", "median", "full"):
         compare(gpu_run(ctx, f[None], stop_after=stop)[0], oracle.complete(f, stop_after=stop),
                 stop, str(hw))
 

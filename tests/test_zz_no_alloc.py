@@ -1,5 +1,5 @@
 """The allocation-free entry point, dc_complete_noalloc, against the regular
-dc_complete_uniform on the same frames.
+dc_complete_uniform on the same frames and against the CPU oracle.
 
 dc_complete_noalloc exists for callers that cannot allocate device memory
 at run time (fixed memory plans, plug-ins handed their buffers by a host
@@ -54,6 +54,58 @@ def test_noalloc_matches_regular_entry_point_twice(dc, stop, exact):
             _same(y_new.cpu().numpy(), y_ref.cpu().numpy(), exact)
     finally:
         ctx.close()
+
+
+def _oracle_case(dc, frames, exact_stop, **kw):
+    """dc_complete_noalloc on `frames` against the oracle, frame by frame."""
+    import oracle
+    x = torch.from_numpy(frames).cuda()
+    y = torch.full_like(x, -9.0)
+    n, H, W = frames.shape
+    p = dc.params(**kw)
+    dc.dc_complete_noalloc(x.data_ptr(), y.data_ptr(), n, H, W, p, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    for i in range(n):
+        _same(got[i], oracle.complete(frames[i], **kw), exact_stop)
+
+
+@pytest.mark.parametrize("stop", ["invert", "dilate", "close", "fill7", "extend", "fill_large", "median",
+                                  "blur", "full"])
+def test_noalloc_every_stop_against_the_oracle(dc, stop):
+    # stops before step 5 run stage A alone, writing the output directly
+    frames = synth.make_batch(2, synth.FrameSpec(96, 200, 16, 0.05, 2.0, 80.0), config=9, first=50)
+    _oracle_case(dc, frames, stop not in ("blur", "full"), stop_after=stop)
+
+
+@pytest.mark.parametrize("kw", [dict(blur="bilateral"), dict(blur="none", median=False),
+                                dict(extend_top=False, large_fill_on=False), dict(extend_rows=8)])
+def test_noalloc_variants_against_the_oracle(dc, kw):
+    frames = synth.make_batch(2, synth.FrameSpec(120, 260, 32, 0.06, 1.0, 90.0), config=9, first=60)
+    _oracle_case(dc, frames, False, **kw)
+
+
+def test_noalloc_off_grid_depths_against_the_oracle(dc):
+    # depths off the 1/256 m grid: the step-4 values go through the array's float part
+    frames = np.stack([synth.random_sparse(90, 170, 0.08, 70 + i) for i in range(2)])
+    _oracle_case(dc, frames, True, stop_after="median")
+    _oracle_case(dc, frames, False)
+
+
+def test_noalloc_at_its_limits(dc):
+    # 64 frames of 32 x 1024: exactly DC_NOALLOC_MAX_PIXELS padded pixels and
+    # DC_NOALLOC_MAX_FRAMES frames; sampled frames against the oracle
+    import oracle
+    spec = synth.FrameSpec(32, 1024, 8, 0.1, 2.0, 80.0)
+    frames = synth.make_batch(64, spec, config=9, first=200)
+    x = torch.from_numpy(frames).cuda()
+    y = torch.full_like(x, -9.0)
+    p = dc.params()
+    dc.dc_complete_noalloc(x.data_ptr(), y.data_ptr(), 64, 32, 1024, p, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    for i in (0, 17, 63):
+        _same(got[i], oracle.complete(frames[i]), False)
 
 
 def test_noalloc_refuses_sizes_beyond_its_array(dc):
