@@ -37,6 +37,8 @@ constexpr int kNoTop = 0x7F7F7F7F;
 // valid inputs lie below 100, so a real key is at most kKeyMax.
 constexpr unsigned kKeyOff = 0xFFFFu;
 constexpr unsigned kKeyMax = 25600u;
+// A key k is empty (k / 256 < 0.1) exactly when k <= 25.
+constexpr unsigned kEmptyKeyMax = 25;
 
 // 16-bit key of v: k with v == k / 256 exactly, k < 65536; `ok` is cleared
 // when v has no such key.  fma(v, 256, 2^23) holds 2^23 + k exactly iff
@@ -66,9 +68,11 @@ __device__ __forceinline__ unsigned long long top_pack(int row, unsigned key)
     return ((unsigned long long)(unsigned)row << 32) | (unsigned long long)key;
 }
 
-// Stage A: one warp streams one (strip, band) unit; 4 units per block.
+// Stage A: one warp streams one (strip, band) unit; one warp per block.
 constexpr int kStageAColsPerLane = 4;
 constexpr int kThreadsA = 32;  // one warp per CTA: the block scheduler spreads warps evenly
+constexpr int kStageAFloatWarpsPerSM = 12;  // the float kernel's registers allow twelve per SM
+constexpr int kStageAKeysWarpsPerSM = 16;   // the key kernel's
 // Stage B output tile (median blocks of 2 x 8 over the tile + 2 ring).
 constexpr int kTileBH = 60;
 constexpr int kTileBW = 60;
@@ -203,9 +207,17 @@ constexpr Tuning kDefaultTuning{8, 5, 160};
 // take units (zeroed before stage A starts), then those tiles.  band_stride:
 // the batch's strip count when all frames have one shape (units then go
 // band by band over the whole batch, bottom bands first), else 0.
+// fallback: null, every unit (counter work[2]); else the units the key
+// kernel left: fallback[0] of them from fallback[2], taken by the counter
+// fallback[1] (zeroed before the call like work[2]).
 cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_units,
                            int shape, int stop, int* work, int band_stride, int sm_count,
-                           cudaStream_t stream);
+                           cudaStream_t stream, const int* fallback = nullptr);
+// Steps 1-4 of the full chain on packed 16-bit keys (stage_a_keys.cu); a
+// unit whose inputs are off the key grid is appended to `fallback` (count in
+// fallback[0], zeroed before) for launch_stage_a with that list.
+cudaError_t launch_stage_a_keys(const FrameDesc* d_frames, int n_frames, int total_units, int shape, int* work,
+                                int band_stride, int* fallback, int sm_count, cudaStream_t stream);
 // cmap: with p.tma, the tensor map of the batch's step-4 maps C as a
 // W x H x n_frames array (rows c_pitch floats apart, frames H c_pitch);
 // err: set to 1 when a bounded device-side wait gives up.

@@ -555,15 +555,28 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
 // Persistent: warp w of the grid starts with unit w and then takes the next
 // unclaimed unit from work[2] (zeroed before the launch), so SMs that drew
 // cheap units (mostly empty rows) take more.  Unit 0 also zeroes work[0]
-// and work[1] for stage B.
+// and work[1] for stage B.  With a fallback list (after the key kernel of
+// stage_a_keys.cu) the warps take the listed units instead, from the counter
+// fallback[1]; warps beyond the list's length leave at once.
 template <int S>
-__global__ void __launch_bounds__(kThreadsA, 12)
+__global__ void __launch_bounds__(kThreadsA, kStageAFloatWarpsPerSM)
 stage_a_stream(const FrameDesc* __restrict__ frames, int n_frames, int total_units, int stop,
-               int* __restrict__ work, int band_stride)
+               int* __restrict__ work, int band_stride, const int* __restrict__ fallback)
 {
-    wait_previous_kernel();  // the frame table, the reset tops and counter
+    wait_previous_kernel();  // the frame table, the reset tops and counter (or the key kernel)
     allow_next_kernel();
     const int lane = threadIdx.x & 31;
+    if (fallback) {
+        const int count = fallback[0];
+        if ((int)(blockIdx.x * (kThreadsA / 32) + (threadIdx.x >> 5)) >= count) return;
+        for (;;) {
+            int idx = 0;
+            if (lane == 0) idx = atomicAdd(const_cast<int*>(fallback) + 1, 1);
+            idx = __shfl_sync(0xffffffffu, idx, 0);
+            if (idx >= count) return;
+            stage_a_unit<S>(frames, n_frames, fallback[2 + idx], stop, band_stride);
+        }
+    }
     int unit = blockIdx.x * (kThreadsA / 32) + (threadIdx.x >> 5);
     if (unit == 0 && lane < 2) work[lane] = 0;  // step-6 count, stage-B tile counter
     const int warps = gridDim.x * (kThreadsA / 32);
@@ -577,14 +590,15 @@ stage_a_stream(const FrameDesc* __restrict__ frames, int n_frames, int total_uni
 
 template <int S>
 cudaError_t launch_shape(const FrameDesc* d_frames, int n_frames, int total_units, int stop, int* work,
-                         int band_stride, int sm_count, cudaStream_t stream)
+                         int band_stride, int sm_count, cudaStream_t stream, const int* fallback)
 {
     const int per_block = kThreadsA / 32;
     int grid = (total_units + per_block - 1) / per_block;
-    if (grid > 12 * sm_count) grid = 12 * sm_count;  // twelve one-warp CTAs per SM (registers), persistent
+    // one-warp CTAs, as many per SM as the registers allow, persistent
+    if (grid > kStageAFloatWarpsPerSM * sm_count) grid = kStageAFloatWarpsPerSM * sm_count;
     if (grid < 1) return cudaSuccess;
     return launch_after_previous(stage_a_stream<S>, dim3(grid), dim3(kThreadsA), 0, stream, d_frames, n_frames,
-                                 total_units, stop, work, band_stride);
+                                 total_units, stop, work, band_stride, fallback);
 }
 
 }  // namespace
@@ -616,15 +630,15 @@ int stage_a_band_rows(int H, long long total_strips, long long target_warps)
 }
 
 cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_units, int shape, int stop,
-                           int* work, int band_stride, int sm_count, cudaStream_t stream)
+                           int* work, int band_stride, int sm_count, cudaStream_t stream, const int* fallback)
 {
     switch (shape) {
-    case kDiamond5: return launch_shape<kDiamond5>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream);
-    case kFull5: return launch_shape<kFull5>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream);
-    case kCross5: return launch_shape<kCross5>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream);
-    case kFull3: return launch_shape<kFull3>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream);
-    case kCircle5: return launch_shape<kCircle5>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream);
-    case kFull7: return launch_shape<kFull7>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream);
+    case kDiamond5: return launch_shape<kDiamond5>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream, fallback);
+    case kFull5: return launch_shape<kFull5>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream, fallback);
+    case kCross5: return launch_shape<kCross5>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream, fallback);
+    case kFull3: return launch_shape<kFull3>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream, fallback);
+    case kCircle5: return launch_shape<kCircle5>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream, fallback);
+    case kFull7: return launch_shape<kFull7>(d_frames, n_frames, total_units, stop, work, band_stride, sm_count, stream, fallback);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -75,8 +75,6 @@ struct PackedKeyOps {
     }
 };
 
-// A key k is empty (k / 256 < 0.1) exactly when k <= 25.
-constexpr unsigned kEmptyKeyMax = 25;
 
 __device__ __forceinline__ int clampi(int p, int n) { return p < 0 ? 0 : (p >= n ? n - 1 : p); }
 

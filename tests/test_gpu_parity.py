@@ -272,6 +272,20 @@ def test_out_of_range_inputs_follow_the_formulas(ctx):
                 stop, "range")
 
 
+@pytest.mark.parametrize("extreme", [100.0, 99.95703125, 100.5, 0.09765625])
+def test_quantised_depths_at_the_key_range_ends(ctx, extreme):
+    # depths in 1/256 m steps with one extreme value: 100 m inverts to 0 and
+    # (256 d) - 25600 = 0 is still a key; just below 100 m inverts to a
+    # non-empty-looking but empty value; above 100 m inverts below 0, which
+    # no key holds (that unit runs on floats); just below 0.1 m is empty
+    f = synth.random_sparse(90, 300, 0.1, 17, 2.0, 80.0, quantize=True)
+    f[40, 150] = extreme
+    f[80, 20] = extreme
+    for stop in ("fill7", "median", "full"):
+        compare(gpu_run(ctx, f[None], stop_after=stop)[0], oracle.complete(f, stop_after=stop),
+                stop, f"extreme {extreme}")
+
+
 def test_full_size_frame_352x1216(ctx):
     f = synth.make_frame(synth.ONE_FRAME, synth.frame_seed(0, 0))
     for stop in ("fill7", "median", "full"):
