@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--tuning", default=None,
                     help="launch shape 'a_warps_per_sm,b_ctas_per_sm,b_sparse_fill' instead of the tuning "
                          "cache or the autotuner (e.g. 16,5,160: profile captures name it)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave the further workloads (configs 2-4) out of the bench line")
     ap.add_argument("--configs", action="store_true",
                     help="instead of the bench line: one JSON line per further workload (the 375x1242 "
                          "batch with both blurs, the four-resolution mix, the element x fill-size sweep)")
@@ -425,6 +427,7 @@ def run_gpu(args, world, rank, local):
     e2e_sync_fps = B * e2e_steps * world / e2e_sync_s
 
     next_rows = run_next_rows(ctx, ins, outs, stream, B)
+    configs = None if args.no_configs else run_configs(args, ctx)
 
     serving = None
     if args.serve_seconds > 0:
@@ -478,6 +481,7 @@ def run_gpu(args, world, rank, local):
         "gpu_launches": launches_per_step * args.steps,
         "served": serving,
         "next_rows": next_rows,
+        "configs": configs,
         "clocks": clocks.summary(),
     }
     if not args.no_cpu_baseline and world == 1:
@@ -590,45 +594,54 @@ def run_serving(seconds):
     return out
 
 
-def run_configs(args):
-    """Throughput of the further workloads, one JSON line each.  Every
-    timing: CUDA events around `steps` calls after `warmup` on rotating input
-    sets whose total exceeds the L2; frames/s and algorithmic GB/s (8 B/px)."""
+def run_configs(args, ctx=None):
+    """Throughput of the further workloads (configs 2-4 of the benchmark
+    plan): a dict per workload.  Every timing: CUDA events around `steps`
+    calls after `warmup` on rotating input sets whose total exceeds the L2;
+    frames/s and algorithmic GB/s (8 B/px).  Clocks are sampled throughout."""
     import torch
 
     from paper_1802_00036_gb300 import dc, synth
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    ctx = dc.Context(0)
-    stream = torch.cuda.Stream()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    own = ctx is None
+    if own:
+        ctx = dc.Context(dev.index)
+    stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
-    steps, warm = max(args.steps // 10, 20), max(args.warmup, 3)
+    steps, warm = max(min(args.steps // 10, 100), 20), max(args.warmup, 3)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.2)
+    clocks.mark("start")
 
-    def timed(call, sets):
+    def timed(call, sets, n_steps=steps):
         for i in range(warm):
             call(i % sets)
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for i in range(steps):
+        for i in range(n_steps):
             call(i % sets)
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps  # ms per call
+        return e0.elapsed_time(e1) / n_steps  # ms per call
 
     def batch_sets(host, sets):
         return [torch.from_numpy(host).to(dev) for _ in range(sets)], [torch.empty(host.shape, device=dev)
                                                                         for _ in range(sets)]
 
+    res = {}
     # the 64-frame 375x1242 batch, 4-6 % per frame: one call vs 64 calls, both blurs
     host = synth.make_batch(64, synth.UNIFORM_375, config=2, density_range=(0.04, 0.06))
     ins, outs = batch_sets(host, 4)
     n, H, W = host.shape
+    rows = {}
     for blur in ("gauss", "bilateral"):
         p = dc.params(blur=blur)
         ms = timed(lambda i: dc.dc_complete_uniform(ctx.h, ins[i].data_ptr(), outs[i].data_ptr(), n, H, W, p, sp), 4)
+        pf_steps = max(steps // 4, 5)
         ms1 = timed(lambda i: [dc.dc_complete_uniform(ctx.h, ins[i][k].data_ptr(), outs[i][k].data_ptr(), 1, H, W,
-                                                      p, sp) for k in range(n)], 4)
+                                                      p, sp) for k in range(n)], 4, pf_steps)
         # the same from CUDA graphs (dc_set_graph_cache): the batch as one graph
         # launch per call; the 64 per-frame calls of one buffer set as 64 graphs
         dc.dc_set_graph_cache(ctx.h, 4)
@@ -636,14 +649,16 @@ def run_configs(args):
                     4)
         dc.dc_set_graph_cache(ctx.h, 64)
         msg1 = timed(lambda i: [dc.dc_complete_uniform(ctx.h, ins[0][k].data_ptr(), outs[0][k].data_ptr(), 1, H, W,
-                                                       p, sp) for k in range(n)], 1)
+                                                       p, sp) for k in range(n)], 1, pf_steps)
         dc.dc_set_graph_cache(ctx.h, 0)
-        print(json.dumps({"workload": f"64 x 375x1242, 4-6 % valid, 1-90 m, median + {blur}",
-                          "batched_frames_per_s": round(n / ms * 1e3, 1),
-                          "per_frame_frames_per_s": round(n / ms1 * 1e3, 1),
-                          "batched_graph_frames_per_s": round(n / msg * 1e3, 1),
-                          "per_frame_graph_frames_per_s": round(n / msg1 * 1e3, 1),
-                          "batched_GBps": round(n * H * W * 8 / ms / 1e6, 1)}), flush=True)
+        rows[blur] = {"batched_frames_per_s": round(n / ms * 1e3, 1),
+                      "per_frame_frames_per_s": round(n / ms1 * 1e3, 1),
+                      "batched_graph_frames_per_s": round(n / msg * 1e3, 1),
+                      "per_frame_graph_frames_per_s": round(n / msg1 * 1e3, 1),
+                      "batched_GBps": round(n * H * W * 8 / ms / 1e6, 1)}
+    res["batched_375x1242"] = {"workload": "64 x 375x1242, 4-6 % valid, 1-90 m, median + Gaussian / bilateral",
+                               **rows}
+    del ins, outs
 
     # the four-resolution mix: 32 frames of each, one call (dc_complete) and per resolution
     mix = []
@@ -668,10 +683,11 @@ def run_configs(args):
         msr = timed(lambda i: dc.dc_complete_uniform(ctx.h, dev_in[i][k].data_ptr(), dev_out[i][k].data_ptr(), 32, h,
                                                      w, p, sp), 2)
         per_res[f"{h}x{w}"] = round(32 / msr * 1e3, 1)
-    print(json.dumps({"workload": "128 frames, 32 each of 256x512@3%, 352x1216@5%, 375x1242@5%, 512x2048@10%",
-                      "one_call_frames_per_s": round(128 / ms * 1e3, 1),
-                      "one_call_GBps": round(px * 8 / ms / 1e6, 1),
-                      "per_resolution_batch_of_32_frames_per_s": per_res}), flush=True)
+    res["uneven_mix"] = {"workload": "128 frames, 32 each of 256x512@3%, 352x1216@5%, 375x1242@5%, 512x2048@10%",
+                         "one_call_frames_per_s": round(128 / ms * 1e3, 1),
+                         "one_call_GBps": round(px * 8 / ms / 1e6, 1),
+                         "per_resolution_batch_of_32_frames_per_s": per_res}
+    del dev_in, dev_out
 
     # first element x large-fill size on 32 x 352x1216
     host = synth.make_batch(32, synth.ONE_FRAME, config=4)
@@ -685,15 +701,27 @@ def run_configs(args):
                                                         sp), 4)
             rows.append({"first": shape, "fill": fill, "frames_per_s": round(n / ms * 1e3, 1),
                          "GBps": round(n * H * W * 8 / ms / 1e6, 1)})
-    print(json.dumps({"workload": "32 x 352x1216, 5 % valid: first element x large fill", "rows": rows}),
-          flush=True)
-    ctx.close()
+    res["shape_sweep"] = {"workload": "32 x 352x1216, 5 % valid: first element x large fill", "rows": rows}
+    clocks.mark("stop")
+    time.sleep(0.2)
+    clocks.stop()
+    res["clocks"] = clocks.summary()
+    res["timing"] = (f"CUDA events, {steps} calls after {warm} warm-up ({max(steps // 4, 5)} rounds of 64 calls "
+                     f"for per-frame), inputs rotating over sets larger than the L2")
+    if own:
+        ctx.close()
+    return res
 
 
 def main():
     args = parse()
     if args.configs:
-        run_configs(args)
+        import torch
+        torch.cuda.set_device(0)
+        import __graft_entry__
+        __graft_entry__.build()
+        for name, row in run_configs(args).items():
+            print(json.dumps({"config": name, **row} if isinstance(row, dict) else {name: row}), flush=True)
         return
     if args.impl == "reference":
         # the CPU oracle needs no process group: rank 0 runs it, others exit

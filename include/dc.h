@@ -251,6 +251,19 @@ dc_status dc_kernel_times(dc_ctx* ctx, float* ms, int max_calls, int* n_out);
  * its outputs are incomplete). */
 dc_status dc_last_async_error(dc_ctx* ctx);
 
+/* Testing hook: put the context in the state a failure would leave, without
+ * any failure on the GPU, so that callers can test their error handling.
+ *   DC_FAULT_WAIT: set the context's device error word, as stage B does when
+ *     its bounded wait for a region copy gives up; the next
+ *     dc_last_async_error() returns DC_ERR_TIMEOUT, the one after DC_OK.
+ *   DC_FAULT_LAUNCH: the next call that launches kernels fails as if its
+ *     first launch had been refused: it queues nothing and returns
+ *     DC_ERR_CUDA, which dc_last_async_error() (or the call after) then
+ *     reports once more, as for any CUDA error.
+ * Returns DC_ERR_INVALID_ARG for a null context or an unknown fault. */
+typedef enum { DC_FAULT_WAIT = 1, DC_FAULT_LAUNCH = 2 } dc_fault;
+dc_status dc_inject_fault(dc_ctx* ctx, int fault);
+
 /* Human-readable name of a status code (static storage). */
 const char* dc_status_str(dc_status s);
 

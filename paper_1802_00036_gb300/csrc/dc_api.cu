@@ -96,6 +96,7 @@ struct dc_ctx {
     cudaEvent_t last_done = nullptr;  // event of the latest call, or null
     int last_launches = 0;
     dc_status sticky = DC_OK;
+    bool fail_next_launch = false;  // dc_inject_fault(DC_FAULT_LAUNCH)
     // profiling ring: 3 events per call (before A, between, after B)
     bool profiling = false;
     int prof_every = 1;                 // profile one call in prof_every
@@ -384,6 +385,10 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         d.top = need_b ? ctx->top + reinterpret_cast<size_t>(d.top) : nullptr;
     }
 
+    if (ctx->fail_next_launch) {  // an injected launch failure: nothing is queued
+        ctx->fail_next_launch = false;
+        return DC_ERR_CUDA;
+    }
     // calls share the scratch: order this one after the previous call
     if (!capture && ctx->last_done && stream != ctx->last_stream &&
         cudaStreamWaitEvent(stream, ctx->last_done, 0) != cudaSuccess)
@@ -944,6 +949,22 @@ dc_status dc_last_async_error(dc_ctx* ctx)
     }
     if (cudaGetLastError() != cudaSuccess) s = DC_ERR_CUDA;
     return s;
+}
+
+dc_status dc_inject_fault(dc_ctx* ctx, int fault)
+{
+    if (!ctx) return DC_ERR_INVALID_ARG;
+    if (fault == DC_FAULT_WAIT) {
+        DeviceGuard g(ctx->device);
+        const int one = 1;
+        if (cudaMemcpy(ctx->err, &one, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return DC_ERR_CUDA;
+        return DC_OK;
+    }
+    if (fault == DC_FAULT_LAUNCH) {
+        ctx->fail_next_launch = true;
+        return DC_OK;
+    }
+    return DC_ERR_INVALID_ARG;
 }
 
 const char* dc_status_str(dc_status s)

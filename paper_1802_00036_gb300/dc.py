@@ -17,6 +17,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "lib", "libdc.so")
 
 DC_OK = 0
+DC_ERR_INVALID_ARG, DC_ERR_OOM, DC_ERR_CUDA, DC_ERR_TIMEOUT, DC_ERR_UNSUPPORTED = 1, 2, 3, 4, 5
 STATUS = {0: "DC_OK", 1: "DC_ERR_INVALID_ARG", 2: "DC_ERR_OOM", 3: "DC_ERR_CUDA",
           4: "DC_ERR_TIMEOUT", 5: "DC_ERR_UNSUPPORTED"}
 KERNELS = {"diamond5": 0, "full5": 1, "cross5": 2, "full3": 3, "circle5": 4, "full7": 5}
@@ -103,6 +104,7 @@ SIGNATURES = [
     ("dc_kernel_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int)]),
     ("dc_last_async_error", ctypes.c_int, [ctypes.c_void_p]),
+    ("dc_inject_fault", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("dc_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("dc_destroy", None, [ctypes.c_void_p]),
     ("dc_complete_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -328,6 +330,15 @@ def dc_kernel_times(ctx, max_calls: int = DC_PROFILE_CALLS):
 
 def dc_last_async_error(ctx) -> int:
     return int(load().dc_last_async_error(ctx))
+
+
+DC_FAULT_WAIT, DC_FAULT_LAUNCH = 1, 2
+
+
+def dc_inject_fault(ctx, fault: int) -> None:
+    """Testing hook (see include/dc.h): leave the context as a device-side
+    wait timeout (DC_FAULT_WAIT) or a refused launch (DC_FAULT_LAUNCH) would."""
+    _check(load().dc_inject_fault(ctx, int(fault)), "dc_inject_fault")
 
 
 def dc_status_str(s: int) -> str:

@@ -94,3 +94,4 @@ def test_calls_without_a_context_are_refused(lib):
     assert L.dc_kernel_times(None, buf, 1, ctypes.byref(n)) == INVALID
     p = dc.dc_params_default()
     assert L.dc_complete_uniform(None, None, None, 1, 8, 8, ctypes.byref(p), None) == INVALID
+    assert L.dc_inject_fault(None, dc.DC_FAULT_WAIT) == INVALID

@@ -17,33 +17,6 @@ def test_poisson_schedule_is_sorted_and_rate_plausible():
 
 
 @pytest.mark.gpu
-def test_served_results_equal_alone():
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    from paper_1802_00036_gb300 import build, dc
-    from paper_1802_00036_gb300.serve import Server
-    build.build()
-    specs = [synth.FrameSpec(352, 1216, 64, 0.05), synth.FrameSpec(512, 2048, 128, 0.08),
-             synth.FrameSpec(256, 512, 32, 0.03)]
-    frames = [synth.make_frame(specs[i % 3], 7000 + i) for i in range(24)]
-    srv = Server(max_hw=(512, 2048), budget_bytes=1 << 30, deadline_ms=3.0, max_batch=8, lanes=2)
-    try:
-        futs = [srv.submit(f, sensor=i % 4) for i, f in enumerate(frames)]
-        got = [f.result(timeout=60) for f in futs]
-        st = srv.stats().summary()
-    finally:
-        srv.close()
-    assert st["frames"] == 24 and st["batches"] >= 3
-    ctx = dc.Context(0)
-    try:
-        for f, g in zip(frames, got):
-            alone = ctx.complete(torch.from_numpy(f).cuda()).cpu().numpy()
-            assert np.array_equal(alone.view(np.uint32), g.view(np.uint32))
-    finally:
-        ctx.close()
-
-
-@pytest.mark.gpu
 def test_native_server_results_equal_alone():
     # libdc's serving worker: frames of three sizes from four sensors, batched
     # by size and deadline on two lanes; every result equals the frame run alone
