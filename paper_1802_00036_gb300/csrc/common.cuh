@@ -221,8 +221,10 @@ cudaError_t launch_stage_a_keys(const FrameDesc* d_frames, int n_frames, int tot
 // cmap: with p.tma, the tensor map of the batch's step-4 maps C as a
 // W x H x n_frames array (rows c_pitch floats apart, frames H c_pitch);
 // err: set to 1 when a bounded device-side wait gives up.
+// ffill: the step-6 tiles off the key grid, ffill[0] of them from ffill[1]
+// (ffill[0] zeroed before the call, room for every tile).
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,
-                           const StageBParams& p, int* worklist, int sm_count, int ctas_per_sm,
+                           const StageBParams& p, int* worklist, int* ffill, int sm_count, int ctas_per_sm,
                            const CUtensorMap* cmap, int* err, cudaStream_t stream);
 
 // Accuracy measures (metrics.cu): acc holds 5 n doubles of scratch, out

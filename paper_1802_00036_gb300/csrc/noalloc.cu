@@ -65,12 +65,14 @@ dc_status setup(int dev, unsigned char** ptr, int* sms)
 __global__ void noalloc_prepare(FrameDesc* table, unsigned long long* top, unsigned short* ckeys, float* cmap,
                                 const float* in, float* out,
                                 int n, int H, int W, int c_pitch, int tiles_x_a, int tiles_a, int band_a,
-                                int tiles_x_b, int tiles_b, int top_ints, int* counter, int* fallback, int* err)
+                                int tiles_x_b, int tiles_b, int top_ints, int* counter, int* fallback, int* ffill,
+                                int* err)
 {
     allow_next_kernel();  // stage A may launch; it waits for this kernel's writes
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     if (tid < 2) fallback[tid] = 0;  // stage A's fallback list: length, taken
+    if (tid == 0) *ffill = 0;        // stage B's float step-6 list: length
     if (tid == 0) {
         *counter = 0;  // stage A's unit counter
         *err = 0;      // stage B's error word (set only by its tensor-copy wait, which this path does not use)
@@ -137,11 +139,13 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     const int tiles_x_b = (W + kTileBW - 1) / kTileBW;
     const int tiles_b = tiles_x_b * ((H + kTileBH - 1) / kTileBH);
     // work: three counters, the step-6 tile list, stage A's fallback list
-    // (two counters and the units), the error word last
+    // (two counters and the units), the float step-6 list (a count and the
+    // tiles), the error word last
     if ((long long)tiles_a * n > INT32_MAX / 2 ||
-        (long long)tiles_b * n + 5 + (long long)tiles_a * n + 1 > DC_NOALLOC_WORK_INTS)
+        2 * (long long)tiles_b * n + 6 + (long long)tiles_a * n + 1 > DC_NOALLOC_WORK_INTS)
         return DC_ERR_UNSUPPORTED;
     int* fallback = work + 3 + (size_t)tiles_b * n;
+    int* ffill = fallback + 2 + (size_t)tiles_a * n;
     cudaStream_t st = (cudaStream_t)stream;
 
     const int top_ints = need_b ? (int)((size_t)n * c_pitch) : 0;
@@ -151,7 +155,7 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     noalloc_prepare<<<blocks, threads, 0, st>>>(table, need_b ? top : nullptr, need_b ? ckeys : nullptr,
                                                  need_b ? cmap : nullptr,
                                                  in, out, n, H, W, (int)c_pitch, tiles_x_a, tiles_a, band_a,
-                                                 tiles_x_b, tiles_b, top_ints, work + 2, fallback,
+                                                 tiles_x_b, tiles_b, top_ints, work + 2, fallback, ffill,
                                                  work + DC_NOALLOC_WORK_INTS - 1);
     if (cudaGetLastError() != cudaSuccess) return DC_ERR_CUDA;
 
@@ -183,7 +187,7 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
         bp.inv_2sc2 = (float)(1.0 / (2.0 * sc * sc));
         // regions by cp.async (no tensor map: the map would have to be written
         // for the array's address); the error word is zeroed by noalloc_prepare
-        if (launch_stage_b(table, n, tiles_b * n, bp, work, sms, kDefaultTuning.b_ctas_per_sm, nullptr,
+        if (launch_stage_b(table, n, tiles_b * n, bp, work, ffill, sms, kDefaultTuning.b_ctas_per_sm, nullptr,
                            work + DC_NOALLOC_WORK_INTS - 1, st) != cudaSuccess)
             return DC_ERR_CUDA;
     }

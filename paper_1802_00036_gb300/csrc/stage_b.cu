@@ -1150,7 +1150,7 @@ __device__ bool tile_keys(const Tile& T, const StageBParams& p, const MainSmem& 
 // grid: E from C's keys and the float map, then the same steps on floats
 // (the median and blur still run on keys when the region's values allow).
 template <bool kFill>
-__device__ void tile_floats(const Tile& T, const StageBParams& p, const MainSmem& S, int t, int* worklist,
+__device__ void tile_floats(const Tile& T, const StageBParams& p, const MainSmem& S, int t, int* ffill,
                             bool ext_tile)
 {
     const int tid = threadIdx.x, H = T.fd.H, W = T.fd.W;
@@ -1256,8 +1256,8 @@ __device__ void tile_floats(const Tile& T, const StageBParams& p, const MainSmem
         store_tile(E);
     } else if (n_empty > p.sparse_fill_max) {
         if (tid == 0) {
-            const int slot = atomicAdd(worklist, 1);
-            worklist[3 + slot] = t;
+            const int slot = atomicAdd(ffill, 1);
+            ffill[1 + slot] = t;
         }
     } else {
         if (n_empty > 0) {
@@ -1397,7 +1397,8 @@ __device__ void tile_floats(const Tile& T, const StageBParams& p, const MainSmem
 template <bool kFill>
 __global__ void __launch_bounds__(kThreadsB, 5)
 stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles, StageBParams p,
-             int* __restrict__ worklist, const __grid_constant__ CUtensorMap cmap, int* __restrict__ err)
+             int* __restrict__ worklist, int* __restrict__ ffill, const __grid_constant__ CUtensorMap cmap,
+             int* __restrict__ err)
 {
     wait_previous_kernel();  // C, the tops and counters of stage A
     allow_next_kernel();
@@ -1470,7 +1471,7 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
         } else if (void_tile) {
             store_zero_tile(T);
         } else if (!tile_keys<kFill>(T, p, S, t, worklist, ext_tile)) {
-            tile_floats<kFill>(T, p, S, t, worklist, ext_tile);
+            tile_floats<kFill>(T, p, S, t, ffill, ext_tile);
         }
 
         __syncthreads();
@@ -1484,7 +1485,262 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
 // shift of the region's first column down to a 16-byte boundary.
 __host__ __device__ constexpr int fill_row_stride(int GC) { return (GC + 6) / 4 * 4; }
 
-// Phase 2: tiles from the worklist, with step 6.  Shared memory: G (E over
+// Row stride (in keys) of the wide key region of phase 2: the region's first
+// column rounded down to a multiple of 8 (16-byte chunks) leaves up to 7
+// keys before it; a multiple of 8.
+__host__ __device__ constexpr int fill_key_stride(int GC) { return (GC + 14) / 8 * 8; }
+
+// Bytes of the wide key region, also the Gaussian's row-pass buffer later.
+__host__ __device__ constexpr size_t fill_key_gbytes(int large_radius)
+{
+    const size_t g = (size_t)(kER + 2 * large_radius) * fill_key_stride(kEC + 2 * large_radius) * 2;
+    const size_t r = (size_t)kMR * kRS * sizeof(float);
+    return ((g > r ? g : r) + 15) / 16 * 16;
+}
+
+// Phase 2 on keys: the tiles with more empty pixels than a tile fills
+// itself (worklist[0] of them from worklist[3]), with step 6.  The wide
+// region (tile + 4 + the window radius) of C's keys arrives by 16-byte
+// cp.async chunks (the few across the frame's edges by plain loads, key 0
+// outside it), step 5 is applied per column, and K (the median's packed
+// layout) takes E over tile + 4, border replicated.  The window maxima are
+// taken in place on packed words (two columns each) by doubling (a pass
+// with step s leaves at each position the maximum of the next 2 s; after
+// the largest power of two P within the window, one pass at wl - P): down
+// the columns with each warp holding a word column in registers (row r in
+// lane r % 32, register r / 32; a step is two warp shuffles), then along
+// the rows with word pairs (a byte permute shifts an odd step by one
+// column).  K's empty positions take the maximum at their window's corner;
+// then the packed median, the exact blur on keys and the store.  A tile
+// whose region holds a value off the key grid goes to the float list
+// (ffill[0] of them from ffill[1]) for stage_b_fill.  About 41 KB of shared
+// memory at the paper's 31 x 31: five CTAs per SM.
+__global__ void __launch_bounds__(kThreadsB, 5)
+stage_b_fill_keys(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
+                  const int* __restrict__ worklist, int* __restrict__ ffill)
+{
+    wait_previous_kernel();  // the worklist and outputs of the main pass
+    allow_next_kernel();
+    extern __shared__ __align__(16) unsigned char dynk[];
+    const int Rl = p.large_radius;
+    const int GR = kER + 2 * Rl, GC = kEC + 2 * Rl;
+    const int GSk = fill_key_stride(GC), GSW = GSk / 2;  // keys, words per row
+    unsigned short* Gk = reinterpret_cast<unsigned short*>(dynk);
+    unsigned* Gw = reinterpret_cast<unsigned*>(dynk);
+    float* R = reinterpret_cast<float*>(dynk);
+    unsigned* K = reinterpret_cast<unsigned*>(dynk + fill_key_gbytes(Rl));
+    unsigned short* Mk = reinterpret_cast<unsigned short*>(K + kPR * kES);
+    int* ctop = reinterpret_cast<int*>(Mk + kMR * kMS);
+    unsigned* ctv = reinterpret_cast<unsigned*>(ctop + GC);
+
+    const int count = worklist[0];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wl = 2 * Rl + 1;
+    int P = 1;
+    while (2 * P <= wl) P *= 2;
+    for (int w = blockIdx.x; w < count; w += gridDim.x) {
+        __syncthreads();
+        const int t = worklist[3 + w];
+        const Tile T = tile_of(frames, n_frames, t, p.row_stride);
+        const int H = T.fd.H, W = T.fd.W;
+        const int gy = T.y0 - 4 - Rl, gx = T.x0 - 4 - Rl;  // frame position of the wide region's (0, 0)
+        const int gxa = gx & ~7, sh = gx - gxa;            // buffer column b is frame column gxa + b
+        load_tops(T, p, gx, GC, ctop, ctv);
+        // a wide region empty in every column: every window of step 6 holds
+        // only empty values, so does the median, and the output is 0
+        if (p.stop == kStopFull) {
+            bool empty_cols = true;
+            const int last = min(H - 1, gy + GR - 1);
+            for (int l = tid; l < GC; l += kThreadsB) {
+                const int x = gx + l;
+                if (x >= 0 && x < W) empty_cols = empty_cols && column_empty_to(T, p, x, last);
+            }
+            if (__syncthreads_and(empty_cols)) {
+                store_zero_tile(T);
+                continue;
+            }
+        }
+        // C's keys over the wide region's rows, whole 16-byte chunks inside the
+        // frame, the rest key by key with 0 outside the frame
+        const int nch = GSk / 8;
+        for (int i = tid; i < GR * nch; i += kThreadsB) {
+            const int k = i / nch, j = i - k * nch;
+            const int y = gy + k, x = gxa + 8 * j;
+            unsigned short* dst = Gk + k * GSk + 8 * j;
+            if (y >= 0 && y < H && x >= 0 && x + 8 <= W) {
+                cp_async16(dst, T.fd.ck + (size_t)y * T.fd.c_pitch + x);
+            } else {
+                const bool row_in = y >= 0 && y < H;
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    dst[e] = (row_in && x + e >= 0 && x + e < W) ? T.fd.ck[(size_t)y * T.fd.c_pitch + x + e]
+                                                                 : (unsigned short)0;
+            }
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+        // step 5: the rows above each in-frame column's top (within the cap)
+        if (p.extend_top) {
+            for (int l = tid; l < GC; l += kThreadsB) {
+                const int top = ctop[l], x = gx + l;
+                if (top == kNoTop || x < 0 || x >= W) continue;
+                const int klo = max(-gy, p.extend_rows < 0 ? 0 : top - p.extend_rows - gy);
+                const int khi = min(GR, top - gy);
+                const unsigned short v = (unsigned short)ctv[l];
+                for (int k = max(0, klo); k < khi; ++k) Gk[k * GSk + sh + l] = v;
+            }
+            __syncthreads();
+        }
+        // a value off the key grid anywhere in the buffer: the float pass does the tile
+        unsigned mx = 0u;
+        for (int i = tid; i < GR * GSW; i += kThreadsB) mx = __vmaxu2(mx, Gw[i]);
+        if (__syncthreads_or((mx & 0xFFFFu) > kKeyMax || (mx >> 16) > kKeyMax)) {
+            if (tid == 0) {
+                const int slot = atomicAdd(ffill, 1);
+                ffill[1 + slot] = t;
+            }
+            continue;
+        }
+        // K: E over tile + 4, border replicated, rows (kp, kp + kHalf) per word;
+        // thread t < kRowGroups x kChunksPerRow takes column chunk t %
+        // kChunksPerRow of every kRowGroups-th K row
+        const int g = tid / kChunksPerRow, q = tid - g * kChunksPerRow;
+        if (tid < kRowGroups * kChunksPerRow) {
+            int bcol[4];  // buffer columns of the chunk (clamped into the frame)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) bcol[e] = clampi(T.x0 - 4 + 4 * q + e, W) - gxa;
+            for (int kp = g; kp < kPR; kp += kRowGroups) {
+                const unsigned short* ra = Gk + (clampi(T.y0 - 4 + kp, H) - gy) * GSk;
+                const unsigned short* rb = Gk + (clampi(T.y0 - 4 + kp + kHalf, H) - gy) * GSk;
+                unsigned wd[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) wd[e] = (unsigned)ra[bcol[e]] | ((unsigned)rb[bcol[e]] << 16);
+                *reinterpret_cast<uint4*>(K + kp * kES + 4 * q) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+            }
+        }
+        __syncthreads();
+        // the passes of the doubling: steps 1, 2, 4, .. below P, then wl - P
+        const int npass = (31 - __clz(P)) + (wl > P ? 1 : 0);
+        // window maxima down the columns: rows [0, kER) end with the maximum
+        // over [r, r + 2 Rl]; rows beyond the region count as key 0
+        {
+            constexpr int kVR = (kER + 2 * (kMaxLargeFill / 2) + 31) / 32;
+            const int nvr = (GR + 31) / 32;  // registers in use (warp-uniform)
+            const int wc0 = sh >> 1, wc1 = (sh + GC + 1) >> 1;
+            for (int wc = wc0 + warp; wc < wc1; wc += kThreadsB / 32) {
+                unsigned v[kVR];
+#pragma unroll
+                for (int j = 0; j < kVR; ++j) {
+                    const int r = lane + 32 * j;
+                    v[j] = r < GR ? Gw[r * GSW + wc] : 0u;
+                }
+                for (int pass = 0; pass < npass; ++pass) {
+                    // v[r] = max(v[r], v[r + s]), 0 < s < 32
+                    const int s = (1 << pass) < P ? (1 << pass) : wl - P;
+                    const int src = (lane + s) & 31;
+                    const bool wrap = lane + s >= 32;
+                    unsigned carry = 0u;  // register j + 1's shuffled word, from the step before
+#pragma unroll
+                    for (int j = kVR - 1; j >= 0; --j) {
+                        if (j < nvr) {
+                            const unsigned a = __shfl_sync(0xffffffffu, v[j], src);
+                            const unsigned m = __vmaxu2(v[j], wrap ? carry : a);
+                            carry = a;
+                            v[j] = m;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kVR; ++j) {
+                    const int r = lane + 32 * j;
+                    if (r < kER) Gw[r * GSW + wc] = v[j];
+                }
+            }
+        }
+        __syncthreads();
+        // window maxima along the rows [0, kER): positions [sh, sh + kEC) end
+        // with the maximum over [c, c + 2 Rl]; one warp per row, word m in
+        // lane m % 32, register m / 32, a step of s positions is the word
+        // q = s / 2 further (s even), or the pair across words q and q + 1
+        // (s odd: a byte permute)
+        {
+            constexpr int kPW = (fill_key_stride(kEC + 2 * (kMaxLargeFill / 2)) / 2 + 31) / 32;
+            const int npw = (GSW + 31) / 32;  // registers in use (warp-uniform)
+            for (int k = warp; k < kER; k += kThreadsB / 32) {
+                unsigned* row = Gw + k * GSW;
+                unsigned v[kPW];
+#pragma unroll
+                for (int j = 0; j < kPW; ++j) {
+                    const int m = lane + 32 * j;
+                    v[j] = m < GSW ? row[m] : 0u;
+                }
+                for (int pass = 0; pass < npass; ++pass) {
+                    const int s = (1 << pass) < P ? (1 << pass) : wl - P;
+                    const int q = s >> 1;
+                    const int src0 = (lane + q) & 31, src1 = (lane + q + 1) & 31;
+                    const bool wrap0 = lane + q >= 32, wrap1 = lane + q + 1 >= 32;
+                    unsigned c0 = 0u, c1 = 0u;  // register j + 1's shuffled words
+#pragma unroll
+                    for (int j = kPW - 1; j >= 0; --j) {
+                        if (j < npw) {
+                            const unsigned a0 = __shfl_sync(0xffffffffu, v[j], src0);
+                            const unsigned w0 = wrap0 ? c0 : a0;  // word m + q
+                            unsigned o = w0;
+                            if (s & 1) {
+                                const unsigned a1 = __shfl_sync(0xffffffffu, v[j], src1);
+                                const unsigned w1 = wrap1 ? c1 : a1;  // word m + q + 1
+                                o = __byte_perm(w0, w1, 0x5432);
+                                c1 = a1;
+                            }
+                            c0 = a0;
+                            v[j] = __vmaxu2(v[j], o);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kPW; ++j) {
+                    const int m = lane + 32 * j;
+                    if (m < GSW) row[m] = v[j];
+                }
+            }
+        }
+        __syncthreads();
+        // step 6: an empty position takes the maximum at its window's corner
+        // (the clamped pixel's, at the replicated border)
+        if (tid < kRowGroups * kChunksPerRow) {
+            // a window's corner column is the clamped column - Rl, in buffer columns
+            int bcol[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) bcol[e] = clampi(T.x0 - 4 + 4 * q + e, W) - gxa - Rl;
+            for (int kp = g; kp < kPR; kp += kRowGroups) {
+                uint4* cell = reinterpret_cast<uint4*>(K + kp * kES + 4 * q);
+                uint4 c4 = *cell;
+                unsigned wd[4] = {c4.x, c4.y, c4.z, c4.w};
+                const unsigned mn = __vminu2(__vimin3_u16x2(wd[0], wd[1], wd[2]), wd[3]);
+                if ((mn & 0xFFFFu) > kEmptyKeyMax && (mn >> 16) > kEmptyKeyMax) continue;  // nothing empty
+                const unsigned short* ga = Gk + (clampi(T.y0 - 4 + kp, H) - gy - Rl) * GSk;
+                const unsigned short* gb = Gk + (clampi(T.y0 - 4 + kp + kHalf, H) - gy - Rl) * GSk;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if ((wd[e] & 0xFFFFu) <= kEmptyKeyMax) wd[e] = (wd[e] & 0xFFFF0000u) | ga[bcol[e]];
+                    if ((wd[e] >> 16) <= kEmptyKeyMax) wd[e] = (wd[e] & 0xFFFFu) | ((unsigned)gb[bcol[e]] << 16);
+                }
+                *cell = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+            }
+        }
+        __syncthreads();
+        if (p.stop == kStopFillLarge) {
+            store_keys_tile(T, K);
+            continue;
+        }
+        median_blur_store(T, p, nullptr, K, true, reinterpret_cast<float*>(K), Mk, R);
+    }
+}
+
+// Phase 2 on floats: the tiles with many empty pixels whose values are off
+// the key grid, from the float list (ffill[0] of them from ffill[1]), with
+// step 6.  Shared memory: G (E over
 // the wide region, rows of GS floats, 16-byte aligned, frame column gx at
 // offset sh; the window maxima are taken in place there, then it holds the
 // median output), F (E, then the step-6 output, over tile + 4; the blur's
@@ -1492,9 +1748,9 @@ __host__ __device__ constexpr int fill_row_stride(int GC) { return (GC + 6) / 4 
 // 60 KB at the paper's 31 x 31: three CTAs per SM.
 __global__ void __launch_bounds__(kThreadsB, 3)
 stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
-             const int* __restrict__ worklist)
+             const int* __restrict__ ffill)
 {
-    wait_previous_kernel();  // the worklist and outputs of the main pass
+    wait_previous_kernel();  // the list and outputs of the main pass and of the key pass
     extern __shared__ __align__(16) float dyn[];
     const int Rl = p.large_radius;
     const int GR = kER + 2 * Rl, GC = kEC + 2 * Rl;  // the wide region
@@ -1507,11 +1763,11 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
     const float* cval = reinterpret_cast<const float*>(ctv);  // after tops_to_floats
     float* R = F;
 
-    const int count = worklist[0];
+    const int count = ffill[0];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int w = blockIdx.x; w < count; w += gridDim.x) {
         __syncthreads();
-        const Tile T = tile_of(frames, n_frames, worklist[3 + w], p.row_stride);
+        const Tile T = tile_of(frames, n_frames, ffill[1 + w], p.row_stride);
         const int H = T.fd.H, W = T.fd.W;
         const int gy = T.y0 - 4 - Rl, gx = T.x0 - 4 - Rl;  // frame position of the wide region's (0, 0)
         load_tops(T, p, gx, GC, ctop, ctv);
@@ -1641,8 +1897,26 @@ size_t stage_b_fill_smem_bytes(int large_radius)
     return sizeof(float) * ((size_t)GR * fill_row_stride(GC) + kER * kES + 2 * GC);
 }
 
+size_t stage_b_fill_keys_smem_bytes(int large_radius)
+{
+    return fill_key_gbytes(large_radius) + sizeof(unsigned) * kPR * kES + sizeof(unsigned short) * kMR * kMS +
+           2 * sizeof(int) * (kEC + 2 * large_radius);
+}
+
+// As many CTAs per SM of a kernel as shared memory and registers hold.
+template <class Kern>
+int occupancy_ctas(Kern kernel, size_t smem)
+{
+    int n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kThreadsB, smem) != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n < 1 ? 1 : n;
+}
+
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,
-                           const StageBParams& p, int* worklist, int sm_count, int ctas_per_sm,
+                           const StageBParams& p, int* worklist, int* ffill, int sm_count, int ctas_per_sm,
                            const CUtensorMap* cmap, int* err, cudaStream_t stream)
 {
     static int configured_dev = -1;
@@ -1652,6 +1926,9 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
     if (configured_dev != dev) {
         cudaError_t e = cudaFuncSetAttribute(stage_b_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)stage_b_fill_smem_bytes(kMaxLargeFill / 2));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(stage_b_fill_keys, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)stage_b_fill_keys_smem_bytes(kMaxLargeFill / 2));
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(stage_b_main<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)main_smem);
         if (e != cudaSuccess) return e;
@@ -1669,20 +1946,20 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
     q.tma = (p.tma && cmap) ? 1 : 0;
     cudaError_t e = launch_after_previous(p.large_fill_on ? stage_b_main<true> : stage_b_main<false>, dim3(main_grid),
                                           dim3(kThreadsB), main_smem, stream, d_frames, n_frames, total_tiles, q,
-                                          worklist, map, err);
+                                          worklist, ffill, map, err);
     if (e != cudaSuccess || !p.large_fill_on || p.stop == kStopExtend) return e;
-    // as many CTAs per SM as shared memory and registers hold
-    const size_t fill_smem = stage_b_fill_smem_bytes(p.large_radius);
-    int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_b_fill, kThreadsB, fill_smem) != cudaSuccess) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
-    if (per_sm < 1) per_sm = 1;
-    int grid = per_sm * sm_count;
+    // step 6 over the worklist on keys, then on floats over the tiles off the key grid
+    const size_t kfill_smem = stage_b_fill_keys_smem_bytes(p.large_radius);
+    int grid = occupancy_ctas(stage_b_fill_keys, kfill_smem) * sm_count;
     if (grid > total_tiles) grid = total_tiles;
-    return launch_after_previous(stage_b_fill, dim3(grid), dim3(kThreadsB), stage_b_fill_smem_bytes(p.large_radius),
-                                 stream, d_frames, n_frames, p, static_cast<const int*>(worklist));
+    e = launch_after_previous(stage_b_fill_keys, dim3(grid), dim3(kThreadsB), kfill_smem, stream, d_frames, n_frames,
+                              p, static_cast<const int*>(worklist), ffill);
+    if (e != cudaSuccess) return e;
+    const size_t fill_smem = stage_b_fill_smem_bytes(p.large_radius);
+    grid = occupancy_ctas(stage_b_fill, fill_smem) * sm_count;
+    if (grid > total_tiles) grid = total_tiles;
+    return launch_after_previous(stage_b_fill, dim3(grid), dim3(kThreadsB), fill_smem, stream, d_frames, n_frames, p,
+                                 static_cast<const int*>(ffill));
 }
 
 }  // namespace dcgb
