@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--tuning", default=None,
                     help="launch shape 'a_warps_per_sm,b_ctas_per_sm,b_sparse_fill' instead of the tuning "
                          "cache or the autotuner (e.g. 16,5,160: profile captures name it)")
+    ap.add_argument("--params", default="",
+                    help="chain parameters other than the paper's for the batched step, 'key=value,...' (e.g. "
+                         "extend_rows=50: the capped extension of Sec. V-B), for profiling")
     ap.add_argument("--no-configs", action="store_true",
                     help="leave the further workloads (configs 2-4) out of the bench line")
     ap.add_argument("--configs", action="store_true",
@@ -311,7 +314,11 @@ def run_gpu(args, world, rank, local):
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
     ctx = dc.Context(local)
-    p = dc.params(blur=args.blur)
+    extra = {}
+    for item in (args.params.split(",") if args.params else []):
+        k, v = item.split("=")
+        extra[k.strip()] = int(v) if v.strip().lstrip("-").isdigit() else v.strip()
+    p = dc.params(blur=args.blur, **extra)
     dc.dc_reserve(ctx.h, B, H, W)
     from paper_1802_00036_gb300 import tune
     if args.tuning:
@@ -363,7 +370,7 @@ def run_gpu(args, world, rank, local):
     if args.quick:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": round(fps, 1), "unit": "frames/s", "quick": True,
-                              "kernels_ms": {"stage_a": a_ms, "stage_b": b_ms}}), flush=True)
+                              "params": extra, "kernels_ms": {"stage_a": a_ms, "stage_b": b_ms}}), flush=True)
         ctx.close()
         return
 
@@ -449,7 +456,7 @@ def run_gpu(args, world, rank, local):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(workload_config(B, args.blur),
+        "config": dict(workload_config(B, args.blur), params=extra or None,
                        parallelism="replicas" if world > 1 else "single",
                        tuning={"a_warps_per_sm": tuning[0][0], "b_ctas_per_sm": tuning[0][1],
                                "b_sparse_fill": tuning[0][2], "source": tuning[1]},
