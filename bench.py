@@ -53,8 +53,8 @@ def parse():
     ap.add_argument("--quick", action="store_true",
                     help="timed batched steps only (no per-frame, e2e or CPU legs): for profiling")
     ap.add_argument("--tuning", default=None,
-                    help="launch shape 'a_warps_per_sm,b_ctas_per_sm,b_sparse_fill' instead of the tuning "
-                         "cache or the autotuner (e.g. 16,5,160: profile captures name it)")
+                    help="launch shape 'a_warps_per_sm,b_ctas_per_sm,b_sparse_fill[,a_strip_cols]' instead of the "
+                         "tuning cache or the autotuner (e.g. 16,5,160: profile captures name it)")
     ap.add_argument("--params", default="",
                     help="chain parameters other than the paper's for the batched step, 'key=value,...' (e.g. "
                          "extend_rows=50: the capped extension of Sec. V-B), for profiling")
@@ -324,7 +324,7 @@ def run_gpu(args, world, rank, local):
     if args.tuning:
         t = tuple(int(v) for v in args.tuning.split(","))
         dc.dc_set_tuning(ctx.h, *t)
-        tuning = (t, "command line")
+        tuning = (dc.dc_get_tuning(ctx.h), "command line")
     else:
         tuning = tune.tuned(ctx, ins[0], outs[0], p, stream)  # before any timed region
 
@@ -459,7 +459,7 @@ def run_gpu(args, world, rank, local):
         "config": dict(workload_config(B, args.blur), params=extra or None,
                        parallelism="replicas" if world > 1 else "single",
                        tuning={"a_warps_per_sm": tuning[0][0], "b_ctas_per_sm": tuning[0][1],
-                               "b_sparse_fill": tuning[0][2], "source": tuning[1]},
+                               "b_sparse_fill": tuning[0][2], "a_strip_cols": tuning[0][3], "source": tuning[1]},
                        l2=f"inputs rotate over {ROTATE} resident batches "
                           f"({ROTATE * B * px * 4 / 1e6:.0f} MB in + same out > 129 MB L2)"),
         "roofline": {

@@ -191,11 +191,15 @@ dc_status dc_metrics(dc_ctx* ctx, const float* pred, const float* gt, int n, int
  * 1..5, default 5).  b_sparse_fill: a stage-B tile with at most this many
  * empty pixels near it fills them itself (step 6); a
  * tile with more goes to a second kernel that works on the whole window
- * region (0..160, default 160). */
+ * region (0..160, default 160).  a_strip_cols: the width of stage A's column
+ * strips, 128 (four columns per lane; least halo, for large batches) or 64
+ * (two; twice the strips and half the work per warp, for one or a few
+ * frames, where each warp's latency sets the time; default 128). */
 typedef struct {
     int a_warps_per_sm;
     int b_ctas_per_sm;
     int b_sparse_fill;
+    int a_strip_cols;
 } dc_tuning;
 
 dc_status dc_set_tuning(dc_ctx* ctx, const dc_tuning* t);
@@ -204,7 +208,7 @@ dc_status dc_get_tuning(const dc_ctx* ctx, dc_tuning* t);
 /* Time dc_complete_uniform on the caller's n packed frames (device `in` /
  * `out`, as for dc_complete_uniform; `out` is overwritten) under a fixed set
  * of tunings (two rounds of one knob at a time), keep the fastest in the
- * context and return it in *best.  Synchronous; runs the chain ~150 times. */
+ * context and return it in *best.  Synchronous; runs the chain ~170 times. */
 dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, int W,
                       const dc_params* params, void* stream, dc_tuning* best);
 

@@ -105,6 +105,7 @@ struct FrameDesc {
     int in_pitch, out_pitch, c_pitch;  // c_pitch: a multiple of 32 elements
     int tiles_x_a, base_a;  // stage A: strips per frame, first flat unit
     int band_a;             // stage A: rows per band
+    int ow_a;               // stage A: output columns per strip
     int tiles_x_b, base_b;  // stage B: same
 };
 
@@ -183,10 +184,11 @@ __device__ __forceinline__ int find_frame(const FrameDesc* __restrict__ d, int n
     return lo;
 }
 
-// Stage A geometry (stage_a.cu): output columns per strip and the halo
+// Stage A geometry (stage_a.cu): output columns per strip of strip_cols
+// columns (128: four per lane; 64: two, the key kernel only) and the halo
 // (= vertical delay) for a first element.
-int stage_a_strip_width(int shape);
-int stage_a_strips(int W, int shape);  // strips covering W columns (the first writes its left halo)
+int stage_a_strip_width(int shape, int strip_cols);
+int stage_a_strips(int W, int shape, int strip_cols);  // strips covering W columns (the first writes its left halo)
 int stage_a_halo(int shape);
 // Rows per stage-A band so that a batch with `total_strips` strips gives
 // about `target_warps` warps; at least 32 rows.
@@ -197,8 +199,9 @@ struct Tuning {
     int a_warps_per_sm;   // stage A: warps in flight per SM the bands aim for
     int b_ctas_per_sm;    // stage B: persistent CTAs per SM (1..5)
     int b_sparse_fill;    // stage B: most empty pixels a tile fills itself (0..160)
+    int a_strip_cols;     // stage A (on keys): strip width, 128 or 64 columns
 };
-constexpr Tuning kDefaultTuning{8, 5, 160};
+constexpr Tuning kDefaultTuning{8, 5, 160, 128};
 
 // Launchers (stage_a.cu, stage_b.cu).  Return cudaGetLastError().
 // `work` holds 3 + (stage B tiles) ints: the number of stage-B tiles that
@@ -216,8 +219,8 @@ cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_un
 // Steps 1-4 of the full chain on packed 16-bit keys (stage_a_keys.cu); a
 // unit whose inputs are off the key grid is appended to `fallback` (count in
 // fallback[0], zeroed before) for launch_stage_a with that list.
-cudaError_t launch_stage_a_keys(const FrameDesc* d_frames, int n_frames, int total_units, int shape, int* work,
-                                int band_stride, int* fallback, int sm_count, cudaStream_t stream);
+cudaError_t launch_stage_a_keys(const FrameDesc* d_frames, int n_frames, int total_units, int shape, int strip_cols,
+                                int* work, int band_stride, int* fallback, int sm_count, cudaStream_t stream);
 // cmap: with p.tma, the tensor map of the batch's step-4 maps C as a
 // W x H x n_frames array (rows c_pitch floats apart, frames H c_pitch);
 // err: set to 1 when a bounded device-side wait gives up.

@@ -228,7 +228,7 @@ template <int K>
 struct TableChunk {
     FrameDesc d[K];
 };
-static_assert(sizeof(TableChunk<384>) + 64 <= 32764, "kernel parameter space");
+static_assert(sizeof(TableChunk<352>) + 64 <= 32764, "kernel parameter space");
 
 template <int K>
 __global__ void table_put(const __grid_constant__ TableChunk<K> src, FrameDesc* __restrict__ dst, int n,
@@ -259,15 +259,15 @@ cudaError_t table_put_chunk(const FrameDesc* desc, int n, FrameDesc* dst, unsign
     return cudaGetLastError();
 }
 
-// Store n descriptors at dst (chunks of up to 384 per launch), reset
+// Store n descriptors at dst (chunks of up to 352 per launch), reset
 // top_ints column tops, zero *counter, fallback[0..1] and *ffill (when not
 // null); returns the number of launches through *launches.
 cudaError_t put_table(const FrameDesc* desc, int n, FrameDesc* dst, unsigned long long* top, size_t top_ints,
                       int* counter, int* fallback, int* ffill, int sms, cudaStream_t stream, int* launches)
 {
     *launches = 0;
-    for (int i = 0; i < n; i += 384) {
-        const int m = n - i < 384 ? n - i : 384;
+    for (int i = 0; i < n; i += 352) {
+        const int m = n - i < 352 ? n - i : 352;
         unsigned long long* t = i == 0 ? top : nullptr;
         const size_t ti = i == 0 ? top_ints : 0;
         int* z = i == 0 ? counter : nullptr;
@@ -275,7 +275,7 @@ cudaError_t put_table(const FrameDesc* desc, int n, FrameDesc* dst, unsigned lon
         int* ff = i == 0 ? ffill : nullptr;
         cudaError_t e = m <= 8    ? table_put_chunk<8>(desc + i, m, dst + i, t, ti, z, fb, ff, sms, stream)
                       : m <= 64   ? table_put_chunk<64>(desc + i, m, dst + i, t, ti, z, fb, ff, sms, stream)
-                                  : table_put_chunk<384>(desc + i, m, dst + i, t, ti, z, fb, ff, sms, stream);
+                                  : table_put_chunk<352>(desc + i, m, dst + i, t, ti, z, fb, ff, sms, stream);
         if (e != cudaSuccess) return e;
         ++*launches;
     }
@@ -345,8 +345,12 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
 
     // layout of scratch, stage-A units (strip x band) and stage-B tiles
     std::vector<FrameDesc> desc((size_t)n);
+    const bool need_b = (p->stop_after == DC_STOP_FULL || p->stop_after >= DC_STOP_EXTEND);
+    // the key kernel (full chain) takes the tuned strip width; the float
+    // kernel alone (a stop before step 5) its own 128 columns
+    const int strip_cols = need_b ? ctx->tune.a_strip_cols : 128;
     long long total_strips = 0;
-    for (int i = 0; i < n; ++i) total_strips += stage_a_strips(frames[i].W, p->first_kernel);
+    for (int i = 0; i < n; ++i) total_strips += stage_a_strips(frames[i].W, p->first_kernel, strip_cols);
     size_t c_off = 0, top_off = 0;
     long long tiles_a = 0, tiles_b = 0;
     for (int i = 0; i < n; ++i) {
@@ -359,7 +363,8 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         d.in_pitch = f.in_pitch;
         d.out_pitch = f.out_pitch;
         d.c_pitch = (int)round_up((size_t)f.W, 32);
-        d.tiles_x_a = stage_a_strips(f.W, p->first_kernel);
+        d.tiles_x_a = stage_a_strips(f.W, p->first_kernel, strip_cols);
+        d.ow_a = stage_a_strip_width(p->first_kernel, strip_cols);
         d.band_a = stage_a_band_rows(f.H, total_strips, (long long)ctx->tune.a_warps_per_sm * ctx->sm_count);
         d.tiles_x_b = ceil_div(f.W, kTileBW);
         d.base_a = (int)tiles_a;
@@ -374,7 +379,6 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
     }
     if (tiles_a > INT32_MAX / 2 || tiles_b > INT32_MAX / 2) return DC_ERR_UNSUPPORTED;
 
-    const bool need_b = (p->stop_after == DC_STOP_FULL || p->stop_after >= DC_STOP_EXTEND);
     // work: three counters, the step-6 tile list, stage A's fallback list
     // (two counters and the units), the float step-6 list (a count and the tiles)
     const size_t fb_off = need_b ? (size_t)tiles_b + 3 : 3;
@@ -421,8 +425,8 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
     // once); a stop before step 5: the float kernel on every unit
     cudaError_t e = cudaSuccess;
     if (stop_a == kStopFull) {
-        e = launch_stage_a_keys(ctx->table, n, (int)tiles_a, p->first_kernel, ctx->work, band_stride, fallback,
-                                ctx->sm_count, stream);
+        e = launch_stage_a_keys(ctx->table, n, (int)tiles_a, p->first_kernel, strip_cols, ctx->work, band_stride,
+                                fallback, ctx->sm_count, stream);
         if (e == cudaSuccess)
             e = launch_stage_a(ctx->table, n, (int)tiles_a, p->first_kernel, stop_a, ctx->work, band_stride,
                                ctx->sm_count, stream, fallback);
@@ -607,7 +611,7 @@ dc_status dc_reserve(dc_ctx* ctx, int n_frames, int H, int W)
     DeviceGuard g(ctx->device);
     const size_t tiles = (size_t)ceil_div(W, kTileBW) * (size_t)ceil_div(H, kTileBH) * (size_t)n_frames;
     // stage-A units: the most strips (the widest halo) times bands of at least 8 rows
-    const size_t units = (size_t)stage_a_strips(W, kFull7) * (size_t)ceil_div(H, 8) * (size_t)n_frames;
+    const size_t units = (size_t)stage_a_strips(W, kFull7, 64) * (size_t)ceil_div(H, 8) * (size_t)n_frames;
     return note(ctx, grow(ctx, frame_c_floats(H, W) * (size_t)n_frames,
                           frame_top_ints(W) * (size_t)n_frames, n_frames, 0, 2 * tiles + 6 + units));
 }
@@ -807,9 +811,10 @@ dc_status dc_metrics(dc_ctx* ctx, const float* pred, const float* gt, int n, int
 dc_status dc_set_tuning(dc_ctx* ctx, const dc_tuning* t)
 {
     if (!ctx || !t || t->a_warps_per_sm < 1 || t->a_warps_per_sm > 64 || t->b_ctas_per_sm < 1 ||
-        t->b_ctas_per_sm > 5 || t->b_sparse_fill < 0 || t->b_sparse_fill > 160)
+        t->b_ctas_per_sm > 5 || t->b_sparse_fill < 0 || t->b_sparse_fill > 160 ||
+        (t->a_strip_cols != 64 && t->a_strip_cols != 128))
         return DC_ERR_INVALID_ARG;
-    ctx->tune = Tuning{t->a_warps_per_sm, t->b_ctas_per_sm, t->b_sparse_fill};
+    ctx->tune = Tuning{t->a_warps_per_sm, t->b_ctas_per_sm, t->b_sparse_fill, t->a_strip_cols};
     return DC_OK;
 }
 
@@ -819,6 +824,7 @@ dc_status dc_get_tuning(const dc_ctx* ctx, dc_tuning* t)
     t->a_warps_per_sm = ctx->tune.a_warps_per_sm;
     t->b_ctas_per_sm = ctx->tune.b_ctas_per_sm;
     t->b_sparse_fill = ctx->tune.b_sparse_fill;
+    t->a_strip_cols = ctx->tune.a_strip_cols;
     return DC_OK;
 }
 
@@ -853,24 +859,38 @@ dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, in
     static const int a_cand[] = {2, 3, 4, 6, 8, 12, 16, 24};
     static const int b_cand[] = {1, 2, 3, 4, 5};
     static const int f_cand[] = {0, 4, 8, 16, 32, 64, 160};
+    static const int c_cand[] = {128, 64};
     Tuning best_t = saved;
     float best_ms = 1e30f;
     s = measure(best_t, &best_ms);
     for (int round = 0; round < 2 && s == DC_OK; ++round) {
         for (int a : a_cand) {
             float ms;
-            if ((s = measure(Tuning{a, best_t.b_ctas_per_sm, best_t.b_sparse_fill}, &ms)) != DC_OK) break;
+            if ((s = measure(Tuning{a, best_t.b_ctas_per_sm, best_t.b_sparse_fill, best_t.a_strip_cols}, &ms)) !=
+                DC_OK)
+                break;
             if (ms < best_ms) { best_ms = ms; best_t.a_warps_per_sm = a; }
         }
         for (int b : b_cand) {
             float ms;
-            if (s != DC_OK || (s = measure(Tuning{best_t.a_warps_per_sm, b, best_t.b_sparse_fill}, &ms)) != DC_OK) break;
+            if (s != DC_OK || (s = measure(Tuning{best_t.a_warps_per_sm, b, best_t.b_sparse_fill, best_t.a_strip_cols},
+                                           &ms)) != DC_OK)
+                break;
             if (ms < best_ms) { best_ms = ms; best_t.b_ctas_per_sm = b; }
         }
         for (int f : f_cand) {
             float ms;
-            if (s != DC_OK || (s = measure(Tuning{best_t.a_warps_per_sm, best_t.b_ctas_per_sm, f}, &ms)) != DC_OK) break;
+            if (s != DC_OK || (s = measure(Tuning{best_t.a_warps_per_sm, best_t.b_ctas_per_sm, f, best_t.a_strip_cols},
+                                           &ms)) != DC_OK)
+                break;
             if (ms < best_ms) { best_ms = ms; best_t.b_sparse_fill = f; }
+        }
+        for (int c : c_cand) {
+            float ms;
+            if (s != DC_OK || (s = measure(Tuning{best_t.a_warps_per_sm, best_t.b_ctas_per_sm, best_t.b_sparse_fill, c},
+                                           &ms)) != DC_OK)
+                break;
+            if (ms < best_ms) { best_ms = ms; best_t.a_strip_cols = c; }
         }
     }
     cudaEventDestroy(e0);
@@ -879,6 +899,7 @@ dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, in
     best->a_warps_per_sm = ctx->tune.a_warps_per_sm;
     best->b_ctas_per_sm = ctx->tune.b_ctas_per_sm;
     best->b_sparse_fill = ctx->tune.b_sparse_fill;
+    best->a_strip_cols = ctx->tune.a_strip_cols;
     return s;
 }
 

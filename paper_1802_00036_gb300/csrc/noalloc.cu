@@ -64,7 +64,7 @@ dc_status setup(int dev, unsigned char** ptr, int* sms)
 // the device so that the call copies nothing from the host.
 __global__ void noalloc_prepare(FrameDesc* table, unsigned long long* top, unsigned short* ckeys, float* cmap,
                                 const float* in, float* out,
-                                int n, int H, int W, int c_pitch, int tiles_x_a, int tiles_a, int band_a,
+                                int n, int H, int W, int c_pitch, int tiles_x_a, int ow_a, int tiles_a, int band_a,
                                 int tiles_x_b, int tiles_b, int top_ints, int* counter, int* fallback, int* ffill,
                                 int* err)
 {
@@ -92,6 +92,7 @@ __global__ void noalloc_prepare(FrameDesc* table, unsigned long long* top, unsig
         d.tiles_x_a = tiles_x_a;
         d.base_a = i * tiles_a;
         d.band_a = band_a;
+        d.ow_a = ow_a;
         d.tiles_x_b = tiles_x_b;
         d.base_b = i * tiles_b;
         table[i] = d;
@@ -132,7 +133,9 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     unsigned short* ckeys = reinterpret_cast<unsigned short*>(base + kTableBytes + kTopBytes + kWorkBytes);
     float* cmap = reinterpret_cast<float*>(base + kTableBytes + kTopBytes + kWorkBytes + kKeyBytes);
     const bool need_b = (params->stop_after == DC_STOP_FULL || params->stop_after >= DC_STOP_EXTEND);
-    const int tiles_x_a = stage_a_strips(W, params->first_kernel);
+    const int strip_cols = kDefaultTuning.a_strip_cols;
+    const int tiles_x_a = stage_a_strips(W, params->first_kernel, strip_cols);
+    const int ow_a = stage_a_strip_width(params->first_kernel, strip_cols);
     const int band_a = stage_a_band_rows(H, (long long)tiles_x_a * n,
                                          (long long)kDefaultTuning.a_warps_per_sm * sms);
     const int tiles_a = tiles_x_a * ((H + band_a - 1) / band_a);
@@ -154,15 +157,15 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     if (blocks > 1024) blocks = 1024;
     noalloc_prepare<<<blocks, threads, 0, st>>>(table, need_b ? top : nullptr, need_b ? ckeys : nullptr,
                                                  need_b ? cmap : nullptr,
-                                                 in, out, n, H, W, (int)c_pitch, tiles_x_a, tiles_a, band_a,
+                                                 in, out, n, H, W, (int)c_pitch, tiles_x_a, ow_a, tiles_a, band_a,
                                                  tiles_x_b, tiles_b, top_ints, work + 2, fallback, ffill,
                                                  work + DC_NOALLOC_WORK_INTS - 1);
     if (cudaGetLastError() != cudaSuccess) return DC_ERR_CUDA;
 
     const int stop_a = need_b ? kStopFull : params->stop_after;
     if (need_b) {  // steps 1-4 on keys, then the units off the key grid on floats
-        if (launch_stage_a_keys(table, n, tiles_a * n, params->first_kernel, work, tiles_x_a * n, fallback, sms,
-                                st) != cudaSuccess ||
+        if (launch_stage_a_keys(table, n, tiles_a * n, params->first_kernel, strip_cols, work, tiles_x_a * n,
+                                fallback, sms, st) != cudaSuccess ||
             launch_stage_a(table, n, tiles_a * n, params->first_kernel, stop_a, work, tiles_x_a * n, sms, st,
                            fallback) != cudaSuccess)
             return DC_ERR_CUDA;

@@ -304,7 +304,6 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
 {
     constexpr int R1 = ShapeInfo<S>::r;
     constexpr int Rh = R1 + 7;        // halo, horizontal and vertical
-    constexpr int OW = kSW - 2 * Rh;  // output columns per strip
     const int lane = threadIdx.x & 31;
     // Bands from the bottom up (the rows with data, the costly ones, come
     // first): with frames of one shape (band_stride = strips of the batch)
@@ -323,6 +322,9 @@ __device__ __forceinline__ void stage_a_unit(const FrameDesc* __restrict__ frame
     }
     const FrameDesc& fd = frames[f];
     const int H = fd.H, W = fd.W, in_pitch = fd.in_pitch;
+    // output columns per strip: kSW - 2 Rh, or fewer when the units are
+    // those of the key kernel's narrower strips (its fallback)
+    const int OW = fd.ow_a;
     const float* __restrict__ src = fd.in;
     const int r0 = band * fd.band_a, r1 = min(r0 + fd.band_a, H);
     // Strip s reads frame columns [s OW, s OW + kSW) and writes [s OW + Rh,
@@ -608,11 +610,11 @@ int stage_a_halo(int shape)
     return shape == kFull3 ? 8 : (shape == kFull7 ? 10 : 9);
 }
 
-int stage_a_strip_width(int shape) { return kSW - 2 * stage_a_halo(shape); }
+int stage_a_strip_width(int shape, int strip_cols) { return strip_cols - 2 * stage_a_halo(shape); }
 
-int stage_a_strips(int W, int shape)
+int stage_a_strips(int W, int shape, int strip_cols)
 {
-    const int ow = stage_a_strip_width(shape), h = stage_a_halo(shape);
+    const int ow = stage_a_strip_width(shape, strip_cols), h = stage_a_halo(shape);
     const int n = (W - h + ow - 1) / ow;
     return n < 1 ? 1 : n;
 }

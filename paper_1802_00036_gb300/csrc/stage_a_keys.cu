@@ -27,10 +27,7 @@
 namespace dcgb {
 namespace {
 
-constexpr int kV = kStageAColsPerLane;  // columns per lane
-constexpr int kP = kV / 2;               // key words per lane
-constexpr int kSW = 32 * kV;             // strip width in columns
-static_assert(kV == 4, "two words of two keys per lane");
+// kP key words (2 kP columns) per lane: strips of 64 kP columns.
 
 constexpr unsigned kNeutralMax = 0u;           // before a maximum: no key is smaller
 constexpr unsigned kNeutralMin = 0xFFFFFFFFu;  // before a minimum: no key is larger
@@ -41,48 +38,60 @@ __device__ __forceinline__ unsigned ext3(unsigned a, unsigned b, unsigned c)
     return kMax ? __vimax3_u16x2(a, b, c) : __vimin3_u16x2(a, b, c);
 }
 
-// Columns (2i - 3, 2i - 2) for i = 0..4 from the words w[i] = columns
-// (2i - 4, 2i - 3): the pair shifted by one column.
-__device__ __forceinline__ unsigned shifted(const unsigned (&w)[6], int i) { return __byte_perm(w[i], w[i + 1], 0x5432); }
-
-// A row of a lane: w[2], w[3] its own words (columns 0-1, 2-3), w[0], w[1]
-// the left neighbour's (columns -4..-1), w[4], w[5] the right one's (4..7).
+// A row of a lane: w[2 .. 2 + kP) its own words (columns 0-1, 2-3, ..),
+// w[0], w[1] the two words left of them (columns -4..-1), w[2 + kP],
+// w[3 + kP] the two right of them.  Word i holds columns (2i - 4, 2i - 3).
+template <int kP>
 struct KRow {
-    unsigned w[6];
+    unsigned w[kP + 4];
+    // Columns (2i - 3, 2i - 2): the pair shifted by one column.
+    __device__ __forceinline__ unsigned shifted(int i) const { return __byte_perm(w[i], w[i + 1], 0x5432); }
     // fetch the neighbour words for radius R (1..3); at the frame's left
-    // edge (at_left, lane 0) they are the neutral value
+    // edge (at_left) those left of the strip are the neutral value
     template <int R>
     __device__ __forceinline__ void neighbours(bool at_left, unsigned neutral)
     {
-        w[1] = __shfl_up_sync(0xffffffffu, w[3], 1);
-        w[4] = __shfl_down_sync(0xffffffffu, w[2], 1);
-        if (R >= 3) {
-            w[0] = __shfl_up_sync(0xffffffffu, w[2], 1);
-            w[5] = __shfl_down_sync(0xffffffffu, w[3], 1);
-        }
-        if (at_left && (threadIdx.x & 31) == 0) {
-            w[1] = neutral;
-            if (R >= 3) w[0] = neutral;
+        const int lane = threadIdx.x & 31;
+        if (kP >= 2) {
+            w[1] = __shfl_up_sync(0xffffffffu, w[kP + 1], 1);
+            w[kP + 2] = __shfl_down_sync(0xffffffffu, w[2], 1);
+            if (R >= 3) {
+                w[0] = __shfl_up_sync(0xffffffffu, w[kP], 1);
+                w[kP + 3] = __shfl_down_sync(0xffffffffu, w[3], 1);
+            }
+            if (at_left && lane == 0) {
+                w[1] = neutral;
+                if (R >= 3) w[0] = neutral;
+            }
+        } else {
+            w[1] = __shfl_up_sync(0xffffffffu, w[2], 1);
+            w[3] = __shfl_down_sync(0xffffffffu, w[2], 1);
+            if (R >= 3) {
+                w[0] = __shfl_up_sync(0xffffffffu, w[2], 2);
+                w[4] = __shfl_down_sync(0xffffffffu, w[2], 2);
+            }
+            if (at_left && lane == 0) w[1] = neutral;
+            if (R >= 3 && at_left && lane < 2) w[0] = neutral;
         }
     }
 };
 
 // Horizontal extremes of radius 1, 2, 3 for the lane's pair j (columns 2j,
 // 2j + 1): h1 over [-1, 1], h2 over [-2, 2], h3 over [-3, 3].
-template <bool kMax>
-__device__ __forceinline__ unsigned hext1(const KRow& x, int j)
+template <bool kMax, int kP>
+__device__ __forceinline__ unsigned hext1(const KRow<kP>& x, int j)
 {
-    return ext3<kMax>(shifted(x.w, 1 + j), x.w[2 + j], shifted(x.w, 2 + j));
+    return ext3<kMax>(x.shifted(1 + j), x.w[2 + j], x.shifted(2 + j));
 }
-template <bool kMax>
-__device__ __forceinline__ unsigned hext2(const KRow& x, int j, unsigned h1)
+template <bool kMax, int kP>
+__device__ __forceinline__ unsigned hext2(const KRow<kP>& x, int j, unsigned h1)
 {
     return ext3<kMax>(h1, x.w[1 + j], x.w[3 + j]);
 }
-template <bool kMax>
-__device__ __forceinline__ unsigned hext3(const KRow& x, int j, unsigned h2)
+template <bool kMax, int kP>
+__device__ __forceinline__ unsigned hext3(const KRow<kP>& x, int j, unsigned h2)
 {
-    return ext3<kMax>(h2, shifted(x.w, j), shifted(x.w, 3 + j));
+    return ext3<kMax>(h2, x.shifted(j), x.shifted(3 + j));
 }
 
 template <int S> struct ShapeInfo;
@@ -95,7 +104,7 @@ template <> struct ShapeInfo<kFull7> { static constexpr int r = 3; };
 
 // 7-row window of a row extreme h: u(o) = ext(h(o-2), h(o-1), h(o));
 // out(o-3) = ext(u(o-4), u(o-1), h(o)).
-template <bool kMax>
+template <bool kMax, int kP>
 struct Window7 {
     unsigned h[2][kP], u[4][kP];
     __device__ void init(unsigned fill)
@@ -119,18 +128,18 @@ struct Window7 {
 // Step 2 for each element (the rows of Fig. 4's shapes as horizontal
 // extremes of radius 0..3): push() takes input row t and returns the
 // dilation of row t - r1, exactly as the float rings of stage_a.cu.
-template <int S> struct FirstDilation;
+template <int S, int kP> struct FirstDilation;
 
-template <> struct FirstDilation<kDiamond5> {
+template <int kP> struct FirstDilation<kDiamond5, kP> {
     unsigned x[2][kP], p[2][kP], h1[kP];
     __device__ void init()
     {
         for (int v = 0; v < kP; ++v) x[0][v] = x[1][v] = p[0][v] = p[1][v] = h1[v] = kNeutralMax;
     }
     template <int PHI>
-    __device__ __forceinline__ void push(KRow& in, unsigned* out, bool at_left)
+    __device__ __forceinline__ void push(KRow<kP>& in, unsigned* out, bool at_left)
     {
-        in.neighbours<2>(at_left, kNeutralMax);
+        in.template neighbours<2>(at_left, kNeutralMax);
 #pragma unroll
         for (int v = 0; v < kP; ++v) {
             const unsigned a1 = hext1<true>(in, v);
@@ -144,16 +153,16 @@ template <> struct FirstDilation<kDiamond5> {
     }
 };
 
-template <> struct FirstDilation<kFull5> {
+template <int kP> struct FirstDilation<kFull5, kP> {
     unsigned h[2][kP], s[2][kP];
     __device__ void init()
     {
         for (int v = 0; v < kP; ++v) h[0][v] = h[1][v] = s[0][v] = s[1][v] = kNeutralMax;
     }
     template <int PHI>
-    __device__ __forceinline__ void push(KRow& in, unsigned* out, bool at_left)
+    __device__ __forceinline__ void push(KRow<kP>& in, unsigned* out, bool at_left)
     {
-        in.neighbours<2>(at_left, kNeutralMax);
+        in.template neighbours<2>(at_left, kNeutralMax);
 #pragma unroll
         for (int v = 0; v < kP; ++v) {
             const unsigned a2 = hext2<true>(in, v, hext1<true>(in, v));
@@ -165,16 +174,16 @@ template <> struct FirstDilation<kFull5> {
     }
 };
 
-template <> struct FirstDilation<kCross5> {
+template <int kP> struct FirstDilation<kCross5, kP> {
     unsigned x[2][kP], p[2][kP];
     __device__ void init()
     {
         for (int v = 0; v < kP; ++v) x[0][v] = x[1][v] = p[0][v] = p[1][v] = kNeutralMax;
     }
     template <int PHI>
-    __device__ __forceinline__ void push(KRow& in, unsigned* out, bool at_left)
+    __device__ __forceinline__ void push(KRow<kP>& in, unsigned* out, bool at_left)
     {
-        in.neighbours<2>(at_left, kNeutralMax);
+        in.template neighbours<2>(at_left, kNeutralMax);
 #pragma unroll
         for (int v = 0; v < kP; ++v) {
             const unsigned a2 = hext2<true>(in, v, hext1<true>(in, v));
@@ -187,16 +196,16 @@ template <> struct FirstDilation<kCross5> {
     }
 };
 
-template <> struct FirstDilation<kFull3> {
+template <int kP> struct FirstDilation<kFull3, kP> {
     unsigned h[2][kP];
     __device__ void init()
     {
         for (int v = 0; v < kP; ++v) h[0][v] = h[1][v] = kNeutralMax;
     }
     template <int PHI>
-    __device__ __forceinline__ void push(KRow& in, unsigned* out, bool at_left)
+    __device__ __forceinline__ void push(KRow<kP>& in, unsigned* out, bool at_left)
     {
-        in.neighbours<1>(at_left, kNeutralMax);
+        in.template neighbours<1>(at_left, kNeutralMax);
 #pragma unroll
         for (int v = 0; v < kP; ++v) {
             const unsigned a1 = hext1<true>(in, v);
@@ -206,16 +215,16 @@ template <> struct FirstDilation<kFull3> {
     }
 };
 
-template <> struct FirstDilation<kCircle5> {
+template <int kP> struct FirstDilation<kCircle5, kP> {
     unsigned h1[2][kP], h2[kP], p[2][kP];
     __device__ void init()
     {
         for (int v = 0; v < kP; ++v) h1[0][v] = h1[1][v] = h2[v] = p[0][v] = p[1][v] = kNeutralMax;
     }
     template <int PHI>
-    __device__ __forceinline__ void push(KRow& in, unsigned* out, bool at_left)
+    __device__ __forceinline__ void push(KRow<kP>& in, unsigned* out, bool at_left)
     {
-        in.neighbours<2>(at_left, kNeutralMax);
+        in.template neighbours<2>(at_left, kNeutralMax);
 #pragma unroll
         for (int v = 0; v < kP; ++v) {
             const unsigned a1 = hext1<true>(in, v);
@@ -229,13 +238,13 @@ template <> struct FirstDilation<kCircle5> {
     }
 };
 
-template <> struct FirstDilation<kFull7> {
-    Window7<true> w;
+template <int kP> struct FirstDilation<kFull7, kP> {
+    Window7<true, kP> w;
     __device__ void init() { w.init(kNeutralMax); }
     template <int PHI>
-    __device__ __forceinline__ void push(KRow& in, unsigned* out, bool at_left)
+    __device__ __forceinline__ void push(KRow<kP>& in, unsigned* out, bool at_left)
     {
-        in.neighbours<3>(at_left, kNeutralMax);
+        in.template neighbours<3>(at_left, kNeutralMax);
 #pragma unroll
         for (int v = 0; v < kP; ++v)
             out[v] = w.template push<PHI>(v, hext3<true>(in, v, hext2<true>(in, v, hext1<true>(in, v))));
@@ -243,7 +252,7 @@ template <> struct FirstDilation<kFull7> {
 };
 
 // 5x5 square max or min (step 3).
-template <bool kMax>
+template <bool kMax, int kP>
 struct Square5 {
     unsigned h[2][kP], s[2][kP];
     __device__ void init(unsigned fill)
@@ -251,9 +260,9 @@ struct Square5 {
         for (int v = 0; v < kP; ++v) h[0][v] = h[1][v] = s[0][v] = s[1][v] = fill;
     }
     template <int PHI>
-    __device__ __forceinline__ void push(KRow& in, unsigned* out, bool at_left)
+    __device__ __forceinline__ void push(KRow<kP>& in, unsigned* out, bool at_left)
     {
-        in.neighbours<2>(at_left, kMax ? kNeutralMax : kNeutralMin);
+        in.template neighbours<2>(at_left, kMax ? kNeutralMax : kNeutralMin);
 #pragma unroll
         for (int v = 0; v < kP; ++v) {
             const unsigned hn = hext2<kMax>(in, v, hext1<kMax>(in, v));
@@ -280,8 +289,9 @@ __device__ __forceinline__ unsigned nonempty_mask(unsigned w)
 }
 
 // Step 4: 7x7 max written into empty pixels of B only.
+template <int kP>
 struct Fill7 {
-    Window7<true> w;
+    Window7<true, kP> w;
     unsigned b[4][kP];  // B rows, to select C(o - 3)
     __device__ void init()
     {
@@ -289,9 +299,9 @@ struct Fill7 {
         for (int v = 0; v < kP; ++v) b[0][v] = b[1][v] = b[2][v] = b[3][v] = kNeutralMax;
     }
     template <int PHI>
-    __device__ __forceinline__ void push(KRow& in, unsigned* out, bool at_left)
+    __device__ __forceinline__ void push(KRow<kP>& in, unsigned* out, bool at_left)
     {
-        in.neighbours<3>(at_left, kNeutralMax);
+        in.template neighbours<3>(at_left, kNeutralMax);
 #pragma unroll
         for (int v = 0; v < kP; ++v) {
             const unsigned hn = hext3<true>(in, v, hext2<true>(in, v, hext1<true>(in, v)));
@@ -320,14 +330,17 @@ __device__ __forceinline__ unsigned input_key(float d, bool& bad)
 }
 
 // One unit of steps 1-4 on keys; false if its inputs left the key grid
-// (then the float kernel redoes it: no top has been written).
-template <int S>
+// (then the float kernel redoes it: no top has been written).  kP words
+// (2 kP columns) per lane: a strip of 64 kP columns, of which the frame's
+// ow_a output columns start Rh in.
+template <int S, int kP>
 __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, int n_frames, int unit,
                                           int band_stride)
 {
+    constexpr int kV = 2 * kP;        // columns per lane
+    constexpr int kSW = 32 * kV;      // strip width in columns
     constexpr int R1 = ShapeInfo<S>::r;
     constexpr int Rh = R1 + 7;        // halo, horizontal and vertical
-    constexpr int OW = kSW - 2 * Rh;  // output columns per strip
     const int lane = threadIdx.x & 31;
     int f, band, strip;
     if (band_stride > 0) {
@@ -342,7 +355,7 @@ __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, 
         strip = local % frames[f].tiles_x_a;
     }
     const FrameDesc& fd = frames[f];
-    const int H = fd.H, W = fd.W, in_pitch = fd.in_pitch;
+    const int H = fd.H, W = fd.W, in_pitch = fd.in_pitch, OW = fd.ow_a;
     const float* __restrict__ src = fd.in;
     const int r0 = band * fd.band_a, r1 = min(r0 + fd.band_a, H);
     const int sx = strip * OW;
@@ -368,10 +381,10 @@ __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, 
     for (int v = 0; v < kP; ++v)
         in_mask[v] = (col_in[2 * v] ? 0xFFFFu : 0u) | (col_in[2 * v + 1] ? 0xFFFF0000u : 0u);
 
-    FirstDilation<S> s2;
-    Square5<true> s3d;
-    Square5<false> s3e;
-    Fill7 s4;
+    FirstDilation<S, kP> s2;
+    Square5<true, kP> s3d;
+    Square5<false, kP> s3e;
+    Fill7<kP> s4;
     s2.init();
     s3d.init(kNeutralMax);
     s3e.init(kNeutralMin);
@@ -402,21 +415,22 @@ __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, 
 #pragma unroll
     for (int q = 0; q < 4; ++q) load_row(t0 + q, raw[q]);
 
-    // rows of C written by one store pattern: both words, or single keys
-    auto store_c = [&](int r, unsigned w0, unsigned w1) {
+    // rows of C written by one store pattern: the words whole (one 8-byte or
+    // 4-byte stores: cx is even, strips start at even columns), or single keys
+    auto store_c = [&](int r, const unsigned* c) {
         unsigned short* kd = kdst0 + (size_t)r * pitch;
         if (all_out) {
-            if (al8) {
-                *reinterpret_cast<uint2*>(kd) = make_uint2(w0, w1);
+            if (kP >= 2 && al8) {
+#pragma unroll
+                for (int v = 0; v + 1 < kP; v += 2) reinterpret_cast<uint2*>(kd)[v / 2] = make_uint2(c[v], c[v + 1]);
             } else {
-                reinterpret_cast<unsigned*>(kd)[0] = w0;
-                reinterpret_cast<unsigned*>(kd)[1] = w1;
+#pragma unroll
+                for (int v = 0; v < kP; ++v) reinterpret_cast<unsigned*>(kd)[v] = c[v];
             }
         } else {
-            const unsigned k[kV] = {w0 & 0xFFFFu, w0 >> 16, w1 & 0xFFFFu, w1 >> 16};
 #pragma unroll
             for (int v = 0; v < kV; ++v)
-                if (col_out[v]) kd[v] = (unsigned short)k[v];
+                if (col_out[v]) kd[v] = (unsigned short)((v & 1) ? c[v >> 1] >> 16 : c[v >> 1] & 0xFFFFu);
         }
     };
 
@@ -430,69 +444,65 @@ __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, 
         constexpr int PHI = decltype(phi)::value;
         const int t = t0 + u0 + PHI;
         const bool row_in = t >= 0 && t < H;
-        const float dmax = fmaxf(fmaxf(raw[PHI][0], raw[PHI][1]), fmaxf(raw[PHI][2], raw[PHI][3]));
+        float dmax = raw[PHI][0];
+#pragma unroll
+        for (int v = 1; v < kV; ++v) dmax = fmaxf(dmax, raw[PHI][v]);
         quiet = (row_in && __all_sync(0xffffffffu, !(dmax >= kEmptyBelow))) ? quiet + 1 : 0;
         if (quiet > kQuiet) {
             load_row(t + 4, raw[PHI]);
             const int r = t - Rh;
-            if (r >= r0 && r < r1) store_c(r, 0u, 0u);
+            const unsigned zero[kP] = {};
+            if (r >= r0 && r < r1) store_c(r, zero);
             return;
         }
         // step 1: the keys of the inverted depths, neutral outside the frame
-        KRow x;
-        x.w[2] = __byte_perm(input_key(raw[PHI][0], bad), input_key(raw[PHI][1], bad), 0x5410);
-        x.w[3] = __byte_perm(input_key(raw[PHI][2], bad), input_key(raw[PHI][3], bad), 0x5410);
-        if (!row_in) {
-            x.w[2] = x.w[3] = kNeutralMax;
-        } else if (edge) {
-            x.w[2] &= in_mask[0];
-            x.w[3] &= in_mask[1];
-        }
+        KRow<kP> x;
+#pragma unroll
+        for (int v = 0; v < kP; ++v)
+            x.w[2 + v] = __byte_perm(input_key(raw[PHI][2 * v], bad), input_key(raw[PHI][2 * v + 1], bad), 0x5410);
+#pragma unroll
+        for (int v = 0; v < kP; ++v)
+            if (!row_in) x.w[2 + v] = kNeutralMax;
+            else if (edge) x.w[2 + v] &= in_mask[v];
         load_row(t + 4, raw[PHI]);
         // step 2: row t -> A(t - R1)
-        KRow a;
+        KRow<kP> a;
         s2.template push<PHI>(x, a.w + 2, at_left);
         const int ra = t - R1;
-        if (ra < 0 || ra >= H) {
-            a.w[2] = a.w[3] = kNeutralMax;
-        } else if (edge) {
-            a.w[2] &= in_mask[0];
-            a.w[3] &= in_mask[1];
-        }
+#pragma unroll
+        for (int v = 0; v < kP; ++v)
+            if (ra < 0 || ra >= H) a.w[2 + v] = kNeutralMax;
+            else if (edge) a.w[2 + v] &= in_mask[v];
         // step 3, dilation: A(ra) -> D(ra - 2)
-        KRow dd;
+        KRow<kP> dd;
         s3d.template push<PHI>(a, dd.w + 2, at_left);
         const int rd = ra - 2;
-        if (rd < 0 || rd >= H) {
-            dd.w[2] = dd.w[3] = kNeutralMin;
-        } else if (edge) {
-            dd.w[2] |= ~in_mask[0];
-            dd.w[3] |= ~in_mask[1];
-        }
+#pragma unroll
+        for (int v = 0; v < kP; ++v)
+            if (rd < 0 || rd >= H) dd.w[2 + v] = kNeutralMin;
+            else if (edge) dd.w[2 + v] |= ~in_mask[v];
         // step 3, erosion: D(rd) -> B(rd - 2)
-        KRow b;
+        KRow<kP> b;
         s3e.template push<PHI>(dd, b.w + 2, at_left);
         const int rb = rd - 2;
-        if (rb < 0 || rb >= H) {
-            b.w[2] = b.w[3] = kNeutralMax;
-        } else if (edge) {
-            b.w[2] &= in_mask[0];
-            b.w[3] &= in_mask[1];
-        }
+#pragma unroll
+        for (int v = 0; v < kP; ++v)
+            if (rb < 0 || rb >= H) b.w[2 + v] = kNeutralMax;
+            else if (edge) b.w[2 + v] &= in_mask[v];
         // step 4: B(rb) -> C(rb - 3)
         unsigned c[kP];
         s4.template push<PHI>(b, c, at_left);
         const int rc = rb - 3;  // == t - Rh
         if (rc >= r0 && rc < r1) {
-            store_c(rc, c[0], c[1]);
+            store_c(rc, c);
             if (tops_pending) {
-                const unsigned k[kV] = {c[0] & 0xFFFFu, c[0] >> 16, c[1] & 0xFFFFu, c[1] >> 16};
                 bool left = false;
 #pragma unroll
                 for (int v = 0; v < kV; ++v) {
-                    if (col_out[v] && k[v] > kEmptyKeyMax && top_row[v] == INT_MAX) {
+                    const unsigned k = (v & 1) ? c[v >> 1] >> 16 : c[v >> 1] & 0xFFFFu;
+                    if (col_out[v] && k > kEmptyKeyMax && top_row[v] == INT_MAX) {
                         top_row[v] = rc;
-                        top_key[v] = k[v];
+                        top_key[v] = k;
                     }
                     left |= col_out[v] && top_row[v] == INT_MAX;
                 }
@@ -518,7 +528,7 @@ __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, 
 // next unclaimed unit from work[2]; unit 0 zeroes work[0] and work[1] for
 // stage B.  A unit whose inputs are off the key grid goes to the fallback
 // list (fallback[0]: its length, then the units from fallback[2]).
-template <int S>
+template <int S, int kP>
 __global__ void __launch_bounds__(kThreadsA, kStageAKeysWarpsPerSM)
 stage_a_keys(const FrameDesc* __restrict__ frames, int n_frames, int total_units, int* __restrict__ work,
              int band_stride, int* __restrict__ fallback)
@@ -530,7 +540,7 @@ stage_a_keys(const FrameDesc* __restrict__ frames, int n_frames, int total_units
     if (unit == 0 && lane < 2) work[lane] = 0;  // step-6 count, stage-B tile counter
     const int warps = gridDim.x * (kThreadsA / 32);
     while (unit < total_units) {  // whole warps only
-        if (!keys_unit<S>(frames, n_frames, unit, band_stride) && lane == 0) {
+        if (!keys_unit<S, kP>(frames, n_frames, unit, band_stride) && lane == 0) {
             const int slot = atomicAdd(fallback, 1);
             fallback[2 + slot] = unit;
         }
@@ -540,7 +550,7 @@ stage_a_keys(const FrameDesc* __restrict__ frames, int n_frames, int total_units
     }
 }
 
-template <int S>
+template <int S, int kP>
 cudaError_t launch_shape(const FrameDesc* d_frames, int n_frames, int total_units, int* work, int band_stride,
                          int* fallback, int sm_count, cudaStream_t stream)
 {
@@ -548,24 +558,36 @@ cudaError_t launch_shape(const FrameDesc* d_frames, int n_frames, int total_unit
     int grid = (total_units + per_block - 1) / per_block;
     if (grid > kStageAKeysWarpsPerSM * sm_count) grid = kStageAKeysWarpsPerSM * sm_count;  // persistent
     if (grid < 1) return cudaSuccess;
-    return launch_after_previous(stage_a_keys<S>, dim3(grid), dim3(kThreadsA), 0, stream, d_frames, n_frames,
+    return launch_after_previous(stage_a_keys<S, kP>, dim3(grid), dim3(kThreadsA), 0, stream, d_frames, n_frames,
                                  total_units, work, band_stride, fallback);
+}
+
+template <int kP>
+cudaError_t launch_words(const FrameDesc* d_frames, int n_frames, int total_units, int shape, int* work,
+                         int band_stride, int* fallback, int sm_count, cudaStream_t stream)
+{
+    switch (shape) {
+    case kDiamond5: return launch_shape<kDiamond5, kP>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
+    case kFull5: return launch_shape<kFull5, kP>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
+    case kCross5: return launch_shape<kCross5, kP>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
+    case kFull3: return launch_shape<kFull3, kP>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
+    case kCircle5: return launch_shape<kCircle5, kP>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
+    case kFull7: return launch_shape<kFull7, kP>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_stage_a_keys(const FrameDesc* d_frames, int n_frames, int total_units, int shape, int* work,
-                                int band_stride, int* fallback, int sm_count, cudaStream_t stream)
+cudaError_t launch_stage_a_keys(const FrameDesc* d_frames, int n_frames, int total_units, int shape, int strip_cols,
+                                int* work, int band_stride, int* fallback, int sm_count, cudaStream_t stream)
 {
-    switch (shape) {
-    case kDiamond5: return launch_shape<kDiamond5>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
-    case kFull5: return launch_shape<kFull5>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
-    case kCross5: return launch_shape<kCross5>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
-    case kFull3: return launch_shape<kFull3>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
-    case kCircle5: return launch_shape<kCircle5>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
-    case kFull7: return launch_shape<kFull7>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
-    default: return cudaErrorInvalidValue;
-    }
+    if (strip_cols == 64)
+        return launch_words<1>(d_frames, n_frames, total_units, shape, work, band_stride, fallback, sm_count, stream);
+    if (strip_cols == 128)
+        return launch_words<2>(d_frames, n_frames, total_units, shape, work, band_stride, fallback, sm_count, stream);
+
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace dcgb

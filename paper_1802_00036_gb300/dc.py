@@ -49,7 +49,7 @@ class dc_params(ctypes.Structure):
 
 class dc_tuning(ctypes.Structure):
     _fields_ = [("a_warps_per_sm", ctypes.c_int), ("b_ctas_per_sm", ctypes.c_int),
-                ("b_sparse_fill", ctypes.c_int)]
+                ("b_sparse_fill", ctypes.c_int), ("a_strip_cols", ctypes.c_int)]
 
 
 class dc_server_stats(ctypes.Structure):
@@ -278,23 +278,24 @@ def dc_metrics(ctx, pred_ptr: int, gt_ptr: int, n: int, H: int, W: int, stream: 
     return [tuple(out[5 * i:5 * i + 5]) for i in range(n)]
 
 
-def dc_set_tuning(ctx, a_warps_per_sm: int, b_ctas_per_sm: int, b_sparse_fill: int = 160) -> None:
-    t = dc_tuning(int(a_warps_per_sm), int(b_ctas_per_sm), int(b_sparse_fill))
+def dc_set_tuning(ctx, a_warps_per_sm: int, b_ctas_per_sm: int, b_sparse_fill: int = 160,
+                  a_strip_cols: int = 128) -> None:
+    t = dc_tuning(int(a_warps_per_sm), int(b_ctas_per_sm), int(b_sparse_fill), int(a_strip_cols))
     _check(load().dc_set_tuning(ctx, ctypes.byref(t)), "dc_set_tuning")
 
 
-def dc_get_tuning(ctx) -> tuple[int, int, int]:
+def dc_get_tuning(ctx) -> tuple[int, int, int, int]:
     t = dc_tuning()
     _check(load().dc_get_tuning(ctx, ctypes.byref(t)), "dc_get_tuning")
-    return t.a_warps_per_sm, t.b_ctas_per_sm, t.b_sparse_fill
+    return t.a_warps_per_sm, t.b_ctas_per_sm, t.b_sparse_fill, t.a_strip_cols
 
 
 def dc_autotune(ctx, in_ptr: int, out_ptr: int, n: int, H: int, W: int, p: dc_params,
-                stream: int = 0) -> tuple[int, int, int]:
+                stream: int = 0) -> tuple[int, int, int, int]:
     t = dc_tuning()
     _check(load().dc_autotune(ctx, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), n, H, W, ctypes.byref(p),
                               ctypes.c_void_p(stream), ctypes.byref(t)), "dc_autotune")
-    return t.a_warps_per_sm, t.b_ctas_per_sm, t.b_sparse_fill
+    return t.a_warps_per_sm, t.b_ctas_per_sm, t.b_sparse_fill, t.a_strip_cols
 
 
 def dc_last_launch_count(ctx) -> int:

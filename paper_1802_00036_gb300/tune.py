@@ -2,7 +2,8 @@
 
 `dc_autotune` (C-ABI) times the chain on the caller's frames under a fixed
 set of tunings -- stage-A warps per SM (how many row bands the streaming
-kernel cuts a batch into) and stage-B persistent CTAs per SM -- and keeps
+kernel cuts a batch into), its strip width, stage-B persistent CTAs per SM
+and the step-6 threshold -- and keeps
 the fastest.  This module caches the result per (GPU, SM count, batch size,
 frame size, chain parameters) so that a later process reuses it.  Results
 never depend on the tuning; only the time does.
@@ -54,7 +55,7 @@ def save_cache(data: dict, path: str | None = None) -> None:
 def tuned(ctx, inp, out, p: dc.dc_params | None = None, stream=None, use_cache: bool = True):
     """Apply the best tuning for this workload to `ctx` (from the cache, or by
     running dc_autotune on `inp` -> `out`, (n, H, W) float32 CUDA tensors) and
-    return ((a_warps_per_sm, b_ctas_per_sm, b_sparse_fill), source)."""
+    return ((a_warps_per_sm, b_ctas_per_sm, b_sparse_fill, a_strip_cols), source)."""
     import torch
     p = p if p is not None else dc.params()
     n, H, W = inp.shape
@@ -62,10 +63,10 @@ def tuned(ctx, inp, out, p: dc.dc_params | None = None, stream=None, use_cache: 
     key = cache_key(props.name, props.multi_processor_count, n, H, W, p)
     with _lock:
         data = load_cache() if use_cache else {}
-        if key in data and len(data[key]) == 3:
-            a, b, f = data[key]
-            dc.dc_set_tuning(ctx.h, a, b, f)
-            return (a, b, f), "cache"
+        if key in data and len(data[key]) == 4:
+            a, b, f, c = data[key]
+            dc.dc_set_tuning(ctx.h, a, b, f, c)
+            return (a, b, f, c), "cache"
     s = Context_stream(stream)
     t = dc.dc_autotune(ctx.h, inp.data_ptr(), out.data_ptr(), n, H, W, p, s)
     if use_cache:

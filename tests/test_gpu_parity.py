@@ -434,21 +434,42 @@ def test_results_do_not_depend_on_tuning(ctx):
     frames = synth.make_batch(6, synth.UNIFORM_375, config=4)
     x = torch.from_numpy(frames).cuda()
     ref = None
-    for a, b, f in ((12, 3, 16), (1, 1, 0), (3, 2, 160), (64, 1, 4), (8, 4, 160), (2, 5, 8), (8, 5, 160)):
-        dc.dc_set_tuning(ctx.h, a, b, f)
+    for a, b, f, c in ((12, 3, 16, 128), (1, 1, 0, 64), (3, 2, 160, 128), (64, 1, 4, 64), (8, 4, 160, 128),
+                       (2, 5, 8, 64), (16, 5, 160, 64), (8, 5, 160, 128)):
+        dc.dc_set_tuning(ctx.h, a, b, f, c)
         y = torch.full_like(x, -2.0)
         ctx.complete(x, y)
         torch.cuda.synchronize()
         got = y.cpu().numpy().view(np.uint32)
         if ref is None:
             ref = got
-        assert np.array_equal(got, ref), (a, b)
+        assert np.array_equal(got, ref), (a, b, f, c)
     y = torch.empty_like(x)
-    a, b, f = dc.dc_autotune(ctx.h, x.data_ptr(), y.data_ptr(), 6, 375, 1242, dc.params())
-    assert 1 <= a <= 64 and 1 <= b <= 5 and 0 <= f <= 160 and dc.dc_get_tuning(ctx.h) == (a, b, f)
+    a, b, f, c = dc.dc_autotune(ctx.h, x.data_ptr(), y.data_ptr(), 6, 375, 1242, dc.params())
+    assert 1 <= a <= 64 and 1 <= b <= 5 and 0 <= f <= 160 and c in (64, 128)
+    assert dc.dc_get_tuning(ctx.h) == (a, b, f, c)
     dc.dc_set_tuning(ctx.h, 8, 5, 160)
     with pytest.raises(dc.DcError):
         dc.dc_set_tuning(ctx.h, 0, 3)
+    with pytest.raises(dc.DcError):
+        dc.dc_set_tuning(ctx.h, 8, 5, 160, 96)
+
+
+@pytest.mark.parametrize("shape", ["diamond5", "full5", "cross5", "full3", "circle5", "full7"])
+@pytest.mark.parametrize("quantize", [False, True])
+def test_narrow_strips_every_element(ctx, shape, quantize):
+    # stage A in 64-column strips (two columns per lane) for every element, on
+    # keys and (off-grid depths) through the float kernel's fallback on the
+    # narrow strips' units; frames wider than one strip with a ragged tail
+    from paper_1802_00036_gb300 import dc
+    f = synth.random_sparse(70, 233, 0.12, 61, quantize=quantize)
+    dc.dc_set_tuning(ctx.h, 8, 5, 160, 64)
+    try:
+        for stop in ("extend", "median", "full"):
+            compare(gpu_run(ctx, f[None], first_kernel=shape, stop_after=stop)[0],
+                    oracle.complete(f, first_kernel=shape, stop_after=stop), stop, f"{shape} narrow")
+    finally:
+        dc.dc_set_tuning(ctx.h, 8, 5, 160)
 
 
 def test_profiling_one_call_in_several(ctx):
