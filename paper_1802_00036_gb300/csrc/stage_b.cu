@@ -1058,11 +1058,17 @@ __device__ bool tile_keys(const Tile& T, const StageBParams& p, const MainSmem& 
         const unsigned m0 = (ncol > 0 ? 0xFFFFu : 0u) | (ncol > 1 ? 0xFFFF0000u : 0u);
         const unsigned m1 = (ncol > 2 ? 0xFFFFu : 0u) | (ncol > 3 ? 0xFFFF0000u : 0u);
         const int klo = max(0, 4 - T.y0), khi = min(kER, H - T.y0 + 4);  // in-frame region rows
-        int ct[4];
-        unsigned ck[4];
+        // step 5 per column: region rows [elo, elo + espan) (the rows above
+        // the top within the cap, inside the frame) take the top's key
+        int elo[4];
+        unsigned espan[4], ck[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            ct[e] = ext_tile ? S.ctop[4 * q + e] : kNoTop;
+            const int top = ext_tile ? S.ctop[4 * q + e] : kNoTop;
+            const int hi = top == kNoTop ? 0 : min(khi, top - (T.y0 - 4));
+            const int lo = max(klo, (top == kNoTop || p.extend_rows < 0) ? 0 : top - p.extend_rows - (T.y0 - 4));
+            elo[e] = lo;
+            espan[e] = (e < ncol && hi > lo) ? (unsigned)(hi - lo) : 0u;
             ck[e] = S.ctv[4 * q + e];
         }
         const unsigned short* src = Ek + ko + 4 * q;
@@ -1071,21 +1077,24 @@ __device__ bool tile_keys(const Tile& T, const StageBParams& p, const MainSmem& 
             uint2 a = *reinterpret_cast<const uint2*>(src + kp * kKeyBoxW);
             uint2 b = *reinterpret_cast<const uint2*>(src + kb * kKeyBoxW);
             const bool ina = kp >= klo && kp < khi, inb = kb >= klo && kb < khi;
+            // chunks wholly inside the frame (nearly all) need no masks
+            const bool inside = ncol == 4 && ina && inb;
             const unsigned ma0 = ina ? m0 : 0u, ma1 = ina ? m1 : 0u;
             const unsigned mb0 = inb ? m0 : 0u, mb1 = inb ? m1 : 0u;
-            a.x &= ma0;
-            a.y &= ma1;
-            b.x &= mb0;
-            b.y &= mb1;
+            if (!inside) {
+                a.x &= ma0;
+                a.y &= ma1;
+                b.x &= mb0;
+                b.y &= mb1;
+            }
             if (ext_tile) {  // step 5: a position above its column's top takes the top's key
-                const int ya = T.y0 - 4 + kp, yb = ya + kHalf;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const unsigned sh = (e & 1) * 16, hm = 0xFFFFu << sh, kv = ck[e] << sh;
                     unsigned& wa = e < 2 ? a.x : a.y;
                     unsigned& wb = e < 2 ? b.x : b.y;
-                    if (((e < 2 ? ma0 : ma1) & hm) && above_top(p, ya, ct[e])) wa = (wa & ~hm) | kv;
-                    if (((e < 2 ? mb0 : mb1) & hm) && above_top(p, yb, ct[e])) wb = (wb & ~hm) | kv;
+                    if ((unsigned)(kp - elo[e]) < espan[e]) wa = (wa & ~hm) | kv;
+                    if ((unsigned)(kb - elo[e]) < espan[e]) wb = (wb & ~hm) | kv;
                 }
             }
             mx = __vimax3_u16x2(mx, a.x, a.y);
@@ -1093,10 +1102,17 @@ __device__ bool tile_keys(const Tile& T, const StageBParams& p, const MainSmem& 
             if (kFill) {
                 // empty in-frame positions (key <= kEmptyKeyMax); out-of-frame ones
                 // are lifted out of the way.  Most chunks hold none: their
-                // smallest key tells
-                const unsigned la0 = a.x | ~ma0, la1 = a.y | ~ma1, lb0 = b.x | ~mb0, lb1 = b.y | ~mb1;
+                // smallest key tells (adding 0x8000 - 26 to a half sets its top
+                // bit exactly when its key is not empty; keys are below 0x8000)
+                unsigned la0 = a.x, la1 = a.y, lb0 = b.x, lb1 = b.y;
+                if (!inside) {
+                    la0 |= ~ma0;
+                    la1 |= ~ma1;
+                    lb0 |= ~mb0;
+                    lb1 |= ~mb1;
+                }
                 const unsigned mn = __vminu2(__vimin3_u16x2(la0, la1, lb0), lb1);
-                if ((mn & 0xFFFFu) <= kEmptyKeyMax || (mn >> 16) <= kEmptyKeyMax) {
+                if (((__vminu2(mn, 0x7FFF7FFFu) + 0x7FE67FE6u) & 0x80008000u) != 0x80008000u) {
                     unsigned ea = 0u, eb = 0u;
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
