@@ -3,17 +3,20 @@
 // The paper has no serving system; this serves the chain to several sensors
 // whose frames arrive one at a time.  One worker thread owns all device work:
 //   admit     a submitted frame takes a free device slot (room for an input
-//             and an output frame of the largest size; the frame lies dense in
-//             it, so each copy is contiguous) and is copied in on the
-//             upload stream; with no free slot it waits (back-pressure);
+//             frame of the largest size; the frame lies dense in it, so its
+//             copy is contiguous) and is copied in on the upload stream; with
+//             no free slot it waits (back-pressure);
 //   batch     the uploaded frames form a batch when max_batch are ready or the
 //             oldest has waited deadline_us since its submission, and the batch
 //             runs as one dc_complete on a free lane (its own context, scratch
-//             reserved for a full batch, and stream), followed on that stream by
-//             the copies of every result into the caller's host buffer;
-//   complete  when a lane's event has passed, its frames are reported done with
-//             their latency (submission to result in host memory) and their
-//             slots and the lane are free again.
+//             reserved for a full batch, stream, and an output buffer in which
+//             the batch's results lie dense), followed on that stream by the
+//             copies of every result into the caller's host buffer;
+//   complete  when a lane's kernels have passed, its frames' slots are free
+//             again (a slot is held from its copy in to the end of the kernels,
+//             not to the end of the copies out); when its copies have passed,
+//             its frames are reported done with their latency (submission to
+//             result in host memory) and the lane is free again.
 // Submission and polling only touch two queues under a mutex, so any thread
 // may call them while the worker runs.
 #include "../../include/dc.h"
@@ -42,14 +45,26 @@ struct Req {
     unsigned long long tag = 0;
     Clock::time_point t0;
     int slot = -1;
-    int ev = -1;  // upload event recorded after its copy in
+    int ev = -1;   // upload event recorded after its copy in
+    int ups = -1;  // the upload stream it was copied on
 };
+
+// Copies in round-robin over kUploadStreams streams and copies out over
+// kDownloadStreams streams per lane, so that several transfers are in flight
+// at once and each one's start-up is hidden behind the others.
+constexpr int kUploadStreams = 4;
+constexpr int kDownloadStreams = 2;
 
 struct Lane {
     dc_ctx* ctx = nullptr;
     cudaStream_t st = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaStream_t down[kDownloadStreams] = {};
+    cudaEvent_t down_done[kDownloadStreams] = {};
+    cudaEvent_t kernels = nullptr;  // after the batch's kernels: its slots are free
+    cudaEvent_t done = nullptr;     // after its copies out
+    float* d_out = nullptr;         // the batch's results, dense
     bool busy = false;
+    bool slots_held = false;
     std::vector<Req> batch;
 };
 
@@ -67,8 +82,8 @@ struct dc_server {
     int deadline_us = 0;
     int max_batch = 1;
     float* d_in = nullptr;
-    float* d_out = nullptr;
-    cudaStream_t upload = nullptr;
+    cudaStream_t upload[kUploadStreams] = {};
+    int up_turn = 0;
     std::vector<cudaEvent_t> up_ev;
     int up_next = 0;
     std::vector<Lane> lanes;
@@ -116,9 +131,11 @@ void dc_server::run()
             free_slots.pop_back();
             // a frame lies dense in its slot (row pitch W): one contiguous copy
             float* dst = d_in + (size_t)r.slot * slot_floats;
+            r.ups = up_turn;
+            up_turn = (up_turn + 1) % kUploadStreams;
             if (cudaMemcpyAsync(dst, r.in, (size_t)r.H * r.W * sizeof(float), cudaMemcpyHostToDevice,
-                                upload) != cudaSuccess ||
-                cudaEventRecord(up_ev[up_next], upload) != cudaSuccess) {
+                                upload[r.ups]) != cudaSuccess ||
+                cudaEventRecord(up_ev[up_next], upload[r.ups]) != cudaSuccess) {
                 cudaGetLastError();
                 fail(DC_ERR_CUDA);
             }
@@ -127,10 +144,22 @@ void dc_server::run()
             ready.push_back(r);
             progress = true;
         }
-        // complete: lanes whose results are in host memory
+        // complete: lanes whose kernels have passed give their slots back;
+        // lanes whose results are in host memory report them
         const Clock::time_point now = Clock::now();
         for (Lane& l : lanes) {
             if (!l.busy) continue;
+            if (l.slots_held) {
+                const cudaError_t qk = cudaEventQuery(l.kernels);
+                if (qk == cudaErrorNotReady) continue;
+                if (qk != cudaSuccess) {
+                    cudaGetLastError();
+                    fail(DC_ERR_CUDA);
+                }
+                for (const Req& r : l.batch) free_slots.push_back(r.slot);
+                l.slots_held = false;
+                progress = true;
+            }
             const cudaError_t q = cudaEventQuery(l.done);
             if (q == cudaErrorNotReady) continue;
             if (q != cudaSuccess) {
@@ -143,7 +172,6 @@ void dc_server::run()
                 for (const Req& r : l.batch)
                     finished.emplace_back(r.tag, std::chrono::duration<double, std::milli>(t - r.t0).count());
             }
-            for (const Req& r : l.batch) free_slots.push_back(r.slot);
             n_done += l.batch.size();
             ++n_batches;
             l.batch.clear();
@@ -161,23 +189,34 @@ void dc_server::run()
             l.batch.assign(ready.begin(), ready.begin() + n);
             ready.erase(ready.begin(), ready.begin() + n);
             frames.resize((size_t)n);
-            int last_ev = -1;
+            int last_ev[kUploadStreams];
+            for (int k = 0; k < kUploadStreams; ++k) last_ev[k] = -1;
+            size_t off = 0;  // results lie dense in the lane's output buffer
             for (int i = 0; i < n; ++i) {
                 const Req& r = l.batch[(size_t)i];
-                frames[(size_t)i] = dc_frame{d_in + (size_t)r.slot * slot_floats, d_out + (size_t)r.slot * slot_floats,
-                                             r.H, r.W, r.W, r.W};
-                last_ev = r.ev;  // uploads are in order: the last one covers the batch
+                frames[(size_t)i] = dc_frame{d_in + (size_t)r.slot * slot_floats, l.d_out + off, r.H, r.W, r.W, r.W};
+                off += (size_t)r.H * r.W;
+                last_ev[r.ups] = r.ev;  // uploads are in order per stream: its last one covers the batch's
             }
             dc_status s = DC_OK;
-            if (cudaStreamWaitEvent(l.st, up_ev[last_ev], 0) != cudaSuccess) s = DC_ERR_CUDA;
+            for (int k = 0; s == DC_OK && k < kUploadStreams; ++k)
+                if (last_ev[k] >= 0 && cudaStreamWaitEvent(l.st, up_ev[last_ev[k]], 0) != cudaSuccess) s = DC_ERR_CUDA;
             if (s == DC_OK) s = dc_complete(l.ctx, frames.data(), n, &params, l.st);
+            if (s == DC_OK && cudaEventRecord(l.kernels, l.st) != cudaSuccess) s = DC_ERR_CUDA;
+            for (int k = 0; s == DC_OK && k < kDownloadStreams; ++k)
+                if (cudaStreamWaitEvent(l.down[k], l.kernels, 0) != cudaSuccess) s = DC_ERR_CUDA;
             for (int i = 0; s == DC_OK && i < n; ++i) {
                 const Req& r = l.batch[(size_t)i];
-                if (cudaMemcpyAsync(r.out, d_out + (size_t)r.slot * slot_floats, (size_t)r.H * r.W * sizeof(float),
-                                    cudaMemcpyDeviceToHost, l.st) != cudaSuccess)
+                if (cudaMemcpyAsync(r.out, frames[(size_t)i].out, (size_t)r.H * r.W * sizeof(float),
+                                    cudaMemcpyDeviceToHost, l.down[i % kDownloadStreams]) != cudaSuccess)
                     s = DC_ERR_CUDA;
             }
+            for (int k = 0; s == DC_OK && k < kDownloadStreams; ++k)
+                if (cudaEventRecord(l.down_done[k], l.down[k]) != cudaSuccess ||
+                    cudaStreamWaitEvent(l.st, l.down_done[k], 0) != cudaSuccess)
+                    s = DC_ERR_CUDA;
             if (s == DC_OK && cudaEventRecord(l.done, l.st) != cudaSuccess) s = DC_ERR_CUDA;
+            l.slots_held = true;
             if (s != DC_OK) {
                 cudaGetLastError();
                 fail(s);
@@ -230,19 +269,21 @@ dc_status dc_server_create(dc_server** out, int device, int max_H, int max_W, si
     cudaGetDevice(&prev);
     cudaSetDevice(device);
     dc_status st = DC_OK;
-    // each lane's scratch for a full batch of the largest frames
+    // each lane: scratch for a full batch of the largest frames (the step-4
+    // map as 16-bit keys and as floats, column tops, work lists: about 6
+    // bytes a pixel) and the batch's results; each slot one input frame
     const size_t cpitch = ((size_t)max_W + 31) / 32 * 32;
-    const size_t lane_bytes = (size_t)max_batch * ((size_t)max_H * cpitch + cpitch) * sizeof(float) + (8u << 20);
-    const size_t slot_bytes = 2 * s->slot_floats * sizeof(float);
+    const size_t lane_bytes = (size_t)max_batch * ((size_t)max_H * cpitch + cpitch) * 6 +
+                              (size_t)max_batch * s->slot_floats * sizeof(float) + (8u << 20);
+    const size_t slot_bytes = s->slot_floats * sizeof(float);
     if (budget_bytes <= (size_t)lanes * lane_bytes + slot_bytes) st = DC_ERR_OOM;
     if (st == DC_OK) {
         size_t slots = (budget_bytes - (size_t)lanes * lane_bytes) / slot_bytes;
         if (slots > 4096) slots = 4096;
         s->n_slots = (int)slots;
-        if (cudaMalloc(&s->d_in, slots * s->slot_floats * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&s->d_out, slots * s->slot_floats * sizeof(float)) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking) != cudaSuccess)
-            st = DC_ERR_OOM;
+        if (cudaMalloc(&s->d_in, slots * s->slot_floats * sizeof(float)) != cudaSuccess) st = DC_ERR_OOM;
+        for (int k = 0; st == DC_OK && k < kUploadStreams; ++k)
+            if (cudaStreamCreateWithFlags(&s->upload[k], cudaStreamNonBlocking) != cudaSuccess) st = DC_ERR_CUDA;
         for (int i = 0; i < s->n_slots; ++i) s->free_slots.push_back(s->n_slots - 1 - i);
     }
     if (st == DC_OK) {
@@ -255,9 +296,16 @@ dc_status dc_server_create(dc_server** out, int device, int max_H, int max_W, si
         Lane& l = s->lanes.back();
         st = dc_create(&l.ctx, device, 0);
         if (st == DC_OK) st = dc_reserve(l.ctx, max_batch, max_H, max_W);
+        if (st == DC_OK && cudaMalloc(&l.d_out, (size_t)max_batch * s->slot_floats * sizeof(float)) != cudaSuccess)
+            st = DC_ERR_OOM;
         if (st == DC_OK && (cudaStreamCreateWithFlags(&l.st, cudaStreamNonBlocking) != cudaSuccess ||
+                            cudaEventCreateWithFlags(&l.kernels, cudaEventDisableTiming) != cudaSuccess ||
                             cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming) != cudaSuccess))
             st = DC_ERR_CUDA;
+        for (int k = 0; st == DC_OK && k < kDownloadStreams; ++k)
+            if (cudaStreamCreateWithFlags(&l.down[k], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&l.down_done[k], cudaEventDisableTiming) != cudaSuccess)
+                st = DC_ERR_CUDA;
     }
     cudaSetDevice(prev);
     if (st != DC_OK) {
@@ -336,17 +384,26 @@ void dc_server_destroy(dc_server* s)
     for (Lane& l : s->lanes) {
         if (l.st) cudaStreamSynchronize(l.st);
         if (l.ctx) dc_destroy(l.ctx);
+        cudaFree(l.d_out);
+        if (l.kernels) cudaEventDestroy(l.kernels);
         if (l.done) cudaEventDestroy(l.done);
+        for (int k = 0; k < kDownloadStreams; ++k) {
+            if (l.down[k]) {
+                cudaStreamSynchronize(l.down[k]);
+                cudaStreamDestroy(l.down[k]);
+            }
+            if (l.down_done[k]) cudaEventDestroy(l.down_done[k]);
+        }
         if (l.st) cudaStreamDestroy(l.st);
     }
-    if (s->upload) {
-        cudaStreamSynchronize(s->upload);
-        cudaStreamDestroy(s->upload);
-    }
+    for (int k = 0; k < kUploadStreams; ++k)
+        if (s->upload[k]) {
+            cudaStreamSynchronize(s->upload[k]);
+            cudaStreamDestroy(s->upload[k]);
+        }
     for (cudaEvent_t e : s->up_ev)
         if (e) cudaEventDestroy(e);
     cudaFree(s->d_in);
-    cudaFree(s->d_out);
     cudaGetLastError();
     cudaSetDevice(prev);
     delete s;
