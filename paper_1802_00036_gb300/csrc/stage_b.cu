@@ -1639,85 +1639,109 @@ stage_b_fill_keys(const FrameDesc* __restrict__ frames, int n_frames, StageBPara
         // the passes of the doubling: steps 1, 2, 4, .. below P, then wl - P
         const int npass = (31 - __clz(P)) + (wl > P ? 1 : 0);
         // window maxima down the columns: rows [0, kER) end with the maximum
-        // over [r, r + 2 Rl]; rows beyond the region count as key 0
+        // over [r, r + 2 Rl]; rows beyond the region count as key 0.  A warp
+        // takes two word columns at a time (two independent chains)
         {
             constexpr int kVR = (kER + 2 * (kMaxLargeFill / 2) + 31) / 32;
             const int nvr = (GR + 31) / 32;  // registers in use (warp-uniform)
             const int wc0 = sh >> 1, wc1 = (sh + GC + 1) >> 1;
-            for (int wc = wc0 + warp; wc < wc1; wc += kThreadsB / 32) {
-                unsigned v[kVR];
+            constexpr int kWarps = kThreadsB / 32;
+            for (int wc = wc0 + warp; wc < wc1; wc += 2 * kWarps) {
+                const int wc2 = wc + kWarps;
+                const bool two = wc2 < wc1;  // warp-uniform
+                unsigned v[kVR], u[kVR];
 #pragma unroll
                 for (int j = 0; j < kVR; ++j) {
                     const int r = lane + 32 * j;
                     v[j] = r < GR ? Gw[r * GSW + wc] : 0u;
+                    u[j] = (two && r < GR) ? Gw[r * GSW + wc2] : 0u;
                 }
                 for (int pass = 0; pass < npass; ++pass) {
                     // v[r] = max(v[r], v[r + s]), 0 < s < 32
                     const int s = (1 << pass) < P ? (1 << pass) : wl - P;
                     const int src = (lane + s) & 31;
                     const bool wrap = lane + s >= 32;
-                    unsigned carry = 0u;  // register j + 1's shuffled word, from the step before
+                    unsigned cv = 0u, cu = 0u;  // register j + 1's shuffled words, from the step before
 #pragma unroll
                     for (int j = kVR - 1; j >= 0; --j) {
                         if (j < nvr) {
                             const unsigned a = __shfl_sync(0xffffffffu, v[j], src);
-                            const unsigned m = __vmaxu2(v[j], wrap ? carry : a);
-                            carry = a;
-                            v[j] = m;
+                            const unsigned b = __shfl_sync(0xffffffffu, u[j], src);
+                            const unsigned mv = __vmaxu2(v[j], wrap ? cv : a);
+                            const unsigned mu = __vmaxu2(u[j], wrap ? cu : b);
+                            cv = a;
+                            cu = b;
+                            v[j] = mv;
+                            u[j] = mu;
                         }
                     }
                 }
 #pragma unroll
                 for (int j = 0; j < kVR; ++j) {
                     const int r = lane + 32 * j;
-                    if (r < kER) Gw[r * GSW + wc] = v[j];
+                    if (r < kER) {
+                        Gw[r * GSW + wc] = v[j];
+                        if (two) Gw[r * GSW + wc2] = u[j];
+                    }
                 }
             }
         }
         __syncthreads();
         // window maxima along the rows [0, kER): positions [sh, sh + kEC) end
-        // with the maximum over [c, c + 2 Rl]; one warp per row, word m in
-        // lane m % 32, register m / 32, a step of s positions is the word
+        // with the maximum over [c, c + 2 Rl]; one warp per pair of rows, word
+        // m in lane m % 32, register m / 32, a step of s positions is the word
         // q = s / 2 further (s even), or the pair across words q and q + 1
         // (s odd: a byte permute)
         {
             constexpr int kPW = (fill_key_stride(kEC + 2 * (kMaxLargeFill / 2)) / 2 + 31) / 32;
+            constexpr int kWarps = kThreadsB / 32;
             const int npw = (GSW + 31) / 32;  // registers in use (warp-uniform)
-            for (int k = warp; k < kER; k += kThreadsB / 32) {
+            for (int k = warp; k < kER; k += 2 * kWarps) {
+                const int k2 = k + kWarps;
+                const bool two = k2 < kER;  // warp-uniform
                 unsigned* row = Gw + k * GSW;
-                unsigned v[kPW];
+                unsigned* row2 = Gw + (two ? k2 : k) * GSW;
+                unsigned v[kPW], u[kPW];
 #pragma unroll
                 for (int j = 0; j < kPW; ++j) {
                     const int m = lane + 32 * j;
                     v[j] = m < GSW ? row[m] : 0u;
+                    u[j] = m < GSW ? row2[m] : 0u;
                 }
                 for (int pass = 0; pass < npass; ++pass) {
                     const int s = (1 << pass) < P ? (1 << pass) : wl - P;
                     const int q = s >> 1;
                     const int src0 = (lane + q) & 31, src1 = (lane + q + 1) & 31;
                     const bool wrap0 = lane + q >= 32, wrap1 = lane + q + 1 >= 32;
-                    unsigned c0 = 0u, c1 = 0u;  // register j + 1's shuffled words
+                    unsigned c0 = 0u, c1 = 0u, d0 = 0u, d1 = 0u;  // register j + 1's shuffled words
 #pragma unroll
                     for (int j = kPW - 1; j >= 0; --j) {
                         if (j < npw) {
                             const unsigned a0 = __shfl_sync(0xffffffffu, v[j], src0);
-                            const unsigned w0 = wrap0 ? c0 : a0;  // word m + q
-                            unsigned o = w0;
+                            const unsigned b0 = __shfl_sync(0xffffffffu, u[j], src0);
+                            unsigned ov = wrap0 ? c0 : a0, ou = wrap0 ? d0 : b0;  // words m + q
                             if (s & 1) {
                                 const unsigned a1 = __shfl_sync(0xffffffffu, v[j], src1);
-                                const unsigned w1 = wrap1 ? c1 : a1;  // word m + q + 1
-                                o = __byte_perm(w0, w1, 0x5432);
+                                const unsigned b1 = __shfl_sync(0xffffffffu, u[j], src1);
+                                ov = __byte_perm(ov, wrap1 ? c1 : a1, 0x5432);  // with words m + q + 1
+                                ou = __byte_perm(ou, wrap1 ? d1 : b1, 0x5432);
                                 c1 = a1;
+                                d1 = b1;
                             }
                             c0 = a0;
-                            v[j] = __vmaxu2(v[j], o);
+                            d0 = b0;
+                            v[j] = __vmaxu2(v[j], ov);
+                            u[j] = __vmaxu2(u[j], ou);
                         }
                     }
                 }
 #pragma unroll
                 for (int j = 0; j < kPW; ++j) {
                     const int m = lane + 32 * j;
-                    if (m < GSW) row[m] = v[j];
+                    if (m < GSW) {
+                        row[m] = v[j];
+                        if (two) row2[m] = u[j];
+                    }
                 }
             }
         }
