@@ -516,8 +516,10 @@ __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, 
         step(std::integral_constant<int, 1>{}, u0);
         step(std::integral_constant<int, 2>{}, u0);
         step(std::integral_constant<int, 3>{}, u0);
+        // inputs off the key grid: the float kernel redoes the whole unit, so
+        // stop at once (one vote per four rows)
+        if (__any_sync(0xffffffffu, bad)) return false;
     }
-    if (__any_sync(0xffffffffu, bad)) return false;
 #pragma unroll
     for (int v = 0; v < kV; ++v)
         if (col_out[v] && top_row[v] != INT_MAX) atomicMin(&fd.top[cx + v], top_pack(top_row[v], top_key[v]));
