@@ -14,9 +14,10 @@
 // valid key is smaller) before a maximum, 0xFFFF before a minimum.
 //
 // Step 1 turns each input depth into its key as the row arrives; a unit
-// whose inputs are not all on the grid (or whose valid depths exceed 100 m,
-// whose inversion is negative) is appended to a fallback list and left to
-// the float kernel of stage_a.cu, which writes the whole unit again.  C's
+// with an input off the grid (a valid depth, or an empty one between 0 and
+// 0.1 m) or a depth above 100 m (whose inversion is negative) is appended to
+// a fallback list and left to the float kernel of stage_a.cu, which writes
+// the whole unit again.  C's
 // rows go out as the words themselves, the tops by the same 64-bit
 // atomicMin as there.  Only the full chain (stop == kStopFull) runs here.
 #include "common.cuh"
@@ -314,19 +315,31 @@ struct Fill7 {
     }
 };
 
-// Key of the inverted input depth: 25600 - 256 d for a valid depth (d >=
-// 0.1) on the 1/256 m grid and at most 100 m; 0 for an empty one.  A valid
-// depth off the grid or above 100 m sets `bad` (its key would not be its
-// value).  With d' = d (valid) or 100 (empty), f = 2^23 + 25600 - 256 d' is
-// exact when 256 d' is an integer no larger than 25600, its low 16 bits are
-// the key, and r = 256 d' - (2^23 + 25600 - f) is 0 exactly then.
-__device__ __forceinline__ unsigned input_key(float d, bool& bad)
+// Step 1 for two columns: the keys of their inverted depths, packed (the
+// first in the low half).  A depth d >= 0.1 on the 1/256 m grid and at most
+// 100 m has the key 25600 - 256 d; an empty one (below 0.1, negative or
+// NaN) has key 0.  With v = max(d, 0) (0 for NaN), f = 2^23 + 25600 - 256 v
+// is exact, its low 16 bits the key, when 256 v is an integer no larger
+// than 25600; r = 256 v - (2^23 + 25600 - f) is then exactly +0 (r's bits
+// are OR-ed into racc) and f >= 2^23 exactly when v <= 100 (f's minimum
+// goes to fmn): a unit whose racc is not 0 or whose fmn is below 2^23 is
+// off the key grid.  Keys >= 25575 (v <= 25/256, below 0.1) are the empty
+// ones: adding 0x8000 - 25575 to each half sets its top bit exactly then,
+// with no carry out of the half (keys are at most 25600 here), and prmt's
+// sign mode spreads the two bits into a mask of the halves to clear.  The
+// arithmetic is three FMA-pipe operations per depth.
+__device__ __forceinline__ unsigned input_word(float d0, float d1, unsigned& racc, float& fmn)
 {
-    const float dv = d >= kEmptyBelow ? d : kInvertFrom;
-    const float f = fmaf(-dv, 256.0f, 8414208.0f);          // 2^23 + 25600
-    const float r = fmaf(dv, 256.0f, f - 8414208.0f);
-    bad = bad || (r != 0.0f) || (dv > kInvertFrom);
-    return __float_as_uint(f);  // the key in the low half
+    const float v0 = fmaxf(d0, 0.0f), v1 = fmaxf(d1, 0.0f);
+    const float f0 = fmaf(-v0, 256.0f, 8414208.0f), f1 = fmaf(-v1, 256.0f, 8414208.0f);  // 2^23 + 25600
+    const float r0 = fmaf(v0, 256.0f, f0 - 8414208.0f), r1 = fmaf(v1, 256.0f, f1 - 8414208.0f);
+    racc |= __float_as_uint(r0) | __float_as_uint(r1);
+    fmn = fminf(fmn, fminf(f0, f1));
+    const unsigned w = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x5410);
+    unsigned e;
+    // selector nibbles 9 and B: the signs of bytes 1 and 3, over their halves
+    asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(e) : "r"(w + 0x1C191C19u));
+    return w & ~e;
 }
 
 // One unit of steps 1-4 on keys; false if its inputs left the key grid
@@ -397,7 +410,8 @@ __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, 
         top_key[v] = 0u;
     }
     bool tops_pending = true;
-    bool bad = false;
+    unsigned racc = 0u;      // the bits of every r of input_word: 0 on the key grid
+    float fmn = 8414208.0f;  // the smallest f of input_word: >= 2^23 for depths up to 100 m
 
     const int t0 = r0 - Rh;
     const int nsteps = (r1 - r0) + 2 * Rh;
@@ -434,9 +448,9 @@ __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, 
         }
     };
 
-    // Consecutive in-frame input rows with no valid depth: after more than
-    // kQuiet of them the rings hold what an all-empty history gives and an
-    // empty row leaves them unchanged (outputs 0), as in stage_a.cu.
+    // Consecutive in-frame input rows of zeros (empty depths): after more
+    // than kQuiet of them the rings hold what an all-empty history gives and
+    // such a row leaves them unchanged (outputs 0), as in stage_a.cu.
     constexpr int kQuiet = 2 * Rh + 4;
     int quiet = 0;
 
@@ -444,10 +458,10 @@ __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, 
         constexpr int PHI = decltype(phi)::value;
         const int t = t0 + u0 + PHI;
         const bool row_in = t >= 0 && t < H;
-        float dmax = raw[PHI][0];
+        unsigned bits = 0u;
 #pragma unroll
-        for (int v = 1; v < kV; ++v) dmax = fmaxf(dmax, raw[PHI][v]);
-        quiet = (row_in && __all_sync(0xffffffffu, !(dmax >= kEmptyBelow))) ? quiet + 1 : 0;
+        for (int v = 0; v < kV; ++v) bits |= __float_as_uint(raw[PHI][v]);
+        quiet = (row_in && __all_sync(0xffffffffu, bits == 0u)) ? quiet + 1 : 0;
         if (quiet > kQuiet) {
             load_row(t + 4, raw[PHI]);
             const int r = t - Rh;
@@ -455,15 +469,11 @@ __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, 
             if (r >= r0 && r < r1) store_c(r, zero);
             return;
         }
-        // step 1: the keys of the inverted depths, neutral outside the frame
+        // step 1: the keys of the inverted depths; rows and columns outside the
+        // frame were loaded as 0, whose key is the neutral 0
         KRow<kP> x;
 #pragma unroll
-        for (int v = 0; v < kP; ++v)
-            x.w[2 + v] = __byte_perm(input_key(raw[PHI][2 * v], bad), input_key(raw[PHI][2 * v + 1], bad), 0x5410);
-#pragma unroll
-        for (int v = 0; v < kP; ++v)
-            if (!row_in) x.w[2 + v] = kNeutralMax;
-            else if (edge) x.w[2 + v] &= in_mask[v];
+        for (int v = 0; v < kP; ++v) x.w[2 + v] = input_word(raw[PHI][2 * v], raw[PHI][2 * v + 1], racc, fmn);
         load_row(t + 4, raw[PHI]);
         // step 2: row t -> A(t - R1)
         KRow<kP> a;
@@ -518,7 +528,7 @@ __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, 
         step(std::integral_constant<int, 3>{}, u0);
         // inputs off the key grid: the float kernel redoes the whole unit, so
         // stop at once (one vote per four rows)
-        if (__any_sync(0xffffffffu, bad)) return false;
+        if (__any_sync(0xffffffffu, racc != 0u || fmn < 8388608.0f)) return false;
     }
 #pragma unroll
     for (int v = 0; v < kV; ++v)

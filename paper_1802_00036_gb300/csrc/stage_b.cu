@@ -308,15 +308,29 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
         for (int i = tid; i < kMR * (kTBW / 4); i += kThreadsB) {
             const int a = i / (kTBW / 4), b0 = 4 * (i - a * (kTBW / 4));
             if constexpr (KEYS) {
-                // exact: the integer sums k(-2) + 4 k(-1) + 6 k + 4 k(1) + k(2) of the keys
+                // the integer sums n = k(-2) + 4 k(-1) + 6 k + 4 k(1) + k(2) of the
+                // keys in float arithmetic (exact: every value is an integer below
+                // 2^24), stored as n + 1 with the sign of the centre's emptiness:
+                // +(n + 1) when its key is not empty, -(n + 1) when it is.  A key
+                // becomes a float as 2^23 + k (the key in the low bits) - 2^23.
                 const uint2 lo = *reinterpret_cast<const uint2*>(Mk + a * kMS + b0);
                 const uint2 hi = *reinterpret_cast<const uint2*>(Mk + a * kMS + b0 + 4);
-                const unsigned k[8] = {lo.x & 0xFFFFu, lo.x >> 16, lo.y & 0xFFFFu, lo.y >> 16,
-                                       hi.x & 0xFFFFu, hi.x >> 16, hi.y & 0xFFFFu, hi.y >> 16};
-                unsigned o[4];
+                const unsigned w[4] = {lo.x, lo.y, hi.x, hi.y};
+                float k[8];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) o[j] = k[j] + k[j + 4] + 4u * (k[j + 1] + k[j + 3]) + 6u * k[j + 2];
-                *reinterpret_cast<uint4*>(R + a * kRS + b0) = make_uint4(o[0], o[1], o[2], o[3]);
+                for (int j = 0; j < 4; ++j) {
+                    k[2 * j] = __uint_as_float(__byte_perm(w[j], 0x4B000000u, 0x7410)) - 8388608.0f;
+                    k[2 * j + 1] = __uint_as_float(__byte_perm(w[j], 0x4B000000u, 0x7432)) - 8388608.0f;
+                }
+                float o[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float n1 = fmaf(6.0f, k[j + 2], fmaf(4.0f, k[j + 1] + k[j + 3], k[j] + k[j + 4])) + 1.0f;
+                    // +1 when the centre's key is above kEmptyKeyMax (keys are integers), else -1
+                    const float sgn = fmaf(2.0f, __saturatef(k[j + 2] - (float)kEmptyKeyMax), -1.0f);
+                    o[j] = n1 * sgn;
+                }
+                *reinterpret_cast<float4*>(R + a * kRS + b0) = make_float4(o[0], o[1], o[2], o[3]);
             } else {
                 float v[8];
                 m_row8<KEYS>(Mf, Mk, a * kMS + b0, v);
@@ -357,6 +371,42 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
                 const bool vec = two && (T.fd.out_pitch % 2) == 0 &&
                                  (reinterpret_cast<uintptr_t>(T.fd.out + x) % sizeof(float2)) == 0;
                 float* dst = T.fd.out + (size_t)(T.y0 + a0) * T.fd.out_pitch + x;
+                if constexpr (KEYS) {
+                    if (p.stop != kStopBlur) {
+                        // sum of the weights times |R| = n + 16 for the 5 x 5 integer sum
+                        // n; 100 - n / 2^16 = c - (n + 16) / 2^16 rounded once (c = 100 +
+                        // 2^-12 is a float), times 1 (centre not empty: R > 0) or 0.  All
+                        // in float arithmetic; five rows per round so that the window
+                        // slides through the registers without moves
+                        constexpr float c = 100.0f + 16.0f / 65536.0f;
+#pragma unroll 1
+                        for (int k0 = 0; k0 < rows; k0 += 5) {
+#pragma unroll
+                            for (int u = 0; u < 5; ++u) {
+                                const int k = k0 + u;
+                                if (k < rows) {
+                                    r[(u + 4) % 5] = *reinterpret_cast<const float2*>(R + (a0 + k + 4) * kRS + b);
+                                    const float2 q0 = r[u % 5], q1 = r[(u + 1) % 5], q2 = r[(u + 2) % 5],
+                                                 q3 = r[(u + 3) % 5], q4 = r[(u + 4) % 5];
+                                    const float s0 = fmaf(6.0f, fabsf(q2.x),
+                                                          fmaf(4.0f, fabsf(q1.x) + fabsf(q3.x), fabsf(q0.x) + fabsf(q4.x)));
+                                    const float s1 = fmaf(6.0f, fabsf(q2.y),
+                                                          fmaf(4.0f, fabsf(q1.y) + fabsf(q3.y), fabsf(q0.y) + fabsf(q4.y)));
+                                    const float o0 = fmaf(-s0, 1.0f / 65536.0f, c) * __saturatef(q2.x);
+                                    const float o1 = fmaf(-s1, 1.0f / 65536.0f, c) * __saturatef(q2.y);
+                                    float* d = dst + (size_t)k * T.fd.out_pitch;
+                                    if (vec) {
+                                        *reinterpret_cast<float2*>(d) = make_float2(o0, o1);
+                                    } else {
+                                        d[0] = o0;
+                                        if (two) d[1] = o1;
+                                    }
+                                }
+                            }
+                        }
+                        return;
+                    }
+                }
 #pragma unroll 1
                 for (int k = 0; k < rows; ++k) {
                     r[4] = *reinterpret_cast<const float2*>(R + (a0 + k + 4) * kRS + b);
@@ -373,16 +423,14 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
                     }
                     float acc0, acc1;
                     if constexpr (KEYS) {
-                        // the integer 5 x 5 sum n over keys; the blur is n / 2^16 exactly
-                        // (n < 256 * 25600 < 2^23, so 2^7 + n / 2^16 is a float)
-                        const unsigned n0 = __float_as_uint(r[0].x) + __float_as_uint(r[4].x) +
-                                            4u * (__float_as_uint(r[1].x) + __float_as_uint(r[3].x)) +
-                                            6u * __float_as_uint(r[2].x);
-                        const unsigned n1 = __float_as_uint(r[0].y) + __float_as_uint(r[4].y) +
-                                            4u * (__float_as_uint(r[1].y) + __float_as_uint(r[3].y)) +
-                                            6u * __float_as_uint(r[2].y);
-                        acc0 = __uint_as_float(0x43000000u | n0) - 128.0f;
-                        acc1 = __uint_as_float(0x43000000u | n1) - 128.0f;
+                        // the blur n / 2^16 exactly (n < 256 * 25600 < 2^23): the sum of the
+                        // weights times |R| is n + 16 (the row pass's +1s)
+                        const float s0 = fmaf(6.0f, fabsf(r[2].x),
+                                              fmaf(4.0f, fabsf(r[1].x) + fabsf(r[3].x), fabsf(r[0].x) + fabsf(r[4].x)));
+                        const float s1 = fmaf(6.0f, fabsf(r[2].y),
+                                              fmaf(4.0f, fabsf(r[1].y) + fabsf(r[3].y), fabsf(r[0].y) + fabsf(r[4].y)));
+                        acc0 = fmaf(s0, 1.0f / 65536.0f, -16.0f / 65536.0f);
+                        acc1 = fmaf(s1, 1.0f / 65536.0f, -16.0f / 65536.0f);
                     } else {
                         acc0 = w0 * r[0].x;
                         acc1 = w0 * r[0].y;
