@@ -210,17 +210,14 @@ constexpr Tuning kDefaultTuning{8, 5, 160, 128};
 // take units (zeroed before stage A starts), then those tiles.  band_stride:
 // the batch's strip count when all frames have one shape (units then go
 // band by band over the whole batch, bottom bands first), else 0.
-// fallback: null, every unit (counter work[2]); else the units the key
-// kernel left: fallback[0] of them from fallback[2], taken by the counter
-// fallback[1] (zeroed before the call like work[2]).
 cudaError_t launch_stage_a(const FrameDesc* d_frames, int n_frames, int total_units,
                            int shape, int stop, int* work, int band_stride, int sm_count,
-                           cudaStream_t stream, const int* fallback = nullptr);
-// Steps 1-4 of the full chain on packed 16-bit keys (stage_a_keys.cu); a
-// unit whose inputs are off the key grid is appended to `fallback` (count in
-// fallback[0], zeroed before) for launch_stage_a with that list.
+                           cudaStream_t stream);
+// Steps 1-4 of the full chain on packed 16-bit keys (stage_a_keys.cu); the
+// warp that meets a unit whose inputs are off the key grid redoes it on
+// floats (stage_a_float.cuh).
 cudaError_t launch_stage_a_keys(const FrameDesc* d_frames, int n_frames, int total_units, int shape, int strip_cols,
-                                int* work, int band_stride, int* fallback, int sm_count, cudaStream_t stream);
+                                int* work, int band_stride, int sm_count, cudaStream_t stream);
 // cmap: with p.tma, the tensor map of the batch's step-4 maps C as a
 // W x H x n_frames array (rows c_pitch floats apart, frames H c_pitch);
 // err: set to 1 when a bounded device-side wait gives up.

@@ -233,13 +233,12 @@ static_assert(sizeof(TableChunk<352>) + 64 <= 32764, "kernel parameter space");
 template <int K>
 __global__ void table_put(const __grid_constant__ TableChunk<K> src, FrameDesc* __restrict__ dst, int n,
                           unsigned long long* __restrict__ top, size_t top_ints, int* __restrict__ counter,
-                          int* __restrict__ fallback, int* __restrict__ ffill)
+                          int* __restrict__ ffill)
 {
     allow_next_kernel();  // stage A may launch; it waits for this kernel's writes
     const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     if (counter && tid == 0) *counter = 0;
-    if (fallback && tid < 2) fallback[tid] = 0;
     if (ffill && tid == 0) *ffill = 0;
     for (size_t i = tid; i < (size_t)n; i += stride) dst[i] = src.d[i];
     if (top)
@@ -248,22 +247,22 @@ __global__ void table_put(const __grid_constant__ TableChunk<K> src, FrameDesc* 
 
 template <int K>
 cudaError_t table_put_chunk(const FrameDesc* desc, int n, FrameDesc* dst, unsigned long long* top, size_t top_ints,
-                            int* counter, int* fallback, int* ffill, int sms, cudaStream_t stream)
+                            int* counter, int* ffill, int sms, cudaStream_t stream)
 {
     TableChunk<K> c;
     std::memcpy(c.d, desc, (size_t)n * sizeof(FrameDesc));
     size_t blocks = (top_ints + 255) / 256;
     if (blocks < 1) blocks = 1;
     if (blocks > (size_t)2 * sms) blocks = (size_t)2 * sms;
-    table_put<K><<<(unsigned)blocks, 256, 0, stream>>>(c, dst, n, top, top_ints, counter, fallback, ffill);
+    table_put<K><<<(unsigned)blocks, 256, 0, stream>>>(c, dst, n, top, top_ints, counter, ffill);
     return cudaGetLastError();
 }
 
 // Store n descriptors at dst (chunks of up to 352 per launch), reset
-// top_ints column tops, zero *counter, fallback[0..1] and *ffill (when not
-// null); returns the number of launches through *launches.
+// top_ints column tops, zero *counter and *ffill (when not null); returns
+// the number of launches through *launches.
 cudaError_t put_table(const FrameDesc* desc, int n, FrameDesc* dst, unsigned long long* top, size_t top_ints,
-                      int* counter, int* fallback, int* ffill, int sms, cudaStream_t stream, int* launches)
+                      int* counter, int* ffill, int sms, cudaStream_t stream, int* launches)
 {
     *launches = 0;
     for (int i = 0; i < n; i += 352) {
@@ -271,11 +270,10 @@ cudaError_t put_table(const FrameDesc* desc, int n, FrameDesc* dst, unsigned lon
         unsigned long long* t = i == 0 ? top : nullptr;
         const size_t ti = i == 0 ? top_ints : 0;
         int* z = i == 0 ? counter : nullptr;
-        int* fb = i == 0 ? fallback : nullptr;
         int* ff = i == 0 ? ffill : nullptr;
-        cudaError_t e = m <= 8    ? table_put_chunk<8>(desc + i, m, dst + i, t, ti, z, fb, ff, sms, stream)
-                      : m <= 64   ? table_put_chunk<64>(desc + i, m, dst + i, t, ti, z, fb, ff, sms, stream)
-                                  : table_put_chunk<352>(desc + i, m, dst + i, t, ti, z, fb, ff, sms, stream);
+        cudaError_t e = m <= 8    ? table_put_chunk<8>(desc + i, m, dst + i, t, ti, z, ff, sms, stream)
+                      : m <= 64   ? table_put_chunk<64>(desc + i, m, dst + i, t, ti, z, ff, sms, stream)
+                                  : table_put_chunk<352>(desc + i, m, dst + i, t, ti, z, ff, sms, stream);
         if (e != cudaSuccess) return e;
         ++*launches;
     }
@@ -379,10 +377,9 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
     }
     if (tiles_a > INT32_MAX / 2 || tiles_b > INT32_MAX / 2) return DC_ERR_UNSUPPORTED;
 
-    // work: three counters, the step-6 tile list, stage A's fallback list
-    // (two counters and the units), the float step-6 list (a count and the tiles)
-    const size_t fb_off = need_b ? (size_t)tiles_b + 3 : 3;
-    const size_t ff_off = fb_off + 2 + (size_t)tiles_a;
+    // work: three counters, the step-6 tile list, the float step-6 list (a
+    // count and the tiles)
+    const size_t ff_off = need_b ? (size_t)tiles_b + 3 : 3;
     dc_status s = grow(ctx, need_b ? c_off : 0, need_b ? top_off : 0, n, 0,
                        need_b ? ff_off + 1 + (size_t)tiles_b : 3);
     if (s != DC_OK) return s;
@@ -402,10 +399,9 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         return DC_ERR_CUDA;
     // the descriptors and the reset of the tops, written by a kernel
     int table_launches = 0;
-    int* fallback = need_b ? ctx->work + fb_off : nullptr;
     int* ffill = need_b ? ctx->work + ff_off : nullptr;
     if (put_table(desc.data(), n, ctx->table, need_b ? ctx->top : nullptr, need_b ? top_off : 0, ctx->work + 2,
-                  fallback, ffill, ctx->sm_count, stream, &table_launches) != cudaSuccess)
+                  ffill, ctx->sm_count, stream, &table_launches) != cudaSuccess)
         return DC_ERR_CUDA;
 
     cudaEvent_t* ev = nullptr;
@@ -420,22 +416,19 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
     bool one_shape = true;
     for (int i = 1; i < n && one_shape; ++i) one_shape = frames[i].H == frames[0].H && frames[i].W == frames[0].W;
     const int band_stride = one_shape ? (int)total_strips : 0;
-    // the full chain: steps 1-4 on keys, then the float kernel on the units
-    // whose inputs are off the key grid (none, usually: its warps leave at
-    // once); a stop before step 5: the float kernel on every unit
+    // the full chain: steps 1-4 on keys (a unit whose inputs are off the
+    // key grid on floats, by the same warp); a stop before step 5: the float
+    // kernel on every unit
     cudaError_t e = cudaSuccess;
     if (stop_a == kStopFull) {
         e = launch_stage_a_keys(ctx->table, n, (int)tiles_a, p->first_kernel, strip_cols, ctx->work, band_stride,
-                                fallback, ctx->sm_count, stream);
-        if (e == cudaSuccess)
-            e = launch_stage_a(ctx->table, n, (int)tiles_a, p->first_kernel, stop_a, ctx->work, band_stride,
-                               ctx->sm_count, stream, fallback);
+                                ctx->sm_count, stream);
     } else {
         e = launch_stage_a(ctx->table, n, (int)tiles_a, p->first_kernel, stop_a, ctx->work, band_stride,
                            ctx->sm_count, stream);
     }
     if (e != cudaSuccess) return DC_ERR_CUDA;
-    ctx->last_launches = table_launches + (stop_a == kStopFull ? 2 : 1);
+    ctx->last_launches = table_launches + 1;
     if (ev && cudaEventRecord(ev[1], stream) != cudaSuccess) return DC_ERR_CUDA;
     if (need_b) {
         StageBParams bp{};
@@ -458,8 +451,8 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         e = launch_stage_b(ctx->table, n, (int)tiles_b, bp, ctx->work, ffill, ctx->sm_count, ctx->tune.b_ctas_per_sm,
                            tma ? &ctx->cmap : nullptr, ctx->err, stream);
         if (e != cudaSuccess) return DC_ERR_CUDA;
-        // stage A is two kernels, stage B one plus the two step-6 passes when step 6 can run
-        ctx->last_launches = table_launches + ((bp.large_fill_on && bp.stop != kStopExtend) ? 5 : 3);
+        // stage A is one kernel, stage B one plus the two step-6 passes when step 6 can run
+        ctx->last_launches = table_launches + ((bp.large_fill_on && bp.stop != kStopExtend) ? 4 : 2);
     }
     if (ev && cudaEventRecord(ev[2], stream) != cudaSuccess) return DC_ERR_CUDA;
     if (capture) return DC_OK;
@@ -610,10 +603,9 @@ dc_status dc_reserve(dc_ctx* ctx, int n_frames, int H, int W)
     if (!ctx || n_frames < 0 || H < 1 || W < 1) return DC_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     const size_t tiles = (size_t)ceil_div(W, kTileBW) * (size_t)ceil_div(H, kTileBH) * (size_t)n_frames;
-    // stage-A units: the most strips (the widest halo) times bands of at least 8 rows
-    const size_t units = (size_t)stage_a_strips(W, kFull7, 64) * (size_t)ceil_div(H, 8) * (size_t)n_frames;
+    // work: three counters, the step-6 list, the float step-6 list and its count
     return note(ctx, grow(ctx, frame_c_floats(H, W) * (size_t)n_frames,
-                          frame_top_ints(W) * (size_t)n_frames, n_frames, 0, 2 * tiles + 6 + units));
+                          frame_top_ints(W) * (size_t)n_frames, n_frames, 0, 2 * tiles + 4));
 }
 
 dc_status dc_complete(dc_ctx* ctx, const dc_frame* frames, int n_frames, const dc_params* params,

@@ -65,13 +65,11 @@ dc_status setup(int dev, unsigned char** ptr, int* sms)
 __global__ void noalloc_prepare(FrameDesc* table, unsigned long long* top, unsigned short* ckeys, float* cmap,
                                 const float* in, float* out,
                                 int n, int H, int W, int c_pitch, int tiles_x_a, int ow_a, int tiles_a, int band_a,
-                                int tiles_x_b, int tiles_b, int top_ints, int* counter, int* fallback, int* ffill,
-                                int* err)
+                                int tiles_x_b, int tiles_b, int top_ints, int* counter, int* ffill, int* err)
 {
     allow_next_kernel();  // stage A may launch; it waits for this kernel's writes
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
-    if (tid < 2) fallback[tid] = 0;  // stage A's fallback list: length, taken
     if (tid == 0) *ffill = 0;        // stage B's float step-6 list: length
     if (tid == 0) {
         *counter = 0;  // stage A's unit counter
@@ -141,14 +139,11 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     const int tiles_a = tiles_x_a * ((H + band_a - 1) / band_a);
     const int tiles_x_b = (W + kTileBW - 1) / kTileBW;
     const int tiles_b = tiles_x_b * ((H + kTileBH - 1) / kTileBH);
-    // work: three counters, the step-6 tile list, stage A's fallback list
-    // (two counters and the units), the float step-6 list (a count and the
-    // tiles), the error word last
-    if ((long long)tiles_a * n > INT32_MAX / 2 ||
-        2 * (long long)tiles_b * n + 6 + (long long)tiles_a * n + 1 > DC_NOALLOC_WORK_INTS)
+    // work: three counters, the step-6 tile list, the float step-6 list (a
+    // count and the tiles), the error word last
+    if ((long long)tiles_a * n > INT32_MAX / 2 || 2 * (long long)tiles_b * n + 4 + 1 > DC_NOALLOC_WORK_INTS)
         return DC_ERR_UNSUPPORTED;
-    int* fallback = work + 3 + (size_t)tiles_b * n;
-    int* ffill = fallback + 2 + (size_t)tiles_a * n;
+    int* ffill = work + 3 + (size_t)tiles_b * n;
     cudaStream_t st = (cudaStream_t)stream;
 
     const int top_ints = need_b ? (int)((size_t)n * c_pitch) : 0;
@@ -158,16 +153,14 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
     noalloc_prepare<<<blocks, threads, 0, st>>>(table, need_b ? top : nullptr, need_b ? ckeys : nullptr,
                                                  need_b ? cmap : nullptr,
                                                  in, out, n, H, W, (int)c_pitch, tiles_x_a, ow_a, tiles_a, band_a,
-                                                 tiles_x_b, tiles_b, top_ints, work + 2, fallback, ffill,
+                                                 tiles_x_b, tiles_b, top_ints, work + 2, ffill,
                                                  work + DC_NOALLOC_WORK_INTS - 1);
     if (cudaGetLastError() != cudaSuccess) return DC_ERR_CUDA;
 
     const int stop_a = need_b ? kStopFull : params->stop_after;
-    if (need_b) {  // steps 1-4 on keys, then the units off the key grid on floats
-        if (launch_stage_a_keys(table, n, tiles_a * n, params->first_kernel, strip_cols, work, tiles_x_a * n,
-                                fallback, sms, st) != cudaSuccess ||
-            launch_stage_a(table, n, tiles_a * n, params->first_kernel, stop_a, work, tiles_x_a * n, sms, st,
-                           fallback) != cudaSuccess)
+    if (need_b) {  // steps 1-4 on keys (a unit off the key grid on floats, by the same warp)
+        if (launch_stage_a_keys(table, n, tiles_a * n, params->first_kernel, strip_cols, work, tiles_x_a * n, sms,
+                                st) != cudaSuccess)
             return DC_ERR_CUDA;
     } else if (launch_stage_a(table, n, tiles_a * n, params->first_kernel, stop_a, work, tiles_x_a * n, sms, st) !=
                cudaSuccess) {

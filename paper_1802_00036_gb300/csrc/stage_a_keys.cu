@@ -16,11 +16,11 @@
 // Step 1 turns each input depth into its key as the row arrives; a unit
 // with an input off the grid (a valid depth, or an empty one between 0 and
 // 0.1 m) or a depth above 100 m (whose inversion is negative) is appended to
-// a fallback list and left to the float kernel of stage_a.cu, which writes
-// the whole unit again.  C's
+// the float unit of stage_a_float.cuh, which the same warp runs at once:
+// it writes the whole unit again.  C's
 // rows go out as the words themselves, the tops by the same 64-bit
 // atomicMin as there.  Only the full chain (stop == kStopFull) runs here.
-#include "common.cuh"
+#include "stage_a_float.cuh"
 
 #include <climits>
 #include <type_traits>
@@ -538,12 +538,14 @@ __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, 
 
 // Persistent, as stage_a_stream: warp w starts with unit w, then takes the
 // next unclaimed unit from work[2]; unit 0 zeroes work[0] and work[1] for
-// stage B.  A unit whose inputs are off the key grid goes to the fallback
-// list (fallback[0]: its length, then the units from fallback[2]).
+// stage B.  A unit whose inputs are off the key grid is done again on
+// floats by the same warp (the float unit needs more registers than this
+// kernel's 128: it spills, on a path that KITTI's 1/256 m depths never
+// take).
 template <int S, int kP>
 __global__ void __launch_bounds__(kThreadsA, kStageAKeysWarpsPerSM)
 stage_a_keys(const FrameDesc* __restrict__ frames, int n_frames, int total_units, int* __restrict__ work,
-             int band_stride, int* __restrict__ fallback)
+             int band_stride)
 {
     wait_previous_kernel();  // the frame table, the reset tops and counters
     allow_next_kernel();
@@ -552,10 +554,8 @@ stage_a_keys(const FrameDesc* __restrict__ frames, int n_frames, int total_units
     if (unit == 0 && lane < 2) work[lane] = 0;  // step-6 count, stage-B tile counter
     const int warps = gridDim.x * (kThreadsA / 32);
     while (unit < total_units) {  // whole warps only
-        if (!keys_unit<S, kP>(frames, n_frames, unit, band_stride) && lane == 0) {
-            const int slot = atomicAdd(fallback, 1);
-            fallback[2 + slot] = unit;
-        }
+        if (!keys_unit<S, kP>(frames, n_frames, unit, band_stride))
+            afloat::stage_a_unit<S>(frames, n_frames, unit, kStopFull, band_stride);
         int next = 0;
         if (lane == 0) next = atomicAdd(work + 2, 1);
         unit = warps + __shfl_sync(0xffffffffu, next, 0);
@@ -564,27 +564,27 @@ stage_a_keys(const FrameDesc* __restrict__ frames, int n_frames, int total_units
 
 template <int S, int kP>
 cudaError_t launch_shape(const FrameDesc* d_frames, int n_frames, int total_units, int* work, int band_stride,
-                         int* fallback, int sm_count, cudaStream_t stream)
+                         int sm_count, cudaStream_t stream)
 {
     const int per_block = kThreadsA / 32;
     int grid = (total_units + per_block - 1) / per_block;
     if (grid > kStageAKeysWarpsPerSM * sm_count) grid = kStageAKeysWarpsPerSM * sm_count;  // persistent
     if (grid < 1) return cudaSuccess;
     return launch_after_previous(stage_a_keys<S, kP>, dim3(grid), dim3(kThreadsA), 0, stream, d_frames, n_frames,
-                                 total_units, work, band_stride, fallback);
+                                 total_units, work, band_stride);
 }
 
 template <int kP>
 cudaError_t launch_words(const FrameDesc* d_frames, int n_frames, int total_units, int shape, int* work,
-                         int band_stride, int* fallback, int sm_count, cudaStream_t stream)
+                         int band_stride, int sm_count, cudaStream_t stream)
 {
     switch (shape) {
-    case kDiamond5: return launch_shape<kDiamond5, kP>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
-    case kFull5: return launch_shape<kFull5, kP>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
-    case kCross5: return launch_shape<kCross5, kP>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
-    case kFull3: return launch_shape<kFull3, kP>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
-    case kCircle5: return launch_shape<kCircle5, kP>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
-    case kFull7: return launch_shape<kFull7, kP>(d_frames, n_frames, total_units, work, band_stride, fallback, sm_count, stream);
+    case kDiamond5: return launch_shape<kDiamond5, kP>(d_frames, n_frames, total_units, work, band_stride, sm_count, stream);
+    case kFull5: return launch_shape<kFull5, kP>(d_frames, n_frames, total_units, work, band_stride, sm_count, stream);
+    case kCross5: return launch_shape<kCross5, kP>(d_frames, n_frames, total_units, work, band_stride, sm_count, stream);
+    case kFull3: return launch_shape<kFull3, kP>(d_frames, n_frames, total_units, work, band_stride, sm_count, stream);
+    case kCircle5: return launch_shape<kCircle5, kP>(d_frames, n_frames, total_units, work, band_stride, sm_count, stream);
+    case kFull7: return launch_shape<kFull7, kP>(d_frames, n_frames, total_units, work, band_stride, sm_count, stream);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -592,12 +592,12 @@ cudaError_t launch_words(const FrameDesc* d_frames, int n_frames, int total_unit
 }  // namespace
 
 cudaError_t launch_stage_a_keys(const FrameDesc* d_frames, int n_frames, int total_units, int shape, int strip_cols,
-                                int* work, int band_stride, int* fallback, int sm_count, cudaStream_t stream)
+                                int* work, int band_stride, int sm_count, cudaStream_t stream)
 {
     if (strip_cols == 64)
-        return launch_words<1>(d_frames, n_frames, total_units, shape, work, band_stride, fallback, sm_count, stream);
+        return launch_words<1>(d_frames, n_frames, total_units, shape, work, band_stride, sm_count, stream);
     if (strip_cols == 128)
-        return launch_words<2>(d_frames, n_frames, total_units, shape, work, band_stride, fallback, sm_count, stream);
+        return launch_words<2>(d_frames, n_frames, total_units, shape, work, band_stride, sm_count, stream);
 
     return cudaErrorInvalidValue;
 }

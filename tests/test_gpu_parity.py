@@ -459,8 +459,8 @@ def test_results_do_not_depend_on_tuning(ctx):
 @pytest.mark.parametrize("quantize", [False, True])
 def test_narrow_strips_every_element(ctx, shape, quantize):
     # stage A in 64-column strips (two columns per lane) for every element, on
-    # keys and (off-grid depths) through the float kernel's fallback on the
-    # narrow strips' units; frames wider than one strip with a ragged tail
+    # keys and (off-grid depths) on floats, the key kernel redoing the narrow
+    # strips' units itself; frames wider than one strip with a ragged tail
     from paper_1802_00036_gb300 import dc
     f = synth.random_sparse(70, 233, 0.12, 61, quantize=quantize)
     dc.dc_set_tuning(ctx.h, 8, 5, 160, 64)
