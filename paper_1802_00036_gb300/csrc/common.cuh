@@ -227,6 +227,15 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
                            const StageBParams& p, int* worklist, int* ffill, int sm_count, int ctas_per_sm,
                            const CUtensorMap* cmap, int* err, cudaStream_t stream);
 
+// Load every kernel of a translation unit on the current device
+// (cudaFuncGetAttributes on each), so that no later launch pays CUDA's lazy
+// module loading; dc_create calls them all.
+cudaError_t preload_stage_a();
+cudaError_t preload_stage_a_keys();
+cudaError_t preload_stage_b();
+cudaError_t preload_metrics();
+cudaError_t preload_project();
+
 // Accuracy measures (metrics.cu): acc holds 5 n doubles of scratch, out
 // (device) receives 5 n doubles.
 cudaError_t launch_metrics(const float* pred, const float* gt, int n, int H, int W, double* acc, double* out,

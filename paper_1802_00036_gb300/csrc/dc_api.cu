@@ -258,6 +258,20 @@ cudaError_t table_put_chunk(const FrameDesc* desc, int n, FrameDesc* dst, unsign
     return cudaGetLastError();
 }
 
+cudaError_t preload_kernels()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, table_put<8>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, table_put<64>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, table_put<352>);
+    if (e == cudaSuccess) e = preload_stage_a();
+    if (e == cudaSuccess) e = preload_stage_a_keys();
+    if (e == cudaSuccess) e = preload_stage_b();
+    if (e == cudaSuccess) e = preload_metrics();
+    if (e == cudaSuccess) e = preload_project();
+    return e;
+}
+
 // Store n descriptors at dst (chunks of up to 352 per launch), reset
 // top_ints column tops, zero *counter and *ffill (when not null); returns
 // the number of launches through *launches.
@@ -589,6 +603,9 @@ dc_status dc_create(dc_ctx** out, int device, size_t scratch_budget_bytes)
     bool ok = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&ctx->done, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaMalloc(&ctx->err, sizeof(int)) == cudaSuccess && cudaMemset(ctx->err, 0, sizeof(int)) == cudaSuccess;
+    // every kernel loaded now: no call pays CUDA's lazy module loading (tens
+    // of milliseconds, at the first launch of each kernel otherwise)
+    ok = ok && preload_kernels() == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         dc_destroy(ctx);

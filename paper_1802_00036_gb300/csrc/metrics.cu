@@ -73,6 +73,14 @@ __global__ void metrics_finish(const double* __restrict__ acc, double* __restric
 
 }  // namespace
 
+cudaError_t preload_metrics()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, metrics_sum);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, metrics_finish);
+    return e;
+}
+
 cudaError_t launch_metrics(const float* pred, const float* gt, int n, int H, int W, double* acc, double* out,
                            cudaStream_t stream)
 {

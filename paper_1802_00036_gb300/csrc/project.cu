@@ -48,6 +48,14 @@ __global__ void far_to_empty(unsigned* __restrict__ bits, int H, int W, int pitc
 
 }  // namespace
 
+cudaError_t preload_project()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, project_points);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, far_to_empty);
+    return e;
+}
+
 cudaError_t launch_project(const float* xyz, long long n, const double* P, int H, int W, double d_min,
                            double d_max, float* depth, int pitch, cudaStream_t stream)
 {

@@ -47,6 +47,18 @@ cudaError_t launch_shape(const FrameDesc* d_frames, int n_frames, int total_unit
 
 }  // namespace
 
+cudaError_t preload_stage_a()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, stage_a_stream<kDiamond5>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_a_stream<kFull5>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_a_stream<kCross5>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_a_stream<kFull3>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_a_stream<kCircle5>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_a_stream<kFull7>);
+    return e;
+}
+
 int stage_a_halo(int shape)
 {
     return shape == kFull3 ? 8 : (shape == kFull7 ? 10 : 9);

@@ -591,6 +591,27 @@ cudaError_t launch_words(const FrameDesc* d_frames, int n_frames, int total_unit
 
 }  // namespace
 
+namespace {
+template <int kP>
+cudaError_t preload_words()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, stage_a_keys<kDiamond5, kP>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_a_keys<kFull5, kP>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_a_keys<kCross5, kP>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_a_keys<kFull3, kP>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_a_keys<kCircle5, kP>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_a_keys<kFull7, kP>);
+    return e;
+}
+}  // namespace
+
+cudaError_t preload_stage_a_keys()
+{
+    const cudaError_t e = preload_words<1>();
+    return e == cudaSuccess ? preload_words<2>() : e;
+}
+
 cudaError_t launch_stage_a_keys(const FrameDesc* d_frames, int n_frames, int total_units, int shape, int strip_cols,
                                 int* work, int band_stride, int sm_count, cudaStream_t stream)
 {

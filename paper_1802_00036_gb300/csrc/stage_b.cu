@@ -2003,6 +2003,16 @@ int occupancy_ctas(Kern kernel, size_t smem)
     return n < 1 ? 1 : n;
 }
 
+cudaError_t preload_stage_b()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, stage_b_main<true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_b_main<false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_b_fill_keys);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_b_fill);
+    return e;
+}
+
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,
                            const StageBParams& p, int* worklist, int* ffill, int sm_count, int ctas_per_sm,
                            const CUtensorMap* cmap, int* err, cudaStream_t stream)
