@@ -77,14 +77,15 @@ def peaks():
 
 def measured_counters(stage):
     """A stage's ncu counters per launch from the committed summary, or None
-    if the kernel source changed since that capture."""
+    if a source of the kernel changed since that capture."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             entry = json.load(fh)[stage]
-        with open(os.path.join(ROOT, entry["source"]), "rb") as fh:
-            if hashlib.sha256(fh.read()).hexdigest() != entry["source_sha256"]:
-                return None
+        for path, digest in entry["sources"].items():
+            with open(os.path.join(ROOT, path), "rb") as fh:
+                if hashlib.sha256(fh.read()).hexdigest() != digest:
+                    return None
         return entry
     except Exception:
         return None
