@@ -1684,57 +1684,38 @@ stage_b_fill_keys(const FrameDesc* __restrict__ frames, int n_frames, StageBPara
             }
         }
         __syncthreads();
-        // the passes of the doubling: steps 1, 2, 4, .. below P, then wl - P
-        const int npass = (31 - __clz(P)) + (wl > P ? 1 : 0);
-        // window maxima down the columns: rows [0, kER) end with the maximum
-        // over [r, r + 2 Rl]; rows beyond the region count as key 0.  A warp
-        // takes two word columns at a time (two independent chains)
+        // window maxima down the columns, in place (van Herk / Gil-Werman):
+        // rows [0, kER) end with the maximum over [r, r + 2 Rl].  In blocks of
+        // wl rows: going down block [b0, b0 + wl) from its end, each row takes
+        // the maximum from it to the block's end; going up again, row b0 + i
+        // takes the larger of that and the maximum of the next block's first i
+        // rows, which is its window.  The next block is overwritten only after
+        // this one is done.  One thread per word column (two columns each).
         {
-            constexpr int kVR = (kER + 2 * (kMaxLargeFill / 2) + 31) / 32;
-            const int nvr = (GR + 31) / 32;  // registers in use (warp-uniform)
             const int wc0 = sh >> 1, wc1 = (sh + GC + 1) >> 1;
-            constexpr int kWarps = kThreadsB / 32;
-            for (int wc = wc0 + warp; wc < wc1; wc += 2 * kWarps) {
-                const int wc2 = wc + kWarps;
-                const bool two = wc2 < wc1;  // warp-uniform
-                unsigned v[kVR], u[kVR];
-#pragma unroll
-                for (int j = 0; j < kVR; ++j) {
-                    const int r = lane + 32 * j;
-                    v[j] = r < GR ? Gw[r * GSW + wc] : 0u;
-                    u[j] = (two && r < GR) ? Gw[r * GSW + wc2] : 0u;
-                }
-                for (int pass = 0; pass < npass; ++pass) {
-                    // v[r] = max(v[r], v[r + s]), 0 < s < 32
-                    const int s = (1 << pass) < P ? (1 << pass) : wl - P;
-                    const int src = (lane + s) & 31;
-                    const bool wrap = lane + s >= 32;
-                    unsigned cv = 0u, cu = 0u;  // register j + 1's shuffled words, from the step before
-#pragma unroll
-                    for (int j = kVR - 1; j >= 0; --j) {
-                        if (j < nvr) {
-                            const unsigned a = __shfl_sync(0xffffffffu, v[j], src);
-                            const unsigned b = __shfl_sync(0xffffffffu, u[j], src);
-                            const unsigned mv = __vmaxu2(v[j], wrap ? cv : a);
-                            const unsigned mu = __vmaxu2(u[j], wrap ? cu : b);
-                            cv = a;
-                            cu = b;
-                            v[j] = mv;
-                            u[j] = mu;
-                        }
+            for (int wc = wc0 + tid; wc < wc1; wc += kThreadsB) {
+                unsigned* col = Gw + wc;
+                for (int b0 = 0; b0 < kER; b0 += wl) {
+                    unsigned h = 0u;
+#pragma unroll 4
+                    for (int r = b0 + wl - 1; r >= b0; --r) {
+                        h = __vmaxu2(h, col[r * GSW]);
+                        col[r * GSW] = h;
                     }
-                }
-#pragma unroll
-                for (int j = 0; j < kVR; ++j) {
-                    const int r = lane + 32 * j;
-                    if (r < kER) {
-                        Gw[r * GSW + wc] = v[j];
-                        if (two) Gw[r * GSW + wc2] = u[j];
+                    const int n = min(wl, kER - b0);
+                    unsigned g = 0u;
+                    col[b0 * GSW] = h;  // i = 0: the block itself
+#pragma unroll 4
+                    for (int i = 1; i < n; ++i) {
+                        g = __vmaxu2(g, col[(b0 + wl + i - 1) * GSW]);
+                        col[(b0 + i) * GSW] = __vmaxu2(col[(b0 + i) * GSW], g);
                     }
                 }
             }
         }
         __syncthreads();
+        // the passes of the doubling: steps 1, 2, 4, .. below P, then wl - P
+        const int npass = (31 - __clz(P)) + (wl > P ? 1 : 0);
         // window maxima along the rows [0, kER): positions [sh, sh + kEC) end
         // with the maximum over [c, c + 2 Rl]; one warp per pair of rows, word
         // m in lane m % 32, register m / 32, a step of s positions is the word
