@@ -1568,13 +1568,12 @@ __host__ __device__ constexpr size_t fill_key_gbytes(int large_radius)
 // cp.async chunks (the few across the frame's edges by plain loads, key 0
 // outside it), step 5 is applied per column, and K (the median's packed
 // layout) takes E over tile + 4, border replicated.  The window maxima are
-// taken in place on packed words (two columns each) by doubling (a pass
-// with step s leaves at each position the maximum of the next 2 s; after
-// the largest power of two P within the window, one pass at wl - P): down
-// the columns with each warp holding a word column in registers (row r in
-// lane r % 32, register r / 32; a step is two warp shuffles), then along
-// the rows with word pairs (a byte permute shifts an odd step by one
-// column).  K's empty positions take the maximum at their window's corner;
+// taken in place by van Herk and Gil-Werman's scheme (three maxima per
+// value whatever the window: per block of wl values the maxima to the
+// block's end, then those combined with the running maxima of the next
+// block's start): down the columns on packed words (two columns each), one
+// thread per word column, then along the rows on keys, one thread per row.
+// K's empty positions take the maximum at their window's corner;
 // then the packed median, the exact blur on keys and the store.  A tile
 // whose region holds a value off the key grid goes to the float list
 // (ffill[0] of them from ffill[1]) for stage_b_fill.  About 41 KB of shared
@@ -1598,10 +1597,8 @@ stage_b_fill_keys(const FrameDesc* __restrict__ frames, int n_frames, StageBPara
     unsigned* ctv = reinterpret_cast<unsigned*>(ctop + GC);
 
     const int count = worklist[0];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
     const int wl = 2 * Rl + 1;
-    int P = 1;
-    while (2 * P <= wl) P *= 2;
     for (int w = blockIdx.x; w < count; w += gridDim.x) {
         __syncthreads();
         const int t = worklist[3 + w];
@@ -1714,63 +1711,41 @@ stage_b_fill_keys(const FrameDesc* __restrict__ frames, int n_frames, StageBPara
             }
         }
         __syncthreads();
-        // the passes of the doubling: steps 1, 2, 4, .. below P, then wl - P
-        const int npass = (31 - __clz(P)) + (wl > P ? 1 : 0);
-        // window maxima along the rows [0, kER): positions [sh, sh + kEC) end
-        // with the maximum over [c, c + 2 Rl]; one warp per pair of rows, word
-        // m in lane m % 32, register m / 32, a step of s positions is the word
-        // q = s / 2 further (s even), or the pair across words q and q + 1
-        // (s odd: a byte permute)
-        {
-            constexpr int kPW = (fill_key_stride(kEC + 2 * (kMaxLargeFill / 2)) / 2 + 31) / 32;
-            constexpr int kWarps = kThreadsB / 32;
-            const int npw = (GSW + 31) / 32;  // registers in use (warp-uniform)
-            for (int k = warp; k < kER; k += 2 * kWarps) {
-                const int k2 = k + kWarps;
-                const bool two = k2 < kER;  // warp-uniform
-                unsigned* row = Gw + k * GSW;
-                unsigned* row2 = Gw + (two ? k2 : k) * GSW;
-                unsigned v[kPW], u[kPW];
-#pragma unroll
-                for (int j = 0; j < kPW; ++j) {
-                    const int m = lane + 32 * j;
-                    v[j] = m < GSW ? row[m] : 0u;
-                    u[j] = m < GSW ? row2[m] : 0u;
+        // window maxima along the rows [0, kER), in place by the same scheme:
+        // region columns [0, kEC) end with the maximum over [l, l + 2 Rl].  One
+        // thread per row; a row's blocks start at column o (0..14 by the
+        // thread's lane, so that at each step the rows of a warp reach
+        // different banks: at the paper's 31 x 31 the rows are 24 words mod 32
+        // apart), and columns [0, o) are a head block before them.
+        if (tid < kER) {
+            unsigned short* x = Gk + tid * GSk + sh;
+            const int o = min(2 * ((tid & 31) >> 2), wl - 1);
+            if (o > 0) {
+                unsigned h = 0u;
+                for (int l = o - 1; l >= 0; --l) {
+                    h = max(h, (unsigned)x[l]);
+                    x[l] = (unsigned short)h;
                 }
-                for (int pass = 0; pass < npass; ++pass) {
-                    const int s = (1 << pass) < P ? (1 << pass) : wl - P;
-                    const int q = s >> 1;
-                    const int src0 = (lane + q) & 31, src1 = (lane + q + 1) & 31;
-                    const bool wrap0 = lane + q >= 32, wrap1 = lane + q + 1 >= 32;
-                    unsigned c0 = 0u, c1 = 0u, d0 = 0u, d1 = 0u;  // register j + 1's shuffled words
-#pragma unroll
-                    for (int j = kPW - 1; j >= 0; --j) {
-                        if (j < npw) {
-                            const unsigned a0 = __shfl_sync(0xffffffffu, v[j], src0);
-                            const unsigned b0 = __shfl_sync(0xffffffffu, u[j], src0);
-                            unsigned ov = wrap0 ? c0 : a0, ou = wrap0 ? d0 : b0;  // words m + q
-                            if (s & 1) {
-                                const unsigned a1 = __shfl_sync(0xffffffffu, v[j], src1);
-                                const unsigned b1 = __shfl_sync(0xffffffffu, u[j], src1);
-                                ov = __byte_perm(ov, wrap1 ? c1 : a1, 0x5432);  // with words m + q + 1
-                                ou = __byte_perm(ou, wrap1 ? d1 : b1, 0x5432);
-                                c1 = a1;
-                                d1 = b1;
-                            }
-                            c0 = a0;
-                            d0 = b0;
-                            v[j] = __vmaxu2(v[j], ov);
-                            u[j] = __vmaxu2(u[j], ou);
-                        }
-                    }
+                unsigned g = 0u;  // block 0's columns before the first window's end
+                for (int l = o; l < wl - 1; ++l) g = max(g, (unsigned)x[l]);
+                for (int l = 0; l < o; ++l) {
+                    g = max(g, (unsigned)x[l + wl - 1]);
+                    x[l] = (unsigned short)max((unsigned)x[l], g);
                 }
-#pragma unroll
-                for (int j = 0; j < kPW; ++j) {
-                    const int m = lane + 32 * j;
-                    if (m < GSW) {
-                        row[m] = v[j];
-                        if (two) row2[m] = u[j];
-                    }
+            }
+            for (int b0 = o; b0 < kEC; b0 += wl) {
+                unsigned h = 0u;
+#pragma unroll 4
+                for (int l = b0 + wl - 1; l >= b0; --l) {
+                    h = max(h, (unsigned)x[l]);
+                    x[l] = (unsigned short)h;
+                }
+                const int n = min(wl, kEC - b0);
+                unsigned g = 0u;
+#pragma unroll 4
+                for (int i = 1; i < n; ++i) {
+                    g = max(g, (unsigned)x[b0 + wl + i - 1]);
+                    x[b0 + i] = (unsigned short)max((unsigned)x[b0 + i], g);
                 }
             }
         }

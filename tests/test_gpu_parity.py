@@ -68,9 +68,13 @@ def test_first_kernel_shapes(ctx, shape, stop):
             oracle.complete(f, first_kernel=shape, stop_after=stop), stop, shape)
 
 
-@pytest.mark.parametrize("large", [3, 15, 31, 51, 63])
-def test_large_fill_sizes(ctx, large):
-    f = synth.random_sparse(120, 170, 0.004, 31 + large)
+@pytest.mark.parametrize("quantize", [False, True])
+@pytest.mark.parametrize("large", [3, 5, 15, 31, 51, 63])
+def test_large_fill_sizes(ctx, large, quantize):
+    # nearly empty maps: most tiles go to the step-6 worklist (on keys when
+    # the depths are in 1/256 m steps, else on floats), every window size
+    # from the smallest block of the window maxima to the largest
+    f = synth.random_sparse(120, 170, 0.004, 31 + large, quantize=quantize)
     for stop in ("fill_large", "median", "full"):
         compare(gpu_run(ctx, f[None], large_fill=large, stop_after=stop)[0],
                 oracle.complete(f, large_fill=large, stop_after=stop), stop, f"large {large}")
