@@ -1864,50 +1864,65 @@ stage_b_fill(const FrameDesc* __restrict__ frames, int n_frames, StageBParams p,
             const int y = clampi(T.y0 - 4 + k, H), x = clampi(T.x0 - 4 + l, W);
             F[k * kES + l] = G[(y - gy) * GS + sh + (x - gx)];
         }
-        // The window maxima, separable and in place, by doubling: a pass with
-        // step s leaves at each index the maximum of the next 2 s elements
-        // (reading index + s, which that pass has not yet written), until the
-        // largest power of two P <= wl; then max(at j, at j + wl - P) covers
-        // [j, j + wl - 1].  G is E over the wide region; F keeps E over
-        // tile + 4 for the fill below.
+        // The window maxima, separable and in place, by van Herk and
+        // Gil-Werman's scheme (as on keys in stage_b_fill_keys): G is E over
+        // the wide region; F keeps E over tile + 4 for the fill below.
         __syncthreads();
         const int wl = 2 * Rl + 1;
-        int P = 1;
-        while (2 * P <= wl) P *= 2;
         // columns, one thread each (neighbouring threads, neighbouring banks):
         // rows [0, kER) end with the maximum over [r, r + 2 Rl]
         for (int c = tid; c < GC; c += kThreadsB) {
             float* __restrict__ col = G + sh + c;
-            for (int st = 1; st < P; st *= 2)
-                for (int r = 0; r + st < GR; ++r) col[r * GS] = fmaxf(col[r * GS], col[(r + st) * GS]);
-            if (wl > P)
-                for (int r = 0; r < kER; ++r) col[r * GS] = fmaxf(col[r * GS], col[(r + wl - P) * GS]);
+            for (int b0 = 0; b0 < kER; b0 += wl) {
+                float h = ninf();
+#pragma unroll 4
+                for (int r = b0 + wl - 1; r >= b0; --r) {
+                    h = fmaxf(h, col[r * GS]);
+                    col[r * GS] = h;
+                }
+                const int n = min(wl, kER - b0);
+                float g = ninf();
+#pragma unroll 4
+                for (int i = 1; i < n; ++i) {
+                    g = fmaxf(g, col[(b0 + wl + i - 1) * GS]);
+                    col[(b0 + i) * GS] = fmaxf(col[(b0 + i) * GS], g);
+                }
+            }
         }
         __syncthreads();
-        // rows [0, kER), one warp each: lanes read a pass's pairs, then write;
-        // columns [0, kEC) end with the maximum over [c, c + 2 Rl]
-        {
-            constexpr int kPer = (kEC + 2 * (kMaxLargeFill / 2) + 31) / 32;  // columns a lane holds
-            const int warp = tid >> 5, lane = tid & 31;
-            for (int k = warp; k < kER; k += kThreadsB / 32) {
-                float* __restrict__ row = G + k * GS + sh;
-                for (int st = 1; st <= P; st *= 2) {
-                    const int step = st < P ? st : wl - P;  // the last pass combines at wl - P
-                    const int n = st < P ? GC - 2 * st + 1 : kEC;
-                    if (st == P && wl == P) break;
-                    float v[kPer];
-#pragma unroll
-                    for (int j = 0; j < kPer; ++j) {
-                        const int c = lane + 32 * j;
-                        v[j] = c < n ? fmaxf(row[c], row[c + step]) : 0.0f;
-                    }
-                    __syncwarp();
-#pragma unroll
-                    for (int j = 0; j < kPer; ++j) {
-                        const int c = lane + 32 * j;
-                        if (c < n) row[c] = v[j];
-                    }
-                    __syncwarp();
+        // rows [0, kER), one thread each, columns [0, kEC) end with the maximum
+        // over [c, c + 2 Rl]; a row's blocks start at column o (0..7 by the
+        // thread's lane: at the paper's 31 x 31 the rows are 8 banks apart),
+        // columns [0, o) a head block before them
+        if (tid < kER) {
+            float* __restrict__ x = G + tid * GS + sh;
+            const int o = min((tid & 31) >> 2, wl - 1);
+            if (o > 0) {
+                float h = ninf();
+                for (int l = o - 1; l >= 0; --l) {
+                    h = fmaxf(h, x[l]);
+                    x[l] = h;
+                }
+                float g = ninf();  // block 0's columns before the first window's end
+                for (int l = o; l < wl - 1; ++l) g = fmaxf(g, x[l]);
+                for (int l = 0; l < o; ++l) {
+                    g = fmaxf(g, x[l + wl - 1]);
+                    x[l] = fmaxf(x[l], g);
+                }
+            }
+            for (int b0 = o; b0 < kEC; b0 += wl) {
+                float h = ninf();
+#pragma unroll 4
+                for (int l = b0 + wl - 1; l >= b0; --l) {
+                    h = fmaxf(h, x[l]);
+                    x[l] = h;
+                }
+                const int n = min(wl, kEC - b0);
+                float g = ninf();
+#pragma unroll 4
+                for (int i = 1; i < n; ++i) {
+                    g = fmaxf(g, x[b0 + wl + i - 1]);
+                    x[b0 + i] = fmaxf(x[b0 + i], g);
                 }
             }
         }
