@@ -1,6 +1,6 @@
 """The bench's roofline inputs from the committed ncu record: DRAM bytes and
-ALU-pipe instructions per launch are reported only while the kernel source
-still has the recorded hash, and the ALU fraction is instructions over time
+ALU-pipe instructions per launch are reported only while every source of
+the kernel still has the recorded hash, and the ALU fraction is instructions over time
 against 152 SMs x 2 warp-instructions per clock x 2070 MHz."""
 import json
 import os
@@ -21,8 +21,7 @@ def _record_at(tmp_path, monkeypatch, source_text=None):
     rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     src = tmp_path / "k.cu"
     src.write_text("// a kernel\n")
-    rec["stage_b"]["source"] = str(src)
-    rec["stage_b"]["source_sha256"] = hashlib.sha256(src.read_bytes()).hexdigest()
+    rec["stage_b"]["sources"] = {str(src): hashlib.sha256(src.read_bytes()).hexdigest()}
     if source_text is not None:
         src.write_text(source_text)
     (tmp_path / "profiles").mkdir()
