@@ -1490,7 +1490,12 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
     __shared__ int s_next;
     __shared__ __align__(8) unsigned long long s_mbar;  // completion of the region's tensor copy
     unsigned mbar_parity = 0;
+    // the two block-wide tests of tile k, as bits of s_flags[k & 1]: 1 a
+    // column top below the region's first row, 2 one at or above its last
+    __shared__ unsigned s_flags[2];
+    int k = 0;
     if (p.tma && tid == 0) mbar_init(&s_mbar);
+    if (tid == 0) s_flags[0] = s_flags[1] = 0u;
     __syncthreads();
     for (;;) {
         const int H = T.fd.H, W = T.fd.W;
@@ -1502,6 +1507,18 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
         load_tops(T, p, T.x0 - 4, kEC, S.ctop, S.ctv);
         reset_empties(S);
         if (tid == 0) s_next = (int)gridDim.x + atomicAdd(worklist + 1, 1);
+        {
+            // thread tid < kEC has just written column tid's top: its votes go
+            // into the flag word now, and the region's barrier below publishes
+            // them (the other word, tile k - 1's, was last read before this
+            // tile began: cleared for tile k + 1)
+            const int top = tid < kEC ? S.ctop[tid] : kNoTop;
+            const bool below = tid < kEC && top != kNoTop && top > T.y0 - 4;
+            const bool above = tid < kEC && (top == kNoTop || top <= T.y0 - 4 + kER - 1);
+            const unsigned vb = __ballot_sync(0xffffffffu, below), va = __ballot_sync(0xffffffffu, above);
+            if ((tid & 31) == 0 && (vb | va)) atomicOr(&s_flags[k & 1], (vb ? 1u : 0u) | (va ? 2u : 0u));
+            if (tid == 0) s_flags[(k + 1) & 1] = 0u;
+        }
         if (p.tma) {
             const bool arrived = mbar_wait(&s_mbar, mbar_parity);
             mbar_parity ^= 1u;
@@ -1513,15 +1530,15 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
             cp_async_wait_all();
             __syncthreads();
         }
-        const bool ext_tile =
-            __syncthreads_or(tid < kEC && S.ctop[tid] != kNoTop && S.ctop[tid] > T.y0 - 4);
+        const unsigned flags = s_flags[k & 1];
+        ++k;
+        // some column's top lies below the region's first row: step 5 writes
+        const bool ext_tile = (flags & 1u) != 0u;
         const int tn = s_next;
         const bool more = tn < total_tiles;
 
         // a region entirely above its columns' tops: one row does for all
-        const bool const_tile = __syncthreads_and(
-            p.extend_top && p.extend_rows < 0 &&
-            (tid >= kEC || (S.ctop[tid] != kNoTop && S.ctop[tid] > T.y0 - 4 + kER - 1)));
+        const bool const_tile = p.extend_top && p.extend_rows < 0 && (flags & 2u) == 0u;
         // without step 6, a region empty in every column down to its last row
         // has an empty median everywhere (every window holds only empty
         // values): the tile's output is 0
