@@ -16,6 +16,7 @@ batch a frame lands in, so results are the same alone and in the mix.
 """
 from __future__ import annotations
 
+import gc
 import time
 
 import numpy as np
@@ -100,24 +101,32 @@ def drive_native(server: NativeServer, frames_by_sensor, rate_hz: float, seconds
             t_last = now
         return len(got)
 
-    t0 = time.perf_counter()
-    for k, (t, s) in enumerate(zip(times, ids)):
-        due = t0 + t
-        while True:
-            now = time.perf_counter()
-            if now >= due and free:
-                break
-            if not collect() and due - now > 1e-4:
-                time.sleep(min(due - now, 1e-3) * 0.5)
-        pool = pools[s]
-        ptr, H, W = pool[counters[s] % len(pool)]
-        counters[s] += 1
-        b = free.pop()
-        in_flight[k] = (b, due, time.perf_counter())
-        server.submit(ptr, out_ptrs[b], H, W, k)
-    while in_flight:
-        if not collect():
-            time.sleep(5e-5)
+    # no collection pauses in the client while it keeps the schedule (one in
+    # a large process's heap delays a submission by tens of milliseconds)
+    gc_was_on = gc.isenabled()
+    gc.disable()
+    try:
+        t0 = time.perf_counter()
+        for k, (t, s) in enumerate(zip(times, ids)):
+            due = t0 + t
+            while True:
+                now = time.perf_counter()
+                if now >= due and free:
+                    break
+                if not collect() and due - now > 1e-4:
+                    time.sleep(min(due - now, 1e-3) * 0.5)
+            pool = pools[s]
+            ptr, H, W = pool[counters[s] % len(pool)]
+            counters[s] += 1
+            b = free.pop()
+            in_flight[k] = (b, due, time.perf_counter())
+            server.submit(ptr, out_ptrs[b], H, W, k)
+        while in_flight:
+            if not collect():
+                time.sleep(5e-5)
+    finally:
+        if gc_was_on:
+            gc.enable()
     n = len(lat)
     span = max((t_last or t0) - (t0 + (times[0] if n else 0.0)), 1e-9)
     arr = np.array(lat) if lat else np.zeros(1)
