@@ -121,6 +121,7 @@ struct StageBParams {
     int sparse_fill_max;  // a tile with more empty pixels goes to the step-6 worklist
     int row_stride;       // frames of one shape: the batch's tiles per tile row (tile order), else 0
     int tma;              // 1: regions come by one tensor copy through the CUtensorMap of C (frames of one shape)
+    int fill_inline;      // 1: the main pass runs step-6 worklist tiles itself (set by launch_stage_b)
     float ws[5];        // bilateral spatial weight for dy^2+dx^2 = 0,1,2,(3),4
     float inv_2sc2;     // 1 / (2 sigma_color^2)
 };
@@ -223,6 +224,8 @@ cudaError_t launch_stage_a_keys(const FrameDesc* d_frames, int n_frames, int tot
 // err: set to 1 when a bounded device-side wait gives up.
 // ffill: the step-6 tiles off the key grid, ffill[0] of them from ffill[1]
 // (ffill[0] zeroed before the call, room for every tile).
+// Kernels one launch_stage_b call starts for these parameters.
+int stage_b_launches(const StageBParams& p);
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,
                            const StageBParams& p, int* worklist, int* ffill, int sm_count, int ctas_per_sm,
                            const CUtensorMap* cmap, int* err, cudaStream_t stream);

@@ -465,8 +465,8 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         e = launch_stage_b(ctx->table, n, (int)tiles_b, bp, ctx->work, ffill, ctx->sm_count, ctx->tune.b_ctas_per_sm,
                            tma ? &ctx->cmap : nullptr, ctx->err, stream);
         if (e != cudaSuccess) return DC_ERR_CUDA;
-        // stage A is one kernel, stage B one plus the two step-6 passes when step 6 can run
-        ctx->last_launches = table_launches + ((bp.large_fill_on && bp.stop != kStopExtend) ? 4 : 2);
+        // stage A is one kernel, stage B one plus the step-6 passes when step 6 can run
+        ctx->last_launches = table_launches + 1 + stage_b_launches(bp);
     }
     if (ev && cudaEventRecord(ev[2], stream) != cudaSuccess) return DC_ERR_CUDA;
     if (capture) return DC_OK;

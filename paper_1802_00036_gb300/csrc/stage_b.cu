@@ -1084,15 +1084,21 @@ __device__ bool fill_keys(const Tile& T, const StageBParams& p, const MainSmem& 
     return !__syncthreads_or(bad);
 }
 
+// A tile of the step-6 worklist, start to end (defined with its kernel).
+__device__ void fill_tile_keys(const Tile& T, int t, const StageBParams& p, unsigned char* __restrict__ dynk,
+                               int* __restrict__ ffill);
+
 // Steps 5-8 of one tile on keys, from the key box in S.E (region column l
 // at box column l + ko).  The fix pass moves the box into K: row pairs
 // (kp, kp + kHalf) of one column chunk per thread, two 8-byte loads and four
 // byte permutes per chunk, out-of-frame positions zeroed, step 5 applied
 // from the column tops, empty pixels recorded (step 6).  Returns false,
 // having stored nothing, when a value the tile needs is off the key grid.
-template <bool kFill>
+// kInline: a tile with more empty pixels than it fills by itself runs the
+// step-6 worklist's code at once, else it goes to the worklist.
+template <bool kFill, bool kInline>
 __device__ bool tile_keys(const Tile& T, const StageBParams& p, const MainSmem& S, int t, int* worklist,
-                          bool ext_tile)
+                          int* ffill, bool ext_tile)
 {
     const int tid = threadIdx.x, H = T.fd.H, W = T.fd.W;
     const unsigned short* Ek = reinterpret_cast<const unsigned short*>(S.E);
@@ -1185,7 +1191,10 @@ __device__ bool tile_keys(const Tile& T, const StageBParams& p, const MainSmem& 
         return true;
     }
     if (n_empty > p.sparse_fill_max) {
-        if (tid == 0) {
+        if constexpr (kInline) {  // the worklist tile's wide region fits here: do it now
+            __syncthreads();      // every thread is done with this tile's buffers
+            fill_tile_keys(T, t, p, reinterpret_cast<unsigned char*>(S.E), ffill);
+        } else if (tid == 0) {
             const int slot = atomicAdd(worklist, 1);
             worklist[3 + slot] = t;
         }
@@ -1457,8 +1466,11 @@ __device__ void tile_floats(const Tile& T, const StageBParams& p, const MainSmem
 // by byte permutes) unless a value it needs is off the key grid, then on
 // floats.  kFill: step 6 on (one instantiation per setting, so that neither
 // carries the other's code: the kernel's speed is sensitive to its
-// instruction footprint).
-template <bool kFill>
+// instruction footprint).  kInline: the step-6 worklist's tiles are done by
+// the tile's CTA at once (for the capped or absent extension, where many
+// tiles have many empty pixels; a kernel of its own otherwise: that code in
+// this one slows the common case).
+template <bool kFill, bool kInline>
 __global__ void __launch_bounds__(kThreadsB, 5)
 stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles, StageBParams p,
              int* __restrict__ worklist, int* __restrict__ ffill, const __grid_constant__ CUtensorMap cmap,
@@ -1551,7 +1563,7 @@ stage_b_main(const FrameDesc* __restrict__ frames, int n_frames, int total_tiles
             constant_tile_store(T, p, reinterpret_cast<const float*>(S.ctv), S.scratch);
         } else if (void_tile) {
             store_zero_tile(T);
-        } else if (!tile_keys<kFill>(T, p, S, t, worklist, ext_tile)) {
+        } else if (!tile_keys<kFill, kInline>(T, p, S, t, worklist, ffill, ext_tile)) {
             tile_floats<kFill>(T, p, S, t, ffill, ext_tile);
         }
 
@@ -1579,6 +1591,202 @@ __host__ __device__ constexpr size_t fill_key_gbytes(int large_radius)
     return ((g > r ? g : r) + 15) / 16 * 16;
 }
 
+// Step 6 and the rest of the chain for tile t (T) of the step-6 worklist,
+// in shared memory from dynk (stage_b_fill_keys_smem_bytes of it; the
+// caller's block has synchronised, and any earlier use of it is over).
+__device__ void fill_tile_keys(const Tile& T, int t, const StageBParams& p, unsigned char* __restrict__ dynk,
+                               int* __restrict__ ffill)
+{
+    const int Rl = p.large_radius;
+    const int GR = kER + 2 * Rl, GC = kEC + 2 * Rl;
+    const int GSk = fill_key_stride(GC), GSW = GSk / 2;  // keys, words per row
+    unsigned short* Gk = reinterpret_cast<unsigned short*>(dynk);
+    unsigned* Gw = reinterpret_cast<unsigned*>(dynk);
+    float* R = reinterpret_cast<float*>(dynk);
+    unsigned* K = reinterpret_cast<unsigned*>(dynk + fill_key_gbytes(Rl));
+    unsigned short* Mk = reinterpret_cast<unsigned short*>(K + kPR * kES);
+    int* ctop = reinterpret_cast<int*>(Mk + kMR * kMS);
+    unsigned* ctv = reinterpret_cast<unsigned*>(ctop + GC);
+    const int tid = threadIdx.x;
+    const int wl = 2 * Rl + 1;
+    const int H = T.fd.H, W = T.fd.W;
+    const int gy = T.y0 - 4 - Rl, gx = T.x0 - 4 - Rl;  // frame position of the wide region's (0, 0)
+    const int gxa = gx & ~7, sh = gx - gxa;            // buffer column b is frame column gxa + b
+    load_tops(T, p, gx, GC, ctop, ctv);
+    // a wide region empty in every column: every window of step 6 holds
+    // only empty values, so does the median, and the output is 0
+    if (p.stop == kStopFull) {
+        bool empty_cols = true;
+        const int last = min(H - 1, gy + GR - 1);
+        for (int l = tid; l < GC; l += kThreadsB) {
+            const int x = gx + l;
+            if (x >= 0 && x < W) empty_cols = empty_cols && column_empty_to(T, p, x, last);
+        }
+        if (__syncthreads_and(empty_cols)) {
+            store_zero_tile(T);
+            return;
+        }
+    }
+    // C's keys over the wide region's rows, whole 16-byte chunks inside the
+    // frame, the rest key by key with 0 outside the frame
+    const int nch = GSk / 8;
+    for (int i = tid; i < GR * nch; i += kThreadsB) {
+        const int k = i / nch, j = i - k * nch;
+        const int y = gy + k, x = gxa + 8 * j;
+        unsigned short* dst = Gk + k * GSk + 8 * j;
+        if (y >= 0 && y < H && x >= 0 && x + 8 <= W) {
+            cp_async16(dst, T.fd.ck + (size_t)y * T.fd.c_pitch + x);
+        } else {
+            const bool row_in = y >= 0 && y < H;
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                dst[e] = (row_in && x + e >= 0 && x + e < W) ? T.fd.ck[(size_t)y * T.fd.c_pitch + x + e]
+                                                             : (unsigned short)0;
+        }
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    // step 5: the rows above each in-frame column's top (within the cap)
+    if (p.extend_top) {
+        for (int l = tid; l < GC; l += kThreadsB) {
+            const int top = ctop[l], x = gx + l;
+            if (top == kNoTop || x < 0 || x >= W) continue;
+            const int klo = max(-gy, p.extend_rows < 0 ? 0 : top - p.extend_rows - gy);
+            const int khi = min(GR, top - gy);
+            const unsigned short v = (unsigned short)ctv[l];
+            for (int k = max(0, klo); k < khi; ++k) Gk[k * GSk + sh + l] = v;
+        }
+        __syncthreads();
+    }
+    // a value off the key grid anywhere in the buffer: the float pass does the tile
+    unsigned mx = 0u;
+    for (int i = tid; i < GR * GSW; i += kThreadsB) mx = __vmaxu2(mx, Gw[i]);
+    if (__syncthreads_or((mx & 0xFFFFu) > kKeyMax || (mx >> 16) > kKeyMax)) {
+        if (tid == 0) {
+            const int slot = atomicAdd(ffill, 1);
+            ffill[1 + slot] = t;
+        }
+        return;
+    }
+    // K: E over tile + 4, border replicated, rows (kp, kp + kHalf) per word;
+    // thread t < kRowGroups x kChunksPerRow takes column chunk t %
+    // kChunksPerRow of every kRowGroups-th K row
+    const int g = tid / kChunksPerRow, q = tid - g * kChunksPerRow;
+    if (tid < kRowGroups * kChunksPerRow) {
+        int bcol[4];  // buffer columns of the chunk (clamped into the frame)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) bcol[e] = clampi(T.x0 - 4 + 4 * q + e, W) - gxa;
+        for (int kp = g; kp < kPR; kp += kRowGroups) {
+            const unsigned short* ra = Gk + (clampi(T.y0 - 4 + kp, H) - gy) * GSk;
+            const unsigned short* rb = Gk + (clampi(T.y0 - 4 + kp + kHalf, H) - gy) * GSk;
+            unsigned wd[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) wd[e] = (unsigned)ra[bcol[e]] | ((unsigned)rb[bcol[e]] << 16);
+            *reinterpret_cast<uint4*>(K + kp * kES + 4 * q) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        }
+    }
+    __syncthreads();
+    // window maxima down the columns, in place (van Herk / Gil-Werman):
+    // rows [0, kER) end with the maximum over [r, r + 2 Rl].  In blocks of
+    // wl rows: going down block [b0, b0 + wl) from its end, each row takes
+    // the maximum from it to the block's end; going up again, row b0 + i
+    // takes the larger of that and the maximum of the next block's first i
+    // rows, which is its window.  The next block is overwritten only after
+    // this one is done.  One thread per word column (two columns each).
+    {
+        const int wc0 = sh >> 1, wc1 = (sh + GC + 1) >> 1;
+        for (int wc = wc0 + tid; wc < wc1; wc += kThreadsB) {
+            unsigned* col = Gw + wc;
+            for (int b0 = 0; b0 < kER; b0 += wl) {
+                unsigned h = 0u;
+#pragma unroll 4
+                for (int r = b0 + wl - 1; r >= b0; --r) {
+                    h = __vmaxu2(h, col[r * GSW]);
+                    col[r * GSW] = h;
+                }
+                const int n = min(wl, kER - b0);
+                unsigned g = 0u;
+                col[b0 * GSW] = h;  // i = 0: the block itself
+#pragma unroll 4
+                for (int i = 1; i < n; ++i) {
+                    g = __vmaxu2(g, col[(b0 + wl + i - 1) * GSW]);
+                    col[(b0 + i) * GSW] = __vmaxu2(col[(b0 + i) * GSW], g);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // window maxima along the rows [0, kER), in place by the same scheme:
+    // region columns [0, kEC) end with the maximum over [l, l + 2 Rl].  One
+    // thread per row; a row's blocks start at column o (0..14 by the
+    // thread's lane, so that at each step the rows of a warp reach
+    // different banks: at the paper's 31 x 31 the rows are 24 words mod 32
+    // apart), and columns [0, o) are a head block before them.
+    if (tid < kER) {
+        unsigned short* x = Gk + tid * GSk + sh;
+        const int o = min(2 * ((tid & 31) >> 2), wl - 1);
+        if (o > 0) {
+            unsigned h = 0u;
+            for (int l = o - 1; l >= 0; --l) {
+                h = max(h, (unsigned)x[l]);
+                x[l] = (unsigned short)h;
+            }
+            unsigned g = 0u;  // block 0's columns before the first window's end
+            for (int l = o; l < wl - 1; ++l) g = max(g, (unsigned)x[l]);
+            for (int l = 0; l < o; ++l) {
+                g = max(g, (unsigned)x[l + wl - 1]);
+                x[l] = (unsigned short)max((unsigned)x[l], g);
+            }
+        }
+        for (int b0 = o; b0 < kEC; b0 += wl) {
+            unsigned h = 0u;
+#pragma unroll 4
+            for (int l = b0 + wl - 1; l >= b0; --l) {
+                h = max(h, (unsigned)x[l]);
+                x[l] = (unsigned short)h;
+            }
+            const int n = min(wl, kEC - b0);
+            unsigned g = 0u;
+#pragma unroll 4
+            for (int i = 1; i < n; ++i) {
+                g = max(g, (unsigned)x[b0 + wl + i - 1]);
+                x[b0 + i] = (unsigned short)max((unsigned)x[b0 + i], g);
+            }
+        }
+    }
+    __syncthreads();
+    // step 6: an empty position takes the maximum at its window's corner
+    // (the clamped pixel's, at the replicated border)
+    if (tid < kRowGroups * kChunksPerRow) {
+        // a window's corner column is the clamped column - Rl, in buffer columns
+        int bcol[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) bcol[e] = clampi(T.x0 - 4 + 4 * q + e, W) - gxa - Rl;
+        for (int kp = g; kp < kPR; kp += kRowGroups) {
+            uint4* cell = reinterpret_cast<uint4*>(K + kp * kES + 4 * q);
+            uint4 c4 = *cell;
+            unsigned wd[4] = {c4.x, c4.y, c4.z, c4.w};
+            const unsigned mn = __vminu2(__vimin3_u16x2(wd[0], wd[1], wd[2]), wd[3]);
+            if ((mn & 0xFFFFu) > kEmptyKeyMax && (mn >> 16) > kEmptyKeyMax) continue;  // nothing empty
+            const unsigned short* ga = Gk + (clampi(T.y0 - 4 + kp, H) - gy - Rl) * GSk;
+            const unsigned short* gb = Gk + (clampi(T.y0 - 4 + kp + kHalf, H) - gy - Rl) * GSk;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if ((wd[e] & 0xFFFFu) <= kEmptyKeyMax) wd[e] = (wd[e] & 0xFFFF0000u) | ga[bcol[e]];
+                if ((wd[e] >> 16) <= kEmptyKeyMax) wd[e] = (wd[e] & 0xFFFFu) | ((unsigned)gb[bcol[e]] << 16);
+            }
+            *cell = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        }
+    }
+    __syncthreads();
+    if (p.stop == kStopFillLarge) {
+        store_keys_tile(T, K);
+        return;
+    }
+    median_blur_store(T, p, nullptr, K, true, reinterpret_cast<float*>(K), Mk, R);
+}
+
 // Phase 2 on keys: the tiles with more empty pixels than a tile fills
 // itself (worklist[0] of them from worklist[3]), with step 6.  The wide
 // region (tile + 4 + the window radius) of C's keys arrives by 16-byte
@@ -1602,200 +1810,11 @@ stage_b_fill_keys(const FrameDesc* __restrict__ frames, int n_frames, StageBPara
     wait_previous_kernel();  // the worklist and outputs of the main pass
     allow_next_kernel();
     extern __shared__ __align__(16) unsigned char dynk[];
-    const int Rl = p.large_radius;
-    const int GR = kER + 2 * Rl, GC = kEC + 2 * Rl;
-    const int GSk = fill_key_stride(GC), GSW = GSk / 2;  // keys, words per row
-    unsigned short* Gk = reinterpret_cast<unsigned short*>(dynk);
-    unsigned* Gw = reinterpret_cast<unsigned*>(dynk);
-    float* R = reinterpret_cast<float*>(dynk);
-    unsigned* K = reinterpret_cast<unsigned*>(dynk + fill_key_gbytes(Rl));
-    unsigned short* Mk = reinterpret_cast<unsigned short*>(K + kPR * kES);
-    int* ctop = reinterpret_cast<int*>(Mk + kMR * kMS);
-    unsigned* ctv = reinterpret_cast<unsigned*>(ctop + GC);
-
     const int count = worklist[0];
-    const int tid = threadIdx.x;
-    const int wl = 2 * Rl + 1;
     for (int w = blockIdx.x; w < count; w += gridDim.x) {
         __syncthreads();
         const int t = worklist[3 + w];
-        const Tile T = tile_of(frames, n_frames, t, p.row_stride);
-        const int H = T.fd.H, W = T.fd.W;
-        const int gy = T.y0 - 4 - Rl, gx = T.x0 - 4 - Rl;  // frame position of the wide region's (0, 0)
-        const int gxa = gx & ~7, sh = gx - gxa;            // buffer column b is frame column gxa + b
-        load_tops(T, p, gx, GC, ctop, ctv);
-        // a wide region empty in every column: every window of step 6 holds
-        // only empty values, so does the median, and the output is 0
-        if (p.stop == kStopFull) {
-            bool empty_cols = true;
-            const int last = min(H - 1, gy + GR - 1);
-            for (int l = tid; l < GC; l += kThreadsB) {
-                const int x = gx + l;
-                if (x >= 0 && x < W) empty_cols = empty_cols && column_empty_to(T, p, x, last);
-            }
-            if (__syncthreads_and(empty_cols)) {
-                store_zero_tile(T);
-                continue;
-            }
-        }
-        // C's keys over the wide region's rows, whole 16-byte chunks inside the
-        // frame, the rest key by key with 0 outside the frame
-        const int nch = GSk / 8;
-        for (int i = tid; i < GR * nch; i += kThreadsB) {
-            const int k = i / nch, j = i - k * nch;
-            const int y = gy + k, x = gxa + 8 * j;
-            unsigned short* dst = Gk + k * GSk + 8 * j;
-            if (y >= 0 && y < H && x >= 0 && x + 8 <= W) {
-                cp_async16(dst, T.fd.ck + (size_t)y * T.fd.c_pitch + x);
-            } else {
-                const bool row_in = y >= 0 && y < H;
-#pragma unroll
-                for (int e = 0; e < 8; ++e)
-                    dst[e] = (row_in && x + e >= 0 && x + e < W) ? T.fd.ck[(size_t)y * T.fd.c_pitch + x + e]
-                                                                 : (unsigned short)0;
-            }
-        }
-        cp_async_commit();
-        cp_async_wait_all();
-        __syncthreads();
-        // step 5: the rows above each in-frame column's top (within the cap)
-        if (p.extend_top) {
-            for (int l = tid; l < GC; l += kThreadsB) {
-                const int top = ctop[l], x = gx + l;
-                if (top == kNoTop || x < 0 || x >= W) continue;
-                const int klo = max(-gy, p.extend_rows < 0 ? 0 : top - p.extend_rows - gy);
-                const int khi = min(GR, top - gy);
-                const unsigned short v = (unsigned short)ctv[l];
-                for (int k = max(0, klo); k < khi; ++k) Gk[k * GSk + sh + l] = v;
-            }
-            __syncthreads();
-        }
-        // a value off the key grid anywhere in the buffer: the float pass does the tile
-        unsigned mx = 0u;
-        for (int i = tid; i < GR * GSW; i += kThreadsB) mx = __vmaxu2(mx, Gw[i]);
-        if (__syncthreads_or((mx & 0xFFFFu) > kKeyMax || (mx >> 16) > kKeyMax)) {
-            if (tid == 0) {
-                const int slot = atomicAdd(ffill, 1);
-                ffill[1 + slot] = t;
-            }
-            continue;
-        }
-        // K: E over tile + 4, border replicated, rows (kp, kp + kHalf) per word;
-        // thread t < kRowGroups x kChunksPerRow takes column chunk t %
-        // kChunksPerRow of every kRowGroups-th K row
-        const int g = tid / kChunksPerRow, q = tid - g * kChunksPerRow;
-        if (tid < kRowGroups * kChunksPerRow) {
-            int bcol[4];  // buffer columns of the chunk (clamped into the frame)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) bcol[e] = clampi(T.x0 - 4 + 4 * q + e, W) - gxa;
-            for (int kp = g; kp < kPR; kp += kRowGroups) {
-                const unsigned short* ra = Gk + (clampi(T.y0 - 4 + kp, H) - gy) * GSk;
-                const unsigned short* rb = Gk + (clampi(T.y0 - 4 + kp + kHalf, H) - gy) * GSk;
-                unsigned wd[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) wd[e] = (unsigned)ra[bcol[e]] | ((unsigned)rb[bcol[e]] << 16);
-                *reinterpret_cast<uint4*>(K + kp * kES + 4 * q) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-            }
-        }
-        __syncthreads();
-        // window maxima down the columns, in place (van Herk / Gil-Werman):
-        // rows [0, kER) end with the maximum over [r, r + 2 Rl].  In blocks of
-        // wl rows: going down block [b0, b0 + wl) from its end, each row takes
-        // the maximum from it to the block's end; going up again, row b0 + i
-        // takes the larger of that and the maximum of the next block's first i
-        // rows, which is its window.  The next block is overwritten only after
-        // this one is done.  One thread per word column (two columns each).
-        {
-            const int wc0 = sh >> 1, wc1 = (sh + GC + 1) >> 1;
-            for (int wc = wc0 + tid; wc < wc1; wc += kThreadsB) {
-                unsigned* col = Gw + wc;
-                for (int b0 = 0; b0 < kER; b0 += wl) {
-                    unsigned h = 0u;
-#pragma unroll 4
-                    for (int r = b0 + wl - 1; r >= b0; --r) {
-                        h = __vmaxu2(h, col[r * GSW]);
-                        col[r * GSW] = h;
-                    }
-                    const int n = min(wl, kER - b0);
-                    unsigned g = 0u;
-                    col[b0 * GSW] = h;  // i = 0: the block itself
-#pragma unroll 4
-                    for (int i = 1; i < n; ++i) {
-                        g = __vmaxu2(g, col[(b0 + wl + i - 1) * GSW]);
-                        col[(b0 + i) * GSW] = __vmaxu2(col[(b0 + i) * GSW], g);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // window maxima along the rows [0, kER), in place by the same scheme:
-        // region columns [0, kEC) end with the maximum over [l, l + 2 Rl].  One
-        // thread per row; a row's blocks start at column o (0..14 by the
-        // thread's lane, so that at each step the rows of a warp reach
-        // different banks: at the paper's 31 x 31 the rows are 24 words mod 32
-        // apart), and columns [0, o) are a head block before them.
-        if (tid < kER) {
-            unsigned short* x = Gk + tid * GSk + sh;
-            const int o = min(2 * ((tid & 31) >> 2), wl - 1);
-            if (o > 0) {
-                unsigned h = 0u;
-                for (int l = o - 1; l >= 0; --l) {
-                    h = max(h, (unsigned)x[l]);
-                    x[l] = (unsigned short)h;
-                }
-                unsigned g = 0u;  // block 0's columns before the first window's end
-                for (int l = o; l < wl - 1; ++l) g = max(g, (unsigned)x[l]);
-                for (int l = 0; l < o; ++l) {
-                    g = max(g, (unsigned)x[l + wl - 1]);
-                    x[l] = (unsigned short)max((unsigned)x[l], g);
-                }
-            }
-            for (int b0 = o; b0 < kEC; b0 += wl) {
-                unsigned h = 0u;
-#pragma unroll 4
-                for (int l = b0 + wl - 1; l >= b0; --l) {
-                    h = max(h, (unsigned)x[l]);
-                    x[l] = (unsigned short)h;
-                }
-                const int n = min(wl, kEC - b0);
-                unsigned g = 0u;
-#pragma unroll 4
-                for (int i = 1; i < n; ++i) {
-                    g = max(g, (unsigned)x[b0 + wl + i - 1]);
-                    x[b0 + i] = (unsigned short)max((unsigned)x[b0 + i], g);
-                }
-            }
-        }
-        __syncthreads();
-        // step 6: an empty position takes the maximum at its window's corner
-        // (the clamped pixel's, at the replicated border)
-        if (tid < kRowGroups * kChunksPerRow) {
-            // a window's corner column is the clamped column - Rl, in buffer columns
-            int bcol[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) bcol[e] = clampi(T.x0 - 4 + 4 * q + e, W) - gxa - Rl;
-            for (int kp = g; kp < kPR; kp += kRowGroups) {
-                uint4* cell = reinterpret_cast<uint4*>(K + kp * kES + 4 * q);
-                uint4 c4 = *cell;
-                unsigned wd[4] = {c4.x, c4.y, c4.z, c4.w};
-                const unsigned mn = __vminu2(__vimin3_u16x2(wd[0], wd[1], wd[2]), wd[3]);
-                if ((mn & 0xFFFFu) > kEmptyKeyMax && (mn >> 16) > kEmptyKeyMax) continue;  // nothing empty
-                const unsigned short* ga = Gk + (clampi(T.y0 - 4 + kp, H) - gy - Rl) * GSk;
-                const unsigned short* gb = Gk + (clampi(T.y0 - 4 + kp + kHalf, H) - gy - Rl) * GSk;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    if ((wd[e] & 0xFFFFu) <= kEmptyKeyMax) wd[e] = (wd[e] & 0xFFFF0000u) | ga[bcol[e]];
-                    if ((wd[e] >> 16) <= kEmptyKeyMax) wd[e] = (wd[e] & 0xFFFFu) | ((unsigned)gb[bcol[e]] << 16);
-                }
-                *cell = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-            }
-        }
-        __syncthreads();
-        if (p.stop == kStopFillLarge) {
-            store_keys_tile(T, K);
-            continue;
-        }
-        median_blur_store(T, p, nullptr, K, true, reinterpret_cast<float*>(K), Mk, R);
+        fill_tile_keys(tile_of(frames, n_frames, t, p.row_stride), t, p, dynk, ffill);
     }
 }
 
@@ -1994,11 +2013,31 @@ int occupancy_ctas(Kern kernel, size_t smem)
 cudaError_t preload_stage_b()
 {
     cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, stage_b_main<true>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_b_main<false>);
+    cudaError_t e = cudaFuncGetAttributes(&a, stage_b_main<true, false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_b_main<true, true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_b_main<false, false>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_b_fill_keys);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, stage_b_fill);
     return e;
+}
+
+namespace {
+// The main pass does the step-6 worklist's tiles itself when the extension
+// is capped or off (then many tiles have many empty pixels) and their wide
+// region fits in its shared memory (windows up to 43 x 43, the paper's 31 x
+// 31 among them): that saves the worklist kernel's launch and spreads the
+// worklist's tiles over the main pass.  Otherwise stage_b_fill_keys.
+bool fill_inline(const StageBParams& p)
+{
+    return p.large_fill_on && (!p.extend_top || p.extend_rows >= 0) &&
+           stage_b_fill_keys_smem_bytes(p.large_radius) <= sizeof(float) * kMainSmemFloats;
+}
+}  // namespace
+
+int stage_b_launches(const StageBParams& p)
+{
+    if (!p.large_fill_on || p.stop == kStopExtend) return 1;
+    return fill_inline(p) ? 2 : 3;
 }
 
 cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_tiles,
@@ -2016,9 +2055,14 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
         e = cudaFuncSetAttribute(stage_b_fill_keys, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)stage_b_fill_keys_smem_bytes(kMaxLargeFill / 2));
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(stage_b_main<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)main_smem);
+        e = cudaFuncSetAttribute(stage_b_main<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)main_smem);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(stage_b_main<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)main_smem);
+        e = cudaFuncSetAttribute(stage_b_main<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)main_smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(stage_b_main<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)main_smem);
         if (e != cudaSuccess) return e;
         configured_dev = dev;
     }
@@ -2030,21 +2074,28 @@ cudaError_t launch_stage_b(const FrameDesc* d_frames, int n_frames, int total_ti
     if (p.tma && cmap) map = *cmap;
     StageBParams q = p;
     q.tma = (p.tma && cmap) ? 1 : 0;
-    cudaError_t e = launch_after_previous(p.large_fill_on ? stage_b_main<true> : stage_b_main<false>, dim3(main_grid),
-                                          dim3(kThreadsB), main_smem, stream, d_frames, n_frames, total_tiles, q,
-                                          worklist, ffill, map, err);
+    q.fill_inline = fill_inline(p) ? 1 : 0;
+    cudaError_t e = launch_after_previous(!p.large_fill_on ? stage_b_main<false, false>
+                                          : q.fill_inline  ? stage_b_main<true, true>
+                                                           : stage_b_main<true, false>,
+                                          dim3(main_grid), dim3(kThreadsB), main_smem, stream, d_frames, n_frames,
+                                          total_tiles, q, worklist, ffill, map, err);
     if (e != cudaSuccess || !p.large_fill_on || p.stop == kStopExtend) return e;
-    // step 6 over the worklist on keys, then on floats over the tiles off the key grid
-    const size_t kfill_smem = stage_b_fill_keys_smem_bytes(p.large_radius);
-    int grid = occupancy_ctas(stage_b_fill_keys, kfill_smem) * sm_count;
-    if (grid > total_tiles) grid = total_tiles;
-    e = launch_after_previous(stage_b_fill_keys, dim3(grid), dim3(kThreadsB), kfill_smem, stream, d_frames, n_frames,
-                              p, static_cast<const int*>(worklist), ffill);
-    if (e != cudaSuccess) return e;
+    // step 6 over the worklist on keys (unless the main pass did its tiles),
+    // then on floats over the tiles off the key grid
+    int grid = 0;
+    if (!q.fill_inline) {
+        const size_t kfill_smem = stage_b_fill_keys_smem_bytes(p.large_radius);
+        grid = occupancy_ctas(stage_b_fill_keys, kfill_smem) * sm_count;
+        if (grid > total_tiles) grid = total_tiles;
+        e = launch_after_previous(stage_b_fill_keys, dim3(grid), dim3(kThreadsB), kfill_smem, stream, d_frames,
+                                  n_frames, q, static_cast<const int*>(worklist), ffill);
+        if (e != cudaSuccess) return e;
+    }
     const size_t fill_smem = stage_b_fill_smem_bytes(p.large_radius);
     grid = occupancy_ctas(stage_b_fill, fill_smem) * sm_count;
     if (grid > total_tiles) grid = total_tiles;
-    return launch_after_previous(stage_b_fill, dim3(grid), dim3(kThreadsB), fill_smem, stream, d_frames, n_frames, p,
+    return launch_after_previous(stage_b_fill, dim3(grid), dim3(kThreadsB), fill_smem, stream, d_frames, n_frames, q,
                                  static_cast<const int*>(ffill));
 }
 
