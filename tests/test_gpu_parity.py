@@ -216,6 +216,24 @@ def test_point_cloud_variants(ctx, variant):
                 oracle.complete(f, stop_after=stop, **variant), stop, str(variant))
 
 
+@pytest.mark.parametrize("large", [31, 51])
+def test_capped_extension_with_scattered_off_grid_depths(ctx, large):
+    # the extension capped at 50 rows sends the upper tiles to step 6's
+    # worklist (run by the main pass itself for windows that fit its shared
+    # memory, 31 here, else by the worklist kernel, 51); depths moved off the
+    # key grid at random put some tiles, or only some tiles' wide step-6
+    # regions, off the grid: those move on to the float passes
+    f = synth.make_frame(synth.ONE_FRAME, synth.frame_seed(2, 9))
+    rng = np.random.default_rng(17)
+    ys, xs = np.nonzero(f > 0)
+    pick = rng.choice(len(ys), max(1, len(ys) // 50), replace=False)
+    f[ys[pick], xs[pick]] += np.float32(1.0 / 1024)
+    for stop in ("fill_large", "median", "full"):
+        compare(gpu_run(ctx, f[None], extend_rows=50, large_fill=large, stop_after=stop)[0],
+                oracle.complete(f, extend_rows=50, large_fill=large, stop_after=stop), stop,
+                f"capped, off-grid, large {large}")
+
+
 @pytest.mark.parametrize("variant", [dict(extend_top=False, large_fill_on=False),
                                      dict(extend_rows=5, large_fill_on=False),
                                      dict(extend_top=False), dict(extend_rows=50),
