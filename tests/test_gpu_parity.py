@@ -389,6 +389,24 @@ def test_uneven_batch_one_call(ctx):
             compare(outs[i].cpu().numpy(), oracle.complete(host[i], stop_after=stop), stop, f"mix {i}")
 
 
+@pytest.mark.parametrize("variant", [dict(extend_rows=20), dict(extend_top=False)])
+def test_uneven_batch_capped_extension(ctx, variant):
+    # frames of four shapes in one call (regions by cp.async, tiles frame by
+    # frame) with the extension capped or off: the tiles with many empty
+    # pixels run the step-6 worklist's code inside the main pass
+    from paper_1802_00036_gb300 import dc
+    specs = [synth.MIX[i % 4] for i in range(4)]
+    host = [synth.make_frame(s, synth.frame_seed(3, i)) for i, s in enumerate(specs)]
+    ins = [torch.from_numpy(h).cuda() for h in host]
+    outs = [torch.full_like(x, -3.0) for x in ins]
+    for stop in ("fill_large", "full"):
+        ctx.complete_frames(list(zip(ins, outs)), dc.params(stop_after=stop, **variant))
+        torch.cuda.synchronize()
+        for i in range(4):
+            compare(outs[i].cpu().numpy(), oracle.complete(host[i], stop_after=stop, **variant), stop,
+                    f"mix {i} {variant}")
+
+
 def test_host_buffers_entry_point(ctx):
     from paper_1802_00036_gb300 import dc
     frames = np.stack([synth.make_frame(SMALL, 900 + i) for i in range(4)])
