@@ -474,6 +474,11 @@ def run_gpu(args, world, rank, local):
             "path_achieved": round(BYTES_PER_PX * px * fps / 1e9, 1),
             "path_frac": round(BYTES_PER_PX * px * fps / 1e9 / hbm, 4),
             "alu": alu_roofline(dom, dom_ms) if B == BATCH else None,
+            # both kernels: the ALU bound and the DRAM traffic per launch (ncu)
+            "by_kernel": {k: {"ms": round(k_ms, 4) if k_ms else None,
+                              "alu": alu_roofline(k, k_ms) if B == BATCH else None,
+                              "traffic": measured_traffic(k) if B == BATCH else None}
+                          for k, k_ms in (("stage_a", a_ms), ("stage_b", b_ms))},
         },
         "kernels_ms": {"stage_a": round(a_ms, 4) if a_ms else None, "stage_b": round(b_ms, 4) if b_ms else None,
                        "calls_timed": len(ktimes), "profiled_every": PROFILE_EVERY},

@@ -414,6 +414,10 @@ __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, 
     float fmn = 8414208.0f;  // the smallest f of input_word: >= 2^23 for depths up to 100 m
 
     const int t0 = r0 - Rh;
+    // every row the stages' outputs hold lies inside the frame (A rows from
+    // t0 - R1, B rows down to t0 - R1 - 4, A rows up to r1 + Rh - 1 - R1):
+    // the per-row frame checks below are skipped
+    const bool rows_inside = t0 - R1 - 4 >= 0 && r1 + Rh - R1 <= H;
     const int nsteps = (r1 - r0) + 2 * Rh;
     float raw[4][kV];
     auto load_row = [&](int t, float (&d)[kV]) {
@@ -479,26 +483,35 @@ __device__ __forceinline__ bool keys_unit(const FrameDesc* __restrict__ frames, 
         KRow<kP> a;
         s2.template push<PHI>(x, a.w + 2, at_left);
         const int ra = t - R1;
+        if (!rows_inside && (ra < 0 || ra >= H)) {
 #pragma unroll
-        for (int v = 0; v < kP; ++v)
-            if (ra < 0 || ra >= H) a.w[2 + v] = kNeutralMax;
-            else if (edge) a.w[2 + v] &= in_mask[v];
+            for (int v = 0; v < kP; ++v) a.w[2 + v] = kNeutralMax;
+        } else if (edge) {
+#pragma unroll
+            for (int v = 0; v < kP; ++v) a.w[2 + v] &= in_mask[v];
+        }
         // step 3, dilation: A(ra) -> D(ra - 2)
         KRow<kP> dd;
         s3d.template push<PHI>(a, dd.w + 2, at_left);
         const int rd = ra - 2;
+        if (!rows_inside && (rd < 0 || rd >= H)) {
 #pragma unroll
-        for (int v = 0; v < kP; ++v)
-            if (rd < 0 || rd >= H) dd.w[2 + v] = kNeutralMin;
-            else if (edge) dd.w[2 + v] |= ~in_mask[v];
+            for (int v = 0; v < kP; ++v) dd.w[2 + v] = kNeutralMin;
+        } else if (edge) {
+#pragma unroll
+            for (int v = 0; v < kP; ++v) dd.w[2 + v] |= ~in_mask[v];
+        }
         // step 3, erosion: D(rd) -> B(rd - 2)
         KRow<kP> b;
         s3e.template push<PHI>(dd, b.w + 2, at_left);
         const int rb = rd - 2;
+        if (!rows_inside && (rb < 0 || rb >= H)) {
 #pragma unroll
-        for (int v = 0; v < kP; ++v)
-            if (rb < 0 || rb >= H) b.w[2 + v] = kNeutralMax;
-            else if (edge) b.w[2 + v] &= in_mask[v];
+            for (int v = 0; v < kP; ++v) b.w[2 + v] = kNeutralMax;
+        } else if (edge) {
+#pragma unroll
+            for (int v = 0; v < kP; ++v) b.w[2 + v] &= in_mask[v];
+        }
         // step 4: B(rb) -> C(rb - 3)
         unsigned c[kP];
         s4.template push<PHI>(b, c, at_left);
