@@ -407,6 +407,25 @@ def test_uneven_batch_capped_extension(ctx, variant):
                     f"mix {i} {variant}")
 
 
+@pytest.mark.parametrize("kw,want", [
+    (dict(), 5),                                   # frame table, stage A, stage B and both step-6 lists
+    (dict(extend_rows=20), 4),                     # worklist tiles inside stage B: no worklist kernel
+    (dict(extend_top=False), 4),
+    (dict(extend_rows=20, large_fill=51), 5),      # a 51 x 51 window's region does not fit there
+    (dict(large_fill_on=False), 3),                # no step 6: no step-6 kernels
+    (dict(stop_after="extend"), 3),
+    (dict(stop_after="fill7"), 2),                 # stage A on floats writes the output
+])
+def test_kernels_launched_per_call(ctx, kw, want):
+    # the launch sequence of one call (dc_last_launch_count), each variant
+    # still giving the oracle's result
+    f = synth.make_frame(SMALL, 321)
+    got = gpu_run(ctx, f[None], **kw)[0]
+    assert ctx.launches() == want
+    stop = kw.get("stop_after", "full")
+    compare(got, oracle.complete(f, **kw), stop, str(kw))
+
+
 def test_host_buffers_entry_point(ctx):
     from paper_1802_00036_gb300 import dc
     frames = np.stack([synth.make_frame(SMALL, 900 + i) for i in range(4)])
