@@ -696,10 +696,29 @@ def run_configs(args, ctx=None):
         msr = timed(lambda i: dc.dc_complete_uniform(ctx.h, dev_in[i][k].data_ptr(), dev_out[i][k].data_ptr(), 32, h,
                                                      w, p, sp), 2)
         per_res[f"{h}x{w}"] = round(32 / msr * 1e3, 1)
+    # each resolution class with its own tuning (the autotuner's choice for a
+    # batch of 32 of it, cached per GPU, batch, frame size and parameters);
+    # the context's tuning is restored afterwards
+    from paper_1802_00036_gb300 import tune
+    keep = dc.dc_get_tuning(ctx.h)
+    per_res_tuned = {}
+    for k, b in enumerate(mix):
+        _, h, w = b.shape
+        choice, source = tune.tuned(ctx, dev_in[0][k], dev_out[0][k], p, stream)
+        msr = timed(lambda i: dc.dc_complete_uniform(ctx.h, dev_in[i][k].data_ptr(), dev_out[i][k].data_ptr(), 32, h,
+                                                     w, p, sp), 2)
+        per_res_tuned[f"{h}x{w}"] = {"tuning": {"a_warps_per_sm": choice[0], "b_ctas_per_sm": choice[1],
+                                                "b_sparse_fill": choice[2], "a_strip_cols": choice[3],
+                                                "source": source},
+                                     "frames_per_s": round(32 / msr * 1e3, 1)}
+    dc.dc_set_tuning(ctx.h, *keep)
     res["uneven_mix"] = {"workload": "128 frames, 32 each of 256x512@3%, 352x1216@5%, 375x1242@5%, 512x2048@10%",
                          "one_call_frames_per_s": round(128 / ms * 1e3, 1),
                          "one_call_GBps": round(px * 8 / ms / 1e6, 1),
-                         "per_resolution_batch_of_32_frames_per_s": per_res}
+                         "per_resolution_batch_of_32_frames_per_s": per_res,
+                         "per_resolution_tuned": per_res_tuned,
+                         "tuning": {"a_warps_per_sm": keep[0], "b_ctas_per_sm": keep[1], "b_sparse_fill": keep[2],
+                                    "a_strip_cols": keep[3], "note": "the one call and the untuned rows"}}
     del dev_in, dev_out
 
     # first element x large-fill size on 32 x 352x1216
