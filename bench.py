@@ -711,12 +711,17 @@ def run_configs(args, ctx=None):
                                                 "b_sparse_fill": choice[2], "a_strip_cols": choice[3],
                                                 "source": source},
                                      "frames_per_s": round(32 / msr * 1e3, 1)}
+    # the one call again, each size's frames with their own step-6 threshold
+    # (the knob that is chosen per tile; the others are launch-wide)
     dc.dc_set_tuning(ctx.h, *keep)
+    ms_cls = timed(lambda i: dc.dc_complete(ctx.h, tables[i], p, sp), 2)
+    dc.dc_set_class_tuning(ctx.h, 0, 0, None)
     res["uneven_mix"] = {"workload": "128 frames, 32 each of 256x512@3%, 352x1216@5%, 375x1242@5%, 512x2048@10%",
                          "one_call_frames_per_s": round(128 / ms * 1e3, 1),
                          "one_call_GBps": round(px * 8 / ms / 1e6, 1),
                          "per_resolution_batch_of_32_frames_per_s": per_res,
                          "per_resolution_tuned": per_res_tuned,
+                         "one_call_per_size_threshold_frames_per_s": round(128 / ms_cls * 1e3, 1),
                          "tuning": {"a_warps_per_sm": keep[0], "b_ctas_per_sm": keep[1], "b_sparse_fill": keep[2],
                                     "a_strip_cols": keep[3], "note": "the one call and the untuned rows"}}
     del dev_in, dev_out

@@ -205,10 +205,22 @@ typedef struct {
 dc_status dc_set_tuning(dc_ctx* ctx, const dc_tuning* t);
 dc_status dc_get_tuning(const dc_ctx* ctx, dc_tuning* t);
 
+/* Tunings per frame size, for calls that mix sizes.  A frame of H x W with
+ * a recorded tuning takes its step-6 threshold (b_sparse_fill, the one
+ * choice that is made per tile) from it in every call; the other knobs are
+ * launch-wide and come from the context's tuning.  dc_autotune records its
+ * choice for its H x W; this records t for H x W, replacing an earlier one,
+ * or with t = NULL forgets every size.  At most DC_MAX_CLASS_TUNINGS sizes
+ * (DC_ERR_UNSUPPORTED beyond); t is checked as by dc_set_tuning.  Drops the
+ * context's cached CUDA graphs (they hold the old thresholds). */
+#define DC_MAX_CLASS_TUNINGS 16
+dc_status dc_set_class_tuning(dc_ctx* ctx, int H, int W, const dc_tuning* t);
+
 /* Time dc_complete_uniform on the caller's n packed frames (device `in` /
  * `out`, as for dc_complete_uniform; `out` is overwritten) under a fixed set
  * of tunings (two rounds of one knob at a time), keep the fastest in the
- * context and return it in *best.  Synchronous; runs the chain ~170 times. */
+ * context, record it for frames of H x W (dc_set_class_tuning) and return
+ * it in *best.  Synchronous; runs the chain ~170 times. */
 dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, int W,
                       const dc_params* params, void* stream, dc_tuning* best);
 

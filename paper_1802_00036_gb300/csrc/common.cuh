@@ -107,6 +107,7 @@ struct FrameDesc {
     int band_a;             // stage A: rows per band
     int ow_a;               // stage A: output columns per strip
     int tiles_x_b, base_b;  // stage B: same
+    int sparse_fill;        // stage B: most empty pixels a tile of this frame fills itself (0..160)
 };
 
 // Runtime parameters of stage B.
@@ -118,7 +119,6 @@ struct StageBParams {
     int extend_top;
     int extend_rows;    // < 0: unlimited
     int stop;
-    int sparse_fill_max;  // a tile with more empty pixels goes to the step-6 worklist
     int row_stride;       // frames of one shape: the batch's tiles per tile row (tile order), else 0
     int tma;              // 1: regions come by one tensor copy through the CUtensorMap of C (frames of one shape)
     int fill_inline;      // 1: the main pass runs step-6 worklist tiles itself (set by launch_stage_b)

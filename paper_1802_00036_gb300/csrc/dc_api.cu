@@ -71,6 +71,15 @@ struct dc_ctx {
         unsigned long long used;
     };
     std::vector<CachedGraph> graphs;
+    // per frame size, a tuning whose step-6 threshold that size's frames
+    // take in every call (dc_set_class_tuning, dc_autotune); off while the
+    // autotuner measures
+    struct ClassTune {
+        int H, W;
+        Tuning t;
+    };
+    std::vector<ClassTune> classes;
+    bool classes_off = false;
     int graph_max = 0;
     unsigned long long graph_tick = 0;
     cudaStream_t s_cap = nullptr;  // stream the graphs are captured from
@@ -379,6 +388,10 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         d.ow_a = stage_a_strip_width(p->first_kernel, strip_cols);
         d.band_a = stage_a_band_rows(f.H, total_strips, (long long)ctx->tune.a_warps_per_sm * ctx->sm_count);
         d.tiles_x_b = ceil_div(f.W, kTileBW);
+        d.sparse_fill = ctx->tune.b_sparse_fill;
+        if (!ctx->classes_off)
+            for (const auto& c : ctx->classes)
+                if (c.H == f.H && c.W == f.W) d.sparse_fill = c.t.b_sparse_fill;
         d.base_a = (int)tiles_a;
         d.base_b = (int)tiles_b;
         tiles_a += (long long)d.tiles_x_a * ceil_div(f.H, d.band_a);
@@ -453,7 +466,6 @@ dc_status run(dc_ctx* ctx, const dc_frame* frames, int n, const dc_params* p, cu
         bp.extend_top = p->extend_top ? 1 : 0;
         bp.extend_rows = p->extend_rows;
         bp.stop = p->stop_after;
-        bp.sparse_fill_max = ctx->tune.b_sparse_fill;
         bp.row_stride = one_shape ? (int)(((frames[0].W + kTileBW - 1) / kTileBW) * (long long)n) : 0;
         const double ss = p->blur == DC_BLUR_BILATERAL ? p->sigma_space : 1.0;
         const double sc = p->blur == DC_BLUR_BILATERAL ? p->sigma_color : 1.0;
@@ -817,14 +829,49 @@ dc_status dc_metrics(dc_ctx* ctx, const float* pred, const float* gt, int n, int
     return DC_OK;
 }
 
+namespace {
+bool tuning_ok(const dc_tuning* t)
+{
+    return t && t->a_warps_per_sm >= 1 && t->a_warps_per_sm <= 64 && t->b_ctas_per_sm >= 1 &&
+           t->b_ctas_per_sm <= 5 && t->b_sparse_fill >= 0 && t->b_sparse_fill <= 160 &&
+           (t->a_strip_cols == 64 || t->a_strip_cols == 128);
+}
+
+// Record (or replace) the tuning of frames of H x W; cached graphs hold the
+// old per-frame thresholds, so they go.
+dc_status put_class(dc_ctx* ctx, int H, int W, const Tuning& t)
+{
+    for (auto& c : ctx->classes)
+        if (c.H == H && c.W == W) {
+            c.t = t;
+            drop_graphs(ctx);
+            return DC_OK;
+        }
+    if ((int)ctx->classes.size() >= DC_MAX_CLASS_TUNINGS) return DC_ERR_UNSUPPORTED;
+    ctx->classes.push_back(dc_ctx::ClassTune{H, W, t});
+    drop_graphs(ctx);
+    return DC_OK;
+}
+}  // namespace
+
 dc_status dc_set_tuning(dc_ctx* ctx, const dc_tuning* t)
 {
-    if (!ctx || !t || t->a_warps_per_sm < 1 || t->a_warps_per_sm > 64 || t->b_ctas_per_sm < 1 ||
-        t->b_ctas_per_sm > 5 || t->b_sparse_fill < 0 || t->b_sparse_fill > 160 ||
-        (t->a_strip_cols != 64 && t->a_strip_cols != 128))
-        return DC_ERR_INVALID_ARG;
+    if (!ctx || !tuning_ok(t)) return DC_ERR_INVALID_ARG;
     ctx->tune = Tuning{t->a_warps_per_sm, t->b_ctas_per_sm, t->b_sparse_fill, t->a_strip_cols};
     return DC_OK;
+}
+
+dc_status dc_set_class_tuning(dc_ctx* ctx, int H, int W, const dc_tuning* t)
+{
+    if (!ctx) return DC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!t) {
+        if (!ctx->classes.empty()) drop_graphs(ctx);
+        ctx->classes.clear();
+        return DC_OK;
+    }
+    if (H < 1 || W < 1 || !tuning_ok(t)) return DC_ERR_INVALID_ARG;
+    return put_class(ctx, H, W, Tuning{t->a_warps_per_sm, t->b_ctas_per_sm, t->b_sparse_fill, t->a_strip_cols});
 }
 
 dc_status dc_get_tuning(const dc_ctx* ctx, dc_tuning* t)
@@ -851,6 +898,7 @@ dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, in
     }
     const Tuning saved = ctx->tune;
     dc_status s = DC_OK;
+    ctx->classes_off = true;  // every candidate's threshold applies to every frame
     // time one tuning: a warm-up call (which also checks the arguments), then three
     auto measure = [&](Tuning t, float* ms) -> dc_status {
         ctx->tune = t;
@@ -904,7 +952,9 @@ dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, in
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    ctx->classes_off = false;
     ctx->tune = (s == DC_OK) ? best_t : saved;
+    if (s == DC_OK) s = put_class(ctx, H, W, best_t);
     best->a_warps_per_sm = ctx->tune.a_warps_per_sm;
     best->b_ctas_per_sm = ctx->tune.b_ctas_per_sm;
     best->b_sparse_fill = ctx->tune.b_sparse_fill;

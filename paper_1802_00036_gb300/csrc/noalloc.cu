@@ -93,6 +93,7 @@ __global__ void noalloc_prepare(FrameDesc* table, unsigned long long* top, unsig
         d.ow_a = ow_a;
         d.tiles_x_b = tiles_x_b;
         d.base_b = i * tiles_b;
+        d.sparse_fill = kDefaultTuning.b_sparse_fill;
         table[i] = d;
     }
     if (top)
@@ -175,7 +176,6 @@ extern "C" dc_status dc_complete_noalloc(const float* in, float* out, int n, int
         bp.extend_top = params->extend_top ? 1 : 0;
         bp.extend_rows = params->extend_rows;
         bp.stop = params->stop_after;
-        bp.sparse_fill_max = kDefaultTuning.b_sparse_fill;
         bp.row_stride = tiles_x_b * n;
         const double ss = params->blur == DC_BLUR_BILATERAL ? params->sigma_space : 1.0;
         const double sc = params->blur == DC_BLUR_BILATERAL ? params->sigma_color : 1.0;

@@ -1190,7 +1190,7 @@ __device__ bool tile_keys(const Tile& T, const StageBParams& p, const MainSmem& 
         store_keys_tile(T, K);
         return true;
     }
-    if (n_empty > p.sparse_fill_max) {
+    if (n_empty > T.fd.sparse_fill) {
         if constexpr (kInline) {  // the worklist tile's wide region fits here: do it now
             __syncthreads();      // every thread is done with this tile's buffers
             fill_tile_keys(T, t, p, reinterpret_cast<unsigned char*>(S.E), ffill);
@@ -1327,7 +1327,7 @@ __device__ void tile_floats(const Tile& T, const StageBParams& p, const MainSmem
     };
     if (p.stop == kStopExtend) {
         store_tile(E);
-    } else if (n_empty > p.sparse_fill_max) {
+    } else if (n_empty > T.fd.sparse_fill) {
         if (tid == 0) {
             const int slot = atomicAdd(ffill, 1);
             ffill[1 + slot] = t;

@@ -94,6 +94,7 @@ SIGNATURES = [
     ("dc_metrics", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     ("dc_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dc_tuning)]),
+    ("dc_set_class_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dc_tuning)]),
     ("dc_get_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dc_tuning)]),
     ("dc_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.POINTER(dc_params), ctypes.c_void_p,
@@ -282,6 +283,16 @@ def dc_set_tuning(ctx, a_warps_per_sm: int, b_ctas_per_sm: int, b_sparse_fill: i
                   a_strip_cols: int = 128) -> None:
     t = dc_tuning(int(a_warps_per_sm), int(b_ctas_per_sm), int(b_sparse_fill), int(a_strip_cols))
     _check(load().dc_set_tuning(ctx, ctypes.byref(t)), "dc_set_tuning")
+
+
+def dc_set_class_tuning(ctx, H: int, W: int, tuning=None) -> None:
+    """Record `tuning` (a_warps_per_sm, b_ctas_per_sm, b_sparse_fill,
+    a_strip_cols) for frames of H x W; None forgets every size."""
+    if tuning is None:
+        _check(load().dc_set_class_tuning(ctx, int(H), int(W), None), "dc_set_class_tuning")
+        return
+    t = dc_tuning(*(int(v) for v in tuning))
+    _check(load().dc_set_class_tuning(ctx, int(H), int(W), ctypes.byref(t)), "dc_set_class_tuning")
 
 
 def dc_get_tuning(ctx) -> tuple[int, int, int, int]:

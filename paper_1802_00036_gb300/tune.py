@@ -54,8 +54,10 @@ def save_cache(data: dict, path: str | None = None) -> None:
 
 def tuned(ctx, inp, out, p: dc.dc_params | None = None, stream=None, use_cache: bool = True):
     """Apply the best tuning for this workload to `ctx` (from the cache, or by
-    running dc_autotune on `inp` -> `out`, (n, H, W) float32 CUDA tensors) and
-    return ((a_warps_per_sm, b_ctas_per_sm, b_sparse_fill, a_strip_cols), source)."""
+    running dc_autotune on `inp` -> `out`, (n, H, W) float32 CUDA tensors),
+    record it for frames of H x W (their step-6 threshold in calls that mix
+    sizes) and return ((a_warps_per_sm, b_ctas_per_sm, b_sparse_fill,
+    a_strip_cols), source)."""
     import torch
     p = p if p is not None else dc.params()
     n, H, W = inp.shape
@@ -66,6 +68,7 @@ def tuned(ctx, inp, out, p: dc.dc_params | None = None, stream=None, use_cache: 
         if key in data and len(data[key]) == 4:
             a, b, f, c = data[key]
             dc.dc_set_tuning(ctx.h, a, b, f, c)
+            dc.dc_set_class_tuning(ctx.h, H, W, (a, b, f, c))  # as dc_autotune records it
             return (a, b, f, c), "cache"
     s = Context_stream(stream)
     t = dc.dc_autotune(ctx.h, inp.data_ptr(), out.data_ptr(), n, H, W, p, s)

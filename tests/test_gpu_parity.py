@@ -426,6 +426,35 @@ def test_kernels_launched_per_call(ctx, kw, want):
     compare(got, oracle.complete(f, **kw), stop, str(kw))
 
 
+def test_per_size_tunings_in_a_mixed_call(ctx):
+    # step-6 thresholds recorded per frame size apply to those frames in a
+    # call that mixes sizes; the results stay the oracle's
+    from paper_1802_00036_gb300 import dc
+    specs = [synth.MIX[i % 4] for i in range(4)]
+    host = [synth.make_frame(s, synth.frame_seed(4, i)) for i, s in enumerate(specs)]
+    ins = [torch.from_numpy(h).cuda() for h in host]
+    outs = [torch.full_like(x, -3.0) for x in ins]
+    try:
+        for i, s in enumerate(specs):
+            dc.dc_set_class_tuning(ctx.h, s.H, s.W, (8, 5, (0, 8, 160, 32)[i], 128))
+        ctx.complete_frames(list(zip(ins, outs)), dc.params(extend_rows=20))
+        torch.cuda.synchronize()
+        for i in range(4):
+            compare(outs[i].cpu().numpy(), oracle.complete(host[i], extend_rows=20), "full", f"mix {i}")
+        with pytest.raises(dc.DcError):
+            dc.dc_set_class_tuning(ctx.h, 10, 10, (8, 5, 161, 128))
+        with pytest.raises(dc.DcError):
+            dc.dc_set_class_tuning(ctx.h, 0, 10, (8, 5, 16, 128))
+        dc.dc_set_class_tuning(ctx.h, 0, 0, None)
+        for k in range(16):  # the table holds 16 sizes
+            dc.dc_set_class_tuning(ctx.h, 10 + k, 10, (8, 5, 16, 128))
+        with pytest.raises(dc.DcError) as e:
+            dc.dc_set_class_tuning(ctx.h, 99, 10, (8, 5, 16, 128))
+        assert e.value.status == 5
+    finally:
+        dc.dc_set_class_tuning(ctx.h, 0, 0, None)
+
+
 def test_host_buffers_entry_point(ctx):
     from paper_1802_00036_gb300 import dc
     frames = np.stack([synth.make_frame(SMALL, 900 + i) for i in range(4)])
