@@ -192,7 +192,7 @@ int stage_a_strip_width(int shape, int strip_cols);
 int stage_a_strips(int W, int shape, int strip_cols);  // strips covering W columns (the first writes its left halo)
 int stage_a_halo(int shape);
 // Rows per stage-A band so that a batch with `total_strips` strips gives
-// about `target_warps` warps; at least 32 rows.
+// about `target_warps` warps; at least 6 rows.
 int stage_a_band_rows(int H, long long total_strips, long long target_warps);
 
 // Launch-shape choices (the results never depend on them).

@@ -81,7 +81,7 @@ int stage_a_band_rows(int H, long long total_strips, long long target_warps)
     long long rows = (H + bands - 1) / bands;
     // short bands cost halo rows but shorten each warp's stream: a small batch
     // (one frame: ~120 units for ~1800 warp slots) finishes sooner
-    if (rows < 8) rows = 8;
+    if (rows < 6) rows = 6;
     return (int)rows;
 }
 
