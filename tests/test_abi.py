@@ -95,3 +95,6 @@ def test_calls_without_a_context_are_refused(lib):
     p = dc.dc_params_default()
     assert L.dc_complete_uniform(None, None, None, 1, 8, 8, ctypes.byref(p), None) == INVALID
     assert L.dc_inject_fault(None, dc.DC_FAULT_WAIT) == INVALID
+    t = dc.dc_tuning(8, 5, 160, 128)
+    assert L.dc_set_class_tuning(None, 8, 8, ctypes.byref(t)) == INVALID
+    assert L.dc_set_class_tuning(None, 0, 0, None) == INVALID
