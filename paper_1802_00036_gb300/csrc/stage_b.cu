@@ -360,9 +360,11 @@ __device__ void blur_store(const Tile& T, const StageBParams& p, float* __restri
             const int b = 2 * cp, x = T.x0 + b;
             const int rows = min(kGRows, H - (T.y0 + a0));
             if (x < W && rows > 0) {
-                // a window of five row-pass rows, slid down the strip (a rolled
-                // loop: the kernel's code is large and shares the instruction
-                // cache between five CTAs in different phases)
+                // a window of five row-pass rows, slid down the strip (on keys
+                // five rows per round, so that no register moves; on floats and
+                // for the blur stop a rolled loop: the kernel's code is large
+                // and shares the instruction cache between five CTAs in
+                // different phases)
                 float2 r[5];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) r[k] = *reinterpret_cast<const float2*>(R + (a0 + k) * kRS + b);
