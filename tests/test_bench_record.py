@@ -56,3 +56,20 @@ def test_changed_source_hides_the_record(tmp_path, monkeypatch):
     assert bench.measured_counters("stage_b") is None
     assert bench.measured_traffic("stage_b") is None
     assert bench.alu_roofline("stage_b", 0.1) is None
+
+
+def test_any_changed_source_hides_the_record(tmp_path, monkeypatch):
+    # a kernel built from two files (stage A: its kernel and the float unit
+    # it inlines) is reported only while both still have their hashes
+    import hashlib
+    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    a, b = tmp_path / "a.cu", tmp_path / "b.cuh"
+    a.write_text("// kernel\n")
+    b.write_text("// its header\n")
+    rec["stage_a"]["sources"] = {str(f): hashlib.sha256(f.read_bytes()).hexdigest() for f in (a, b)}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic("stage_a") == rec["stage_a"]["dram_read_bytes"] + rec["stage_a"]["dram_write_bytes"]
+    b.write_text("// its header, changed\n")
+    assert bench.measured_traffic("stage_a") is None
