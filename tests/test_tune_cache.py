@@ -53,3 +53,37 @@ def test_key_separates_workloads(dc_mod):
     assert len({base, *others}) == len(others) + 1
     assert base == tune.cache_key("GB300", 152, 64, 352, 1216, dc_mod.params())
     json.dumps({base: [1, 2, 3]})  # keys are plain strings
+
+
+class _Tensor:
+    """Stands in for a CUDA tensor: shape, device and a data pointer."""
+
+    def __init__(self, shape):
+        self.shape = shape
+        self.device = "cuda:0"
+
+    def data_ptr(self):
+        return 0
+
+
+def test_tuned_records_the_size_from_cache_and_from_the_autotuner(dc_mod, tmp_path, monkeypatch):
+    # tune.tuned applies a cached tuning (dc_set_tuning) and records it for the
+    # frame size (dc_set_class_tuning), as dc_autotune records its own choice;
+    # on a miss it runs dc_autotune and caches the result (no GPU: the CUDA
+    # and library calls are stood in for)
+    import torch
+    from types import SimpleNamespace
+    monkeypatch.setenv("DCGB_TUNE_CACHE", str(tmp_path / "t.json"))
+    monkeypatch.setattr(torch.cuda, "get_device_properties",
+                        lambda dev: SimpleNamespace(name="GB300", multi_processor_count=152))
+    calls = []
+    monkeypatch.setattr(dc_mod, "dc_set_tuning", lambda h, *t: calls.append(("set", t)))
+    monkeypatch.setattr(dc_mod, "dc_set_class_tuning", lambda h, H, W, t=None: calls.append(("class", H, W, t)))
+    monkeypatch.setattr(dc_mod, "dc_autotune", lambda h, i, o, n, H, W, p, s: (12, 5, 8, 64))
+    ctx = SimpleNamespace(h=1)
+    inp, out = _Tensor((32, 256, 512)), _Tensor((32, 256, 512))
+    t, source = tune.tuned(ctx, inp, out, dc_mod.params(), stream=7)
+    assert (t, source) == ((12, 5, 8, 64), "measured") and calls == []
+    t, source = tune.tuned(ctx, inp, out, dc_mod.params(), stream=7)
+    assert (t, source) == ((12, 5, 8, 64), "cache")
+    assert calls == [("set", (12, 5, 8, 64)), ("class", 256, 512, (12, 5, 8, 64))]
