@@ -219,8 +219,9 @@ dc_status dc_set_class_tuning(dc_ctx* ctx, int H, int W, const dc_tuning* t);
 /* Time dc_complete_uniform on the caller's n packed frames (device `in` /
  * `out`, as for dc_complete_uniform; `out` is overwritten) under a fixed set
  * of tunings (two rounds of one knob at a time), keep the fastest in the
- * context, record it for frames of H x W (dc_set_class_tuning) and return
- * it in *best.  Synchronous; runs the chain ~170 times. */
+ * context, record it for frames of H x W (as dc_set_class_tuning does; with
+ * DC_MAX_CLASS_TUNINGS sizes recorded, the one recorded first makes room)
+ * and return it in *best.  Synchronous; runs the chain ~170 times. */
 dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, int W,
                       const dc_params* params, void* stream, dc_tuning* best);
 

@@ -838,8 +838,9 @@ bool tuning_ok(const dc_tuning* t)
 }
 
 // Record (or replace) the tuning of frames of H x W; cached graphs hold the
-// old per-frame thresholds, so they go.
-dc_status put_class(dc_ctx* ctx, int H, int W, const Tuning& t)
+// old per-frame thresholds, so they go.  A full table refuses a new size,
+// or with evict_oldest drops the size recorded first to make room.
+dc_status put_class(dc_ctx* ctx, int H, int W, const Tuning& t, bool evict_oldest)
 {
     for (auto& c : ctx->classes)
         if (c.H == H && c.W == W) {
@@ -847,7 +848,10 @@ dc_status put_class(dc_ctx* ctx, int H, int W, const Tuning& t)
             drop_graphs(ctx);
             return DC_OK;
         }
-    if ((int)ctx->classes.size() >= DC_MAX_CLASS_TUNINGS) return DC_ERR_UNSUPPORTED;
+    if ((int)ctx->classes.size() >= DC_MAX_CLASS_TUNINGS) {
+        if (!evict_oldest) return DC_ERR_UNSUPPORTED;
+        ctx->classes.erase(ctx->classes.begin());
+    }
     ctx->classes.push_back(dc_ctx::ClassTune{H, W, t});
     drop_graphs(ctx);
     return DC_OK;
@@ -871,7 +875,8 @@ dc_status dc_set_class_tuning(dc_ctx* ctx, int H, int W, const dc_tuning* t)
         return DC_OK;
     }
     if (H < 1 || W < 1 || !tuning_ok(t)) return DC_ERR_INVALID_ARG;
-    return put_class(ctx, H, W, Tuning{t->a_warps_per_sm, t->b_ctas_per_sm, t->b_sparse_fill, t->a_strip_cols});
+    return put_class(ctx, H, W, Tuning{t->a_warps_per_sm, t->b_ctas_per_sm, t->b_sparse_fill, t->a_strip_cols},
+                     false);
 }
 
 dc_status dc_get_tuning(const dc_ctx* ctx, dc_tuning* t)
@@ -954,7 +959,7 @@ dc_status dc_autotune(dc_ctx* ctx, const float* in, float* out, int n, int H, in
     cudaEventDestroy(e1);
     ctx->classes_off = false;
     ctx->tune = (s == DC_OK) ? best_t : saved;
-    if (s == DC_OK) s = put_class(ctx, H, W, best_t);
+    if (s == DC_OK) s = put_class(ctx, H, W, best_t, true);
     best->a_warps_per_sm = ctx->tune.a_warps_per_sm;
     best->b_ctas_per_sm = ctx->tune.b_ctas_per_sm;
     best->b_sparse_fill = ctx->tune.b_sparse_fill;
